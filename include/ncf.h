@@ -1,0 +1,166 @@
+/*
+ * ncf.h -- C ABI of libncf: kernel-weighted auto/cross-correlation of
+ * irregularly sampled time series on one NVIDIA B300 (sm_103a).
+ *
+ * What is computed (arXiv 2609.03866, Sec. 2.3, Eq. kernel_estimator):
+ *
+ *     N_k = sum_i sum_j x_std,i * y_std,j * b(s_j - t_i - tau_k)
+ *     B_k = sum_i sum_j b(s_j - t_i - tau_k)
+ *     c_k = N_k / max(B_k, 1e-16)                       (Algorithms 5-6 clamp)
+ *
+ * for K requested lags tau_k, where x_std = (x - mean(x)) / std(x) with ddof 0
+ * (Appendix, "Prior standardization"), and b is
+ *   - the Gaussian kernel exp(-d^2 / 2h^2) / (sqrt(2 pi) h)  (Eq. Gaussian_kernel), or
+ *   - the rectangle kernel, 1 for |d| <= h, 0 otherwise, h the HALF-width
+ *     (the half-width convention of Algorithms 6 and 8).
+ * The ACF is the case s = t, y = x.  Lag tau > 0 pairs points with
+ * s_j - t_i ~ tau, i.e. y lagging x (Appendix, sign convention).
+ *
+ * Rectangle windows use the predicate of Algorithm 6 evaluated in IEEE FP64
+ * round-to-nearest on the caller's own values: with c = s_j + e*tau_k
+ * (e = +1 for the ACF, -1 for the CCF), a pair counts iff
+ * fl(c - h) <= t_i <= fl(c + h).  Pair counts are exact 64-bit integers.
+ *
+ * Evaluation paths:
+ *   NCF_PATH_SPECTRAL  Wiener-Khinchin (Sec. 2.6): type-1 NUFFT of the values
+ *                      and of unit weights onto a uniform grid, FFT, cross-
+ *                      spectrum times the kernel's Fourier transform, sum of
+ *                      the modes at the K lags.  Gaussian kernel only (the
+ *                      rectangle's transform decays too slowly for a tight
+ *                      tolerance, so the rectangle always uses the exact scan).
+ *   NCF_PATH_WINDOWED  the two-pointer real-space scan (Algorithms 5-8).
+ *   NCF_PATH_AUTO      spectral for the Gaussian, windowed for the rectangle.
+ *
+ * Precision:
+ *   NCF_FP64           FP64 throughout (results within 1e-10 of the FP64
+ *                      definition for the documented workloads).
+ *   NCF_FP32           batched FP32 form: spreading, FFT and the mode-to-lag
+ *                      contraction in FP32 (the contraction on tensor cores
+ *                      where available); FP64 for standardisation, time-to-
+ *                      phase reduction and normalisation.  Rectangle results
+ *                      are identical in both precisions (exact scan).
+ *
+ * Memory and streams: every array argument of ncf_corr and ncf_corr_batch is
+ * a DEVICE pointer owned by the caller, except the CSR offsets of
+ * ncf_corr_batch, which are HOST arrays.  `stream` is a cudaStream_t (NULL =
+ * legacy default stream).  The library owns a workspace per context, grown on
+ * demand with cudaMalloc.  A call validates its inputs, synchronises `stream`
+ * once to read back per-series statistics (time span, variance), then
+ * enqueues its kernels on `stream` and returns; results are ready when the
+ * stream reaches that point.  Validation errors are returned before any
+ * output is written.  No exception crosses the ABI.  A context is not
+ * thread-safe: use one per host thread.
+ */
+#ifndef NCF_H
+#define NCF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NCF_API __attribute__((visibility("default")))
+#else
+#define NCF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NCF_OK = 0,
+    NCF_EINVAL = 1,        /* bad argument: NULL pointer, n < 2, K < 1, h <= 0, bad enum */
+    NCF_ENOTSORTED = 2,    /* times decrease somewhere (equal times are allowed) */
+    NCF_EDEGENERATE = 3,   /* a series has zero variance: x_std undefined */
+    NCF_ENOMEM = 4,        /* workspace allocation failed */
+    NCF_ECUDA = 5,         /* a CUDA runtime call failed; see ncf_last_error */
+    NCF_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
+    NCF_EBUSY = 7,         /* serving: admission budget exhausted */
+    NCF_ENONFINITE = 8,    /* a time, value or lag is NaN or infinite */
+    NCF_EUNSUPPORTED = 9   /* option combination not provided (see ncf_last_error) */
+} ncf_status;
+
+typedef enum { NCF_GAUSSIAN = 0, NCF_RECTANGLE = 1 } ncf_kernel;
+typedef enum { NCF_PATH_AUTO = 0, NCF_PATH_SPECTRAL = 1, NCF_PATH_WINDOWED = 2 } ncf_path;
+typedef enum { NCF_FP64 = 0, NCF_FP32 = 1 } ncf_precision;
+typedef enum {
+    NCF_NORM_NONE = 0,     /* c = N / max(B, 1e-16), Eq. kernel_estimator as written */
+    NCF_NORM_LAG0 = 1      /* Pearson: ACF / ACF(0) (Algorithm 4); CCF / sqrt(ACF_x(0) ACF_y(0)) (Algorithm 10) */
+} ncf_norm;
+
+typedef struct {
+    int32_t kernel;     /* ncf_kernel */
+    int32_t path;       /* ncf_path */
+    int32_t precision;  /* ncf_precision */
+    int32_t norm;       /* ncf_norm */
+    double h;           /* Gaussian sigma, or rectangle half-width; > 0 */
+    double trunc_R;     /* Gaussian windowed path: window [c - R h, c + R h) as in
+                           Algorithm 5 with 6 replaced by R; 0 selects 8 */
+    double tol;         /* spectral path tolerance on the kernel transform and the
+                           spreading; 0 selects 1e-14 (FP64) or 1e-7 (FP32) */
+} ncf_options;
+
+/* Fills *o with: Gaussian, AUTO path, FP64, NORM_NONE, h = 1, trunc_R = 0, tol = 0. */
+NCF_API void ncf_options_default(ncf_options *o);
+
+typedef struct ncf_ctx ncf_ctx;
+
+/* Creates a context bound to CUDA device `device`.  *out is NULL on failure. */
+NCF_API ncf_status ncf_create(ncf_ctx **out, int device);
+/* Frees the context and its workspace (synchronises the device first). */
+NCF_API void ncf_destroy(ncf_ctx *ctx);
+/* Message of the last failed call on ctx ("" if none).  Owned by ctx. */
+NCF_API const char *ncf_last_error(const ncf_ctx *ctx);
+/* Static name of a status code. */
+NCF_API const char *ncf_status_string(ncf_status s);
+/* Number of kernels this context has launched so far. */
+NCF_API uint64_t ncf_launch_count(const ncf_ctx *ctx);
+
+/*
+ * One ACF (s == NULL and y == NULL) or CCF (x at t with y at s).
+ *   t, x   [nx]  device FP64, t non-decreasing, nx >= 2
+ *   s, y   [ny]  device FP64, s non-decreasing, ny >= 2 (ignored for the ACF)
+ *   lags   [K]   device FP64, any order, repeats allowed, K >= 1
+ *   c_out  [K]   device FP64: the estimate c_k, in the order of `lags`
+ *   b_out  [K]   device FP64 or NULL: the effective pair count B_k (unclamped)
+ *   count_out [K] device int64 or NULL: rectangle pair counts (exact); for the
+ *                 Gaussian the number of pairs inside the window (windowed
+ *                 path) or 0 (spectral path)
+ */
+NCF_API ncf_status ncf_corr(ncf_ctx *ctx,
+                    const double *t, const double *x, int64_t nx,
+                    const double *s, const double *y, int64_t ny,
+                    const double *lags, int64_t K, const ncf_options *opt,
+                    double *c_out, double *b_out, int64_t *count_out, void *stream);
+
+/*
+ * B independent ACFs (s == NULL) or CCFs on one shared lag grid, packed CSR:
+ * series b is t[offs_x[b] .. offs_x[b+1]) (and s[offs_y[b] .. offs_y[b+1])).
+ *   offs_x, offs_y  HOST int64 [B+1], offs[0] = 0, non-decreasing, each
+ *                   series of length >= 2
+ *   t, x, s, y      device FP64 arrays of length offs[B]
+ *   lags [K]        device FP64 shared by every series
+ *   c_out, b_out, count_out  device [B*K], row b holds series b (b_out,
+ *                   count_out may be NULL)
+ */
+NCF_API ncf_status ncf_corr_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                          const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                          const double *lags, int64_t K, const ncf_options *opt,
+                          double *c_out, double *b_out, int64_t *count_out, void *stream);
+
+/*
+ * ncf_corr_batch on HOST buffers: copies t, x (s, y) and lags to device
+ * memory owned by the context, runs the batch, copies c (b, count) back and
+ * synchronises the stream before returning.  Host buffers should be pinned
+ * (cudaHostAlloc / torch pin_memory) for full copy bandwidth; pageable memory
+ * works but copies synchronously.  Same argument meanings as ncf_corr_batch.
+ */
+NCF_API ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                               const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                               const double *lags, int64_t K, const ncf_options *opt,
+                               double *c_out, double *b_out, int64_t *count_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NCF_H */

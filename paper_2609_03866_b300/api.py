@@ -1,0 +1,261 @@
+"""Thin Python binding of libncf's C ABI (include/ncf.h).
+
+Argument marshalling only: every step of the computation runs in libncf's
+CUDA kernels.  PyTorch supplies device memory for inputs and outputs and the
+current CUDA stream.  If libncf.so is missing the first call raises; there is
+no fallback implementation.
+
+    ncf.corr(t, x, lags, kernel="gaussian", h=1.0)                # ACF
+    ncf.corr(t, x, lags, kernel="rectangle", h=0.5, s=s, y=y)     # CCF
+    ncf.corr_batch(offs, t, x, lags, ...)                         # B series, CSR
+
+Names follow the paper's calling convention fn(lags, t, x, [s, y], h) -> (c, b)
+(Sec. 2.6, "Unified API"), with keyword arguments in place of positional ones.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libncf.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "ncf.h")
+
+KERNELS = {"gaussian": 0, "rectangle": 1}
+PATHS = {"auto": 0, "spectral": 1, "windowed": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+NORMS = {"none": 0, "lag0": 1}
+
+
+class ncf_options(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("path", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("norm", ctypes.c_int32), ("h", ctypes.c_double), ("trunc_R", ctypes.c_double),
+                ("tol", ctypes.c_double)]
+
+
+class NcfError(RuntimeError):
+    def __init__(self, status: int, name: str, message: str):
+        super().__init__(f"{name}: {message}")
+        self.status = status
+        self.name = name
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libncf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_2609_03866_b300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, dp, i64p = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p
+            L.ncf_options_default.argtypes = [ctypes.POINTER(ncf_options)]
+            L.ncf_options_default.restype = None
+            L.ncf_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
+            L.ncf_create.restype = ctypes.c_int
+            L.ncf_destroy.argtypes = [vp]
+            L.ncf_destroy.restype = None
+            L.ncf_last_error.argtypes = [vp]
+            L.ncf_last_error.restype = ctypes.c_char_p
+            L.ncf_status_string.argtypes = [ctypes.c_int]
+            L.ncf_status_string.restype = ctypes.c_char_p
+            L.ncf_launch_count.argtypes = [vp]
+            L.ncf_launch_count.restype = ctypes.c_uint64
+            L.ncf_corr.argtypes = [vp, dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int64, dp, ctypes.c_int64,
+                                   ctypes.POINTER(ncf_options), dp, dp, i64p, vp]
+            L.ncf_corr.restype = ctypes.c_int
+            for name in ("ncf_corr_batch", "ncf_corr_batch_host"):
+                fn = getattr(L, name)
+                fn.argtypes = [vp, i64p, dp, dp, i64p, dp, dp, ctypes.c_int64, dp, ctypes.c_int64,
+                               ctypes.POINTER(ncf_options), dp, dp, i64p, vp]
+                fn.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def declared_symbols():
+    """Names of the functions include/ncf.h declares with NCF_API."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"NCF_API\s+[\w\s\*]*?\b(ncf_\w+)\s*\(", txt)))
+
+
+def status_name(code: int) -> str:
+    return lib().ncf_status_string(code).decode()
+
+
+def make_options(kernel="gaussian", h=1.0, path="auto", precision="fp64", norm="none",
+                 trunc_R=0.0, tol=0.0) -> ncf_options:
+    o = ncf_options()
+    lib().ncf_options_default(ctypes.byref(o))
+    o.kernel = KERNELS[kernel]
+    o.path = PATHS[path]
+    o.precision = PRECISIONS[precision]
+    o.norm = NORMS[norm]
+    o.h = float(h)
+    o.trunc_R = float(trunc_R)
+    o.tol = float(tol)
+    return o
+
+
+class Context:
+    """Owns an ncf_ctx (workspace, staging buffers) bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._h = ctypes.c_void_p()
+        L = lib()
+        rc = L.ncf_create(ctypes.byref(self._h), int(device))
+        if rc != 0:
+            raise NcfError(rc, status_name(rc), f"ncf_create(device={device}) failed")
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def check(self, rc: int):
+        if rc != 0:
+            raise NcfError(rc, status_name(rc), lib().ncf_last_error(self._h).decode())
+
+    @property
+    def launches(self) -> int:
+        return int(lib().ncf_launch_count(self._h))
+
+    def close(self):
+        if self._h:
+            lib().ncf_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default_ctx = {}
+
+
+def default_context(device: int = 0) -> Context:
+    ctx = _default_ctx.get(device)
+    if ctx is None:
+        ctx = _default_ctx[device] = Context(device)
+    return ctx
+
+
+def _dev(a, device):
+    import torch
+    if not isinstance(a, torch.Tensor):
+        a = torch.as_tensor(np.asarray(a, dtype=np.float64))
+    return a.to(device=device, dtype=torch.float64).contiguous()
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.data_ptr()) if a is not None else ctypes.c_void_p(0)
+
+
+def _stream_handle(stream, device):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def corr(t, x, lags, kernel="gaussian", h=1.0, s=None, y=None, path="auto", precision="fp64",
+         norm="none", trunc_R=0.0, tol=0.0, ctx: Context | None = None, stream=None):
+    """One ACF (s, y omitted) or CCF on the GPU.  Returns dict(c, b, count)
+    of device tensors in the order of `lags`."""
+    import torch
+    ctx = ctx or default_context()
+    dev = torch.device("cuda", ctx.device)
+    t, x, lags = _dev(t, dev), _dev(x, dev), _dev(lags, dev)
+    acf = s is None
+    if not acf:
+        s, y = _dev(s, dev), _dev(y, dev)
+    K = lags.numel()
+    c = torch.empty(K, dtype=torch.float64, device=dev)
+    b = torch.empty(K, dtype=torch.float64, device=dev)
+    cnt = torch.empty(K, dtype=torch.int64, device=dev)
+    o = make_options(kernel, h, path, precision, norm, trunc_R, tol)
+    rc = lib().ncf_corr(ctx.handle, _ptr(t), _ptr(x), t.numel(), _ptr(None if acf else s),
+                        _ptr(None if acf else y), 0 if acf else s.numel(), _ptr(lags), K,
+                        ctypes.byref(o), _ptr(c), _ptr(b), _ptr(cnt), _stream_handle(stream, dev))
+    ctx.check(rc)
+    return {"c": c, "b": b, "count": cnt}
+
+
+def _host_offs(offs):
+    o = np.ascontiguousarray(np.asarray(offs.cpu() if hasattr(offs, "cpu") else offs, dtype=np.int64))
+    return o, ctypes.c_void_p(o.ctypes.data)
+
+
+def corr_batch(offs, t, x, lags, kernel="gaussian", h=1.0, offs_y=None, s=None, y=None, path="auto",
+               precision="fp64", norm="none", trunc_R=0.0, tol=0.0, ctx: Context | None = None,
+               stream=None, out=None):
+    """B series packed CSR (host int64 offsets [B+1]) on one shared lag grid.
+    Returns dict(c, b, count) of device tensors of shape [B, K]."""
+    import torch
+    ctx = ctx or default_context()
+    dev = torch.device("cuda", ctx.device)
+    t, x, lags = _dev(t, dev), _dev(x, dev), _dev(lags, dev)
+    ox, pox = _host_offs(offs)
+    B = ox.size - 1
+    acf = s is None
+    oy, poy = (None, ctypes.c_void_p(0)) if acf else _host_offs(offs_y)
+    if not acf:
+        s, y = _dev(s, dev), _dev(y, dev)
+    K = lags.numel()
+    if out is None:
+        out = {"c": torch.empty(B, K, dtype=torch.float64, device=dev),
+               "b": torch.empty(B, K, dtype=torch.float64, device=dev),
+               "count": torch.empty(B, K, dtype=torch.int64, device=dev)}
+    o = make_options(kernel, h, path, precision, norm, trunc_R, tol)
+    rc = lib().ncf_corr_batch(ctx.handle, pox, _ptr(t), _ptr(x), poy, _ptr(None if acf else s),
+                              _ptr(None if acf else y), B, _ptr(lags), K, ctypes.byref(o),
+                              _ptr(out["c"]), _ptr(out.get("b")), _ptr(out.get("count")),
+                              _stream_handle(stream, dev))
+    ctx.check(rc)
+    return out
+
+
+def corr_batch_host(offs, t, x, lags, kernel="gaussian", h=1.0, offs_y=None, s=None, y=None,
+                    path="auto", precision="fp64", norm="none", trunc_R=0.0, tol=0.0,
+                    ctx: Context | None = None, stream=None, out=None):
+    """corr_batch on host arrays (numpy or pinned CPU tensors): the library
+    copies inputs in and results out and synchronises before returning."""
+    import torch
+    ctx = ctx or default_context()
+    dev = torch.device("cuda", ctx.device)
+
+    def host(a):
+        if a is None:
+            return None
+        if isinstance(a, torch.Tensor):
+            return a.contiguous()
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64))
+
+    ox, pox = _host_offs(offs)
+    B = ox.size - 1
+    acf = s is None
+    oy, poy = (None, ctypes.c_void_p(0)) if acf else _host_offs(offs_y)
+    t, x, lags, s, y = host(t), host(x), host(lags), host(s), host(y)
+    K = lags.numel()
+    if out is None:
+        out = {"c": torch.empty(B, K, dtype=torch.float64), "b": torch.empty(B, K, dtype=torch.float64),
+               "count": torch.empty(B, K, dtype=torch.int64)}
+    o = make_options(kernel, h, path, precision, norm, trunc_R, tol)
+    rc = lib().ncf_corr_batch_host(ctx.handle, pox, _ptr(t), _ptr(x), poy, _ptr(s), _ptr(y), B,
+                                   _ptr(lags), K, ctypes.byref(o), _ptr(out["c"]), _ptr(out.get("b")),
+                                   _ptr(out.get("count")), _stream_handle(stream, dev))
+    ctx.check(rc)
+    return out

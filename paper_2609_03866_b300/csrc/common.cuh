@@ -1,0 +1,108 @@
+// common.cuh -- internal declarations shared by the libncf translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "ncf.h"
+
+namespace ncf {
+
+// Points per CTA of the chunked statistics / keys / prefix passes.
+constexpr int kPrepChunk = 4096;
+
+// Per-series statistics read back by the host after the statistics pass.
+struct SeriesStats {
+    double mean;      // mean of the values
+    double inv_std;   // 1 / population std (ddof 0); 0 when the variance is not positive
+    double t_first;   // first (smallest) time
+    double t_last;    // last (largest) time
+    int64_t n;        // number of points
+    int32_t flags;    // STAT_* bits
+    int32_t pad;
+};
+enum : int32_t { STAT_UNSORTED = 1, STAT_NONFINITE = 2, STAT_DEGENERATE = 4 };
+
+// Partial sums of one chunk of one series (statistics pass).
+struct ChunkPartial {
+    double s1, s2;    // sum of (x - x_ref), sum of (x - x_ref)^2
+    int32_t flags;
+    int32_t pad;
+};
+
+// Fixed-point scales of the exact rectangle scan.
+//   time keys:  T = floor(t * 2^q)               (monotone in t)
+//   values:     X = round(x_std * 2^p)           (exact integer prefix sums)
+struct FixedScales {
+    double tscale;    // 2^q
+    double vscale;    // 2^p
+    int64_t eta;      // half-width of the ambiguity band of a window bound, key units
+    int32_t q, p;
+};
+
+// Stream-ordered bump allocator over the context workspace.
+struct Arena {
+    char *base = nullptr;
+    size_t cap = 0, used = 0;
+    template <class T> T *take(size_t count) {
+        size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        if (used + bytes > cap) return nullptr;
+        T *p = reinterpret_cast<T *>(base + used);
+        used += bytes;
+        return p;
+    }
+};
+
+// ---- statistics and keys (k_prep.cu) ----
+// Chunked statistics: one CTA per chunk of `chunk` points; chunk_base[b] is
+// the first chunk of series b (host-computed, B+1 entries on the device).
+void launch_stats_chunks(const double *t, const double *x, const int64_t *offs,
+                         const int64_t *chunk_base, int64_t B, int64_t n_chunks, int chunk,
+                         ChunkPartial *part, cudaStream_t st);
+void launch_stats_finish(const double *t, const double *x, const int64_t *offs,
+                         const int64_t *chunk_base, int64_t B, const ChunkPartial *part,
+                         SeriesStats *stats, cudaStream_t st);
+// Fixed-point keys and the exclusive prefix sum of the quantised standardised values.
+// Writes Tk[total], Xq[total] and P[total + 1].
+void launch_keys_prefix(const double *t, const double *x, const int64_t *offs,
+                        const int64_t *chunk_base, int64_t B, int64_t n_chunks, int chunk,
+                        const SeriesStats *stats, FixedScales fs, int64_t *Tk, int64_t *Xq,
+                        int64_t *P, int64_t *chunk_sums, int64_t n_total, cudaStream_t st);
+
+// ---- real-space scans (k_scan.cu) ----
+struct ScanTile { int32_t b; int32_t pad; int64_t j0, j1; };
+// Exact rectangle pair counts and fixed-point numerators (Algorithms 6 and 8).
+void launch_rect_scan(const int64_t *Tx, const int64_t *P, const double *tx, const int64_t *offs_x,
+                      const int64_t *Sy, const int64_t *Yq, const double *sy,
+                      const ScanTile *tiles, int64_t n_tiles, const double *lags, int64_t K,
+                      int eps, double h, FixedScales fs,
+                      unsigned long long *cnt, unsigned long long *num128, cudaStream_t st);
+// Gaussian windowed FP64 scan (Algorithms 5 and 7 with window R h).
+void launch_gauss_window(const double *tx, const double *x, const int64_t *offs_x,
+                         const SeriesStats *stx, const double *sy, const double *y,
+                         const SeriesStats *sty, const ScanTile *tiles, int64_t n_tiles,
+                         const double *lags, int64_t K, int eps, double h, double Rh,
+                         double *num, double *den, unsigned long long *cnt, cudaStream_t st);
+// Outer points per scan tile.
+int scan_tile_points();
+// Pearson scale per series from lag-0 ACF accumulators of x (and y for a CCF):
+// scale = c_xx(0) or sqrt(c_xx(0) * c_yy(0)) (Algorithms 4 and 10).
+void launch_lag0_scale_rect(const unsigned long long *cnt_x, const unsigned long long *num_x,
+                            const unsigned long long *cnt_y, const unsigned long long *num_y,
+                            int64_t B, double inv_v2, double *scale, cudaStream_t st);
+void launch_lag0_scale_gauss(const double *num_x, const double *den_x, const double *num_y,
+                             const double *den_y, int64_t B, double *scale, cudaStream_t st);
+// c = N / max(B, 1e-16) from the scan accumulators; optional lag-0 scaling.
+void launch_finish_rect(const unsigned long long *cnt, const unsigned long long *num128,
+                        int64_t B, int64_t K, double inv_v2, const double *scale,
+                        double *c, double *b, int64_t *count, cudaStream_t st);
+void launch_finish_gauss(const double *num, const double *den, const unsigned long long *cnt,
+                         int64_t B, int64_t K, const double *scale, double *c, double *b,
+                         int64_t *count, cudaStream_t st);
+
+}  // namespace ncf
+
+// Launch bookkeeping: every kernel launch in the library goes through this.
+extern thread_local uint64_t *ncf_tls_launch_counter;
+#define NCF_COUNT_LAUNCH() do { if (ncf_tls_launch_counter) ++*ncf_tls_launch_counter; } while (0)

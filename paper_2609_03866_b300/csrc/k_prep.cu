@@ -1,0 +1,244 @@
+// k_prep.cu -- per-series statistics, validation flags, fixed-point keys and
+// exact integer prefix sums.
+//
+// Standardisation (Appendix, "Prior standardization"; step 1 of Algorithms
+// 2, 4, 9, 10): mean and population variance (ddof 0) in FP64.  The pass is
+// chunked -- one CTA per `chunk` points of one series -- so a single series
+// of 1e7 points spreads over the whole GPU; sums are shifted by the series'
+// first value (x - x_ref) so that the one-pass variance S2/n - (S1/n)^2 does
+// not cancel, and partials are combined in a fixed order (deterministic).
+//
+// The exact rectangle scan works on fixed-point images of the inputs:
+//   T_i = floor(t_i * 2^q)  -- monotone, so comparisons against window bounds
+//                              are decided in integer arithmetic except inside
+//                              a narrow ambiguity band that falls back to FP64;
+//   X_i = round(x_std,i * 2^p) and P = exclusive prefix sums of X in int64
+//   with wrap-around: a window sum P[hi] - P[lo] is exact whenever its true
+//   value fits in 63 bits, whatever the prefix values themselves do.
+#include "common.cuh"
+
+namespace ncf {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int64_t find_series(const int64_t *chunk_base, int64_t B, int64_t g) {
+    int64_t lo = 0, hi = B;  // chunk_base[lo] <= g < chunk_base[hi]
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (chunk_base[mid] <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kThreads)
+stats_chunks_kernel(const double *__restrict__ t, const double *__restrict__ x,
+                    const int64_t *__restrict__ offs, const int64_t *__restrict__ chunk_base,
+                    int64_t B, int chunk, ChunkPartial *__restrict__ part) {
+    const int64_t g = blockIdx.x;
+    const int64_t b = find_series(chunk_base, B, g);
+    const int64_t a0 = offs[b], a1 = offs[b + 1];
+    const int64_t start = a0 + (g - chunk_base[b]) * (int64_t)chunk;
+    const int64_t end = min(start + (int64_t)chunk, a1);
+    const double xref = x[a0];
+    double s1 = 0.0, s2 = 0.0;
+    int flags = 0;
+    for (int64_t i = start + threadIdx.x; i < end; i += blockDim.x) {
+        const double xi = x[i], ti = t[i];
+        if (!isfinite(xi) || !isfinite(ti)) flags |= STAT_NONFINITE;
+        if (i > a0 && t[i - 1] > ti) flags |= STAT_UNSORTED;
+        const double d = xi - xref;
+        s1 += d;
+        s2 = fma(d, d, s2);
+    }
+    __shared__ double sh1[kThreads / 32], sh2[kThreads / 32];
+    __shared__ int shf[kThreads / 32];
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    flags = __reduce_or_sync(0xffffffffu, flags);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sh1[w] = s1; sh2[w] = s2; shf[w] = flags; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, c = 0.0;
+        int f = 0;
+        for (int q = 0; q < kThreads / 32; ++q) { a += sh1[q]; c += sh2[q]; f |= shf[q]; }
+        part[g] = ChunkPartial{a, c, f, 0};
+    }
+}
+
+__global__ void stats_finish_kernel(const double *__restrict__ t, const double *__restrict__ x,
+                                    const int64_t *__restrict__ offs,
+                                    const int64_t *__restrict__ chunk_base, int64_t B,
+                                    const ChunkPartial *__restrict__ part,
+                                    SeriesStats *__restrict__ stats) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double s1 = 0.0, s2 = 0.0;
+    int flags = 0;
+    for (int64_t g = chunk_base[b]; g < chunk_base[b + 1]; ++g) {
+        s1 += part[g].s1;
+        s2 += part[g].s2;
+        flags |= part[g].flags;
+    }
+    const int64_t a0 = offs[b], a1 = offs[b + 1];
+    const double n = (double)(a1 - a0);
+    const double m1 = s1 / n;
+    const double var = s2 / n - m1 * m1;
+    SeriesStats st;
+    st.mean = x[a0] + m1;
+    st.n = a1 - a0;
+    if (var > 0.0 && isfinite(var)) {
+        st.inv_std = 1.0 / sqrt(var);
+    } else {
+        st.inv_std = 0.0;
+        flags |= STAT_DEGENERATE;
+    }
+    st.t_first = t[a0];
+    st.t_last = t[a1 - 1];
+    st.flags = flags;
+    st.pad = 0;
+    stats[b] = st;
+}
+
+constexpr int kItems = 16;  // elements per thread in the keys/prefix kernels
+
+__global__ void __launch_bounds__(kThreads)
+keys_chunks_kernel(const double *__restrict__ t, const double *__restrict__ x,
+                   const int64_t *__restrict__ offs, const int64_t *__restrict__ chunk_base,
+                   int64_t B, int chunk, const SeriesStats *__restrict__ stats, FixedScales fs,
+                   int64_t *__restrict__ Tk, int64_t *__restrict__ Xq,
+                   unsigned long long *__restrict__ chunk_sums) {
+    const int64_t g = blockIdx.x;
+    const int64_t b = find_series(chunk_base, B, g);
+    const int64_t a0 = offs[b], a1 = offs[b + 1];
+    const int64_t start = a0 + (g - chunk_base[b]) * (int64_t)chunk;
+    const int64_t end = min(start + (int64_t)chunk, a1);
+    const double mean = stats[b].mean, inv = stats[b].inv_std;
+    unsigned long long acc = 0;
+    for (int64_t i = start + threadIdx.x; i < end; i += blockDim.x) {
+        Tk[i] = __double2ll_rd(t[i] * fs.tscale);
+        const long long q = __double2ll_rn((x[i] - mean) * inv * fs.vscale);
+        Xq[i] = q;
+        acc += (unsigned long long)q;
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ unsigned long long sh[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        for (int q = 0; q < kThreads / 32; ++q) s += sh[q];
+        chunk_sums[g] = s;
+    }
+}
+
+// Exclusive scan of the chunk sums in place (single CTA, wrap-around int64).
+__global__ void __launch_bounds__(1024)
+scan_chunk_sums_kernel(unsigned long long *__restrict__ v, int64_t n,
+                       unsigned long long *__restrict__ total) {
+    const int tid = threadIdx.x;
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t a = min((int64_t)tid * per, n), e = min(a + per, n);
+    unsigned long long s = 0;
+    for (int64_t i = a; i < e; ++i) s += v[i];
+    __shared__ unsigned long long sh[1024];
+    sh[tid] = s;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        unsigned long long add = tid >= o ? sh[tid - o] : 0ull;
+        __syncthreads();
+        sh[tid] += add;
+        __syncthreads();
+    }
+    unsigned long long run = sh[tid] - s;  // exclusive prefix of this thread's segment
+    for (int64_t i = a; i < e; ++i) {
+        unsigned long long c = v[i];
+        v[i] = run;
+        run += c;
+    }
+    if (tid == (int)blockDim.x - 1) *total = sh[tid];
+}
+
+// Per chunk: P[i] = chunk prefix + exclusive scan of Xq inside the chunk.
+__global__ void __launch_bounds__(kThreads)
+prefix_apply_kernel(const int64_t *__restrict__ offs, const int64_t *__restrict__ chunk_base,
+                    int64_t B, int chunk, const int64_t *__restrict__ Xq,
+                    const unsigned long long *__restrict__ chunk_pref,
+                    const unsigned long long *__restrict__ total, int64_t n_total,
+                    int64_t *__restrict__ P) {
+    const int64_t g = blockIdx.x;
+    const int64_t b = find_series(chunk_base, B, g);
+    const int64_t a0 = offs[b], a1 = offs[b + 1];
+    const int64_t start = a0 + (g - chunk_base[b]) * (int64_t)chunk;
+    const int64_t end = min(start + (int64_t)chunk, a1);
+    const int64_t my0 = start + (int64_t)threadIdx.x * kItems;
+    unsigned long long loc[kItems];
+    unsigned long long s = 0;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+        const int64_t i = my0 + q;
+        loc[q] = (i < end) ? (unsigned long long)Xq[i] : 0ull;
+        s += loc[q];
+    }
+    // block exclusive scan of the per-thread sums
+    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long inc = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (l >= o) inc += u;
+    }
+    __shared__ unsigned long long wsum[kThreads / 32];
+    if (l == 31) wsum[w] = inc;
+    __syncthreads();
+    unsigned long long wpre = 0;
+    for (int q = 0; q < w; ++q) wpre += wsum[q];
+    unsigned long long run = chunk_pref[g] + wpre + inc - s;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+        const int64_t i = my0 + q;
+        if (i < end) P[i] = (int64_t)run;
+        run += loc[q];
+    }
+    if (g == (int64_t)gridDim.x - 1 && threadIdx.x == 0) P[n_total] = (int64_t)*total;
+}
+
+}  // namespace
+
+void launch_stats_chunks(const double *t, const double *x, const int64_t *offs,
+                         const int64_t *chunk_base, int64_t B, int64_t n_chunks, int chunk,
+                         ChunkPartial *part, cudaStream_t st) {
+    NCF_COUNT_LAUNCH();
+    stats_chunks_kernel<<<(unsigned)n_chunks, kThreads, 0, st>>>(t, x, offs, chunk_base, B, chunk, part);
+}
+
+void launch_stats_finish(const double *t, const double *x, const int64_t *offs,
+                         const int64_t *chunk_base, int64_t B, const ChunkPartial *part,
+                         SeriesStats *stats, cudaStream_t st) {
+    NCF_COUNT_LAUNCH();
+    stats_finish_kernel<<<(unsigned)((B + 127) / 128), 128, 0, st>>>(t, x, offs, chunk_base, B, part, stats);
+}
+
+void launch_keys_prefix(const double *t, const double *x, const int64_t *offs,
+                        const int64_t *chunk_base, int64_t B, int64_t n_chunks, int chunk,
+                        const SeriesStats *stats, FixedScales fs, int64_t *Tk, int64_t *Xq,
+                        int64_t *P, int64_t *chunk_sums, int64_t n_total, cudaStream_t st) {
+    // chunk must equal kThreads * kItems (= kPrepChunk) for prefix_apply_kernel
+    auto *cs = reinterpret_cast<unsigned long long *>(chunk_sums);
+    NCF_COUNT_LAUNCH();
+    keys_chunks_kernel<<<(unsigned)n_chunks, kThreads, 0, st>>>(t, x, offs, chunk_base, B, chunk,
+                                                                 stats, fs, Tk, Xq, cs);
+    NCF_COUNT_LAUNCH();
+    scan_chunk_sums_kernel<<<1, 1024, 0, st>>>(cs, n_chunks, cs + n_chunks);
+    NCF_COUNT_LAUNCH();
+    prefix_apply_kernel<<<(unsigned)n_chunks, kThreads, 0, st>>>(offs, chunk_base, B, chunk, Xq, cs,
+                                                                  cs + n_chunks, n_total, P);
+}
+
+}  // namespace ncf
