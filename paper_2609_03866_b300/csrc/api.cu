@@ -428,8 +428,11 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
     sa.lag0 = lag0;
     sa.lags = lags;
     sa.h_lags = h_lags;
-    sa.x = {X.t, X.v, X.d_offs, X.d_stats, X.offs.data(), X.stats.data(), X.n_total, X.n_max};
-    if (!acf) sa.y = {Y.t, Y.v, Y.d_offs, Y.d_stats, Y.offs.data(), Y.stats.data(), Y.n_total, Y.n_max};
+    sa.x = {X.t, X.v, X.d_offs, X.d_stats, X.offs.data(), X.stats.data(), X.n_total, X.n_max,
+            X.d_chunk_base, X.n_chunks};
+    if (!acf)
+        sa.y = {Y.t, Y.v, Y.d_offs, Y.d_stats, Y.offs.data(), Y.stats.data(), Y.n_total, Y.n_max,
+                Y.d_chunk_base, Y.n_chunks};
     sa.c_out = c_out;
     sa.b_out = b_out;
     sa.count_out = count_out;

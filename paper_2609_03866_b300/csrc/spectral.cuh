@@ -14,6 +14,8 @@ struct SpecSide {
     const int64_t *h_offs = nullptr;          // host CSR offsets [B+1]
     const SeriesStats *h_stats = nullptr;     // host copy of the statistics
     int64_t n_total = 0, n_max = 0;
+    const int64_t *d_chunk_base = nullptr;    // device chunk table of the statistics pass
+    int64_t n_chunks = 0;
 };
 
 struct SpectralArgs {
