@@ -117,6 +117,30 @@ NCF_API const char *ncf_status_string(ncf_status s);
 NCF_API uint64_t ncf_launch_count(const ncf_ctx *ctx);
 
 /*
+ * Geometry of the most recent spectral call on this context: the common
+ * period L of the Fourier series, the number of modes kept (m = 0 .. modes-1),
+ * the oversampled grid size n_f, the spreading kernel width (cells), and the
+ * batch size B and lag count K it served.  All zero before any spectral call.
+ */
+typedef struct {
+    double period;
+    int64_t modes, grid, width, B, K;
+} ncf_plan_info;
+NCF_API ncf_status ncf_last_plan(const ncf_ctx *ctx, ncf_plan_info *out);
+
+/*
+ * Kernel profiler.  While enabled, every kernel the context launches is
+ * bracketed by two CUDA events recorded on its launch stream.
+ * ncf_profile_report synchronises on the recorded events, folds them into
+ * per-kernel totals and writes lines "name launches total_ms\n" into buf
+ * (NUL-terminated, truncated to len); it returns the full text length, or -1
+ * for a NULL context.  ncf_profile_reset clears the totals.
+ */
+NCF_API ncf_status ncf_profile_enable(ncf_ctx *ctx, int on);
+NCF_API int64_t ncf_profile_report(ncf_ctx *ctx, char *buf, size_t len);
+NCF_API void ncf_profile_reset(ncf_ctx *ctx);
+
+/*
  * One ACF (s == NULL and y == NULL) or CCF (x at t with y at s).
  *   t, x   [nx]  device FP64, t non-decreasing, nx >= 2
  *   s, y   [ny]  device FP64, s non-decreasing, ny >= 2 (ignored for the ACF)

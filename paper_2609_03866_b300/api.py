@@ -37,6 +37,11 @@ class ncf_options(ctypes.Structure):
                 ("tol", ctypes.c_double)]
 
 
+class ncf_plan_info(ctypes.Structure):
+    _fields_ = [("period", ctypes.c_double), ("modes", ctypes.c_int64), ("grid", ctypes.c_int64),
+                ("width", ctypes.c_int64), ("B", ctypes.c_int64), ("K", ctypes.c_int64)]
+
+
 class NcfError(RuntimeError):
     def __init__(self, status: int, name: str, message: str):
         super().__init__(f"{name}: {message}")
@@ -72,6 +77,14 @@ def lib():
             L.ncf_status_string.restype = ctypes.c_char_p
             L.ncf_launch_count.argtypes = [vp]
             L.ncf_launch_count.restype = ctypes.c_uint64
+            L.ncf_last_plan.argtypes = [vp, ctypes.POINTER(ncf_plan_info)]
+            L.ncf_last_plan.restype = ctypes.c_int
+            L.ncf_profile_enable.argtypes = [vp, ctypes.c_int]
+            L.ncf_profile_enable.restype = ctypes.c_int
+            L.ncf_profile_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+            L.ncf_profile_report.restype = ctypes.c_int64
+            L.ncf_profile_reset.argtypes = [vp]
+            L.ncf_profile_reset.restype = None
             L.ncf_corr.argtypes = [vp, dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int64, dp, ctypes.c_int64,
                                    ctypes.POINTER(ncf_options), dp, dp, i64p, vp]
             L.ncf_corr.restype = ctypes.c_int
@@ -130,6 +143,31 @@ class Context:
     @property
     def launches(self) -> int:
         return int(lib().ncf_launch_count(self._h))
+
+    def last_plan(self) -> dict:
+        """Geometry of the most recent spectral call (period, modes, grid, width, B, K)."""
+        info = ncf_plan_info()
+        self.check(lib().ncf_last_plan(self._h, ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in ncf_plan_info._fields_}
+
+    def profile(self, on: bool = True):
+        """Bracket every kernel launch of this context with CUDA events."""
+        self.check(lib().ncf_profile_enable(self._h, int(on)))
+
+    def profile_report(self) -> dict:
+        """{kernel name: (launches, total ms)} accumulated since the last reset
+        (synchronises on the recorded events)."""
+        n = lib().ncf_profile_report(self._h, None, 0)
+        buf = ctypes.create_string_buffer(int(n) + 1)
+        lib().ncf_profile_report(self._h, buf, len(buf))
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, cnt, ms = line.split()
+            out[name] = (int(cnt), float(ms))
+        return out
+
+    def profile_reset(self):
+        lib().ncf_profile_reset(self._h)
 
     def close(self):
         if self._h:

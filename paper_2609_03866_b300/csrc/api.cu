@@ -20,7 +20,16 @@
 #include "common.cuh"
 #include "spectral.cuh"
 
-thread_local uint64_t *ncf_tls_launch_counter = nullptr;
+#include <map>
+
+// Per-context kernel profiler: CUDA events around every launch while enabled.
+struct NcfProfiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;                 // begin/end pairs, reused after a report
+    size_t next = 0;
+    std::vector<std::pair<const char *, size_t>> recs;  // kernel name, index of its begin event
+    std::map<std::string, std::pair<int64_t, double>> totals;  // name -> (launches, ms)
+};
 
 struct ncf_ctx {
     int device = 0;
@@ -35,15 +44,43 @@ struct ncf_ctx {
     size_t hbuf_cap = 0;
     uint64_t launches = 0;
     cudaEvent_t staged = nullptr;  // recorded after staging copies issued past the read-back sync
+    NcfProfiler prof;
+    ncf_plan_info plan{0.0, 0, 0, 0, 0, 0};
     std::string err;
 };
+
+static thread_local ncf_ctx *tls_ctx = nullptr;
+
+namespace ncf {
+LaunchMark::LaunchMark(const char *name, cudaStream_t s) : slot(-1), st(s) {
+    ncf_ctx *c = tls_ctx;
+    if (!c) return;
+    ++c->launches;
+    NcfProfiler &p = c->prof;
+    if (!p.on) return;
+    if (p.next + 2 > p.pool.size()) {
+        for (int q = 0; q < 64; ++q) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return;
+            p.pool.push_back(e);
+        }
+    }
+    slot = (int)p.next;
+    p.next += 2;
+    cudaEventRecord(p.pool[slot], st);
+    p.recs.emplace_back(name, (size_t)slot);
+}
+LaunchMark::~LaunchMark() {
+    if (slot >= 0 && tls_ctx) cudaEventRecord(tls_ctx->prof.pool[slot + 1], st);
+}
+}  // namespace ncf
 
 namespace ncf {
 namespace {
 
 struct LaunchScope {
-    explicit LaunchScope(ncf_ctx *c) { ncf_tls_launch_counter = &c->launches; }
-    ~LaunchScope() { ncf_tls_launch_counter = nullptr; }
+    explicit LaunchScope(ncf_ctx *c) { tls_ctx = c; }
+    ~LaunchScope() { tls_ctx = nullptr; }
 };
 
 ncf_status fail(ncf_ctx *ctx, ncf_status s, const char *fmt, ...) {
@@ -438,8 +475,10 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
     sa.count_out = count_out;
     sa.sm_count = ctx->sm_count;
     std::string msg;
-    rc = run_spectral(sa, &ctx->ws2, &ctx->ws2_cap, &ctx->pinned, &ctx->pinned_cap, st, &msg);
+    SpectralGeometry geom{0.0, 0, 0, 0};
+    rc = run_spectral(sa, &ctx->ws2, &ctx->ws2_cap, &ctx->pinned, &ctx->pinned_cap, st, &msg, &geom);
     if (rc) return fail(ctx, rc, "%s", msg.c_str());
+    ctx->plan = ncf_plan_info{geom.L, geom.M, geom.nf, geom.W, B, K};
     NCF_CUDA(cudaEventRecord(ctx->staged, st));
     NCF_CUDA(cudaGetLastError());
     return NCF_OK;
@@ -508,7 +547,57 @@ void ncf_destroy(ncf_ctx *ctx) {
     if (ctx->hbuf) cudaFree(ctx->hbuf);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->staged) cudaEventDestroy(ctx->staged);
+    for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
     delete ctx;
+}
+
+ncf_status ncf_last_plan(const ncf_ctx *ctx, ncf_plan_info *out) {
+    if (!ctx || !out) return NCF_EINVAL;
+    *out = ctx->plan;
+    return NCF_OK;
+}
+
+ncf_status ncf_profile_enable(ncf_ctx *ctx, int on) {
+    if (!ctx) return NCF_EINVAL;
+    ctx->prof.on = on != 0;
+    return NCF_OK;
+}
+
+int64_t ncf_profile_report(ncf_ctx *ctx, char *buf, size_t len) {
+    if (!ctx) return -1;
+    NcfProfiler &p = ctx->prof;
+    for (auto &r : p.recs) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(p.pool[r.second + 1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, p.pool[r.second], p.pool[r.second + 1]) == cudaSuccess) {
+            auto &t = p.totals[r.first];
+            t.first += 1;
+            t.second += ms;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    p.recs.clear();
+    p.next = 0;
+    std::string out;
+    char line[256];
+    for (auto &kv : p.totals) {
+        snprintf(line, sizeof line, "%s %lld %.6f\n", kv.first.c_str(), (long long)kv.second.first,
+                 kv.second.second);
+        out += line;
+    }
+    if (buf && len) {
+        const size_t n = std::min(len - 1, out.size());
+        std::memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    return (int64_t)out.size();
+}
+
+void ncf_profile_reset(ncf_ctx *ctx) {
+    if (!ctx) return;
+    ncf_profile_report(ctx, nullptr, 0);
+    ctx->prof.totals.clear();
 }
 
 const char *ncf_last_error(const ncf_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }

@@ -103,6 +103,19 @@ void launch_finish_gauss(const double *num, const double *den, const unsigned lo
 
 }  // namespace ncf
 
-// Launch bookkeeping: every kernel launch in the library goes through this.
-extern thread_local uint64_t *ncf_tls_launch_counter;
-#define NCF_COUNT_LAUNCH() do { if (ncf_tls_launch_counter) ++*ncf_tls_launch_counter; } while (0)
+// Launch bookkeeping: every kernel launch in the library goes through
+// NCF_LAUNCH, which counts it and, when the context's profiler is on, brackets
+// it with CUDA events recorded on the launch stream.
+namespace ncf {
+struct LaunchMark {
+    LaunchMark(const char *name, cudaStream_t st);
+    ~LaunchMark();
+    int slot;
+    cudaStream_t st;
+};
+}  // namespace ncf
+#define NCF_LAUNCH(name, st, ...)              \
+    do {                                       \
+        ::ncf::LaunchMark ncf_mark_(name, st); \
+        __VA_ARGS__;                           \
+    } while (0)

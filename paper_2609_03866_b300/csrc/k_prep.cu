@@ -214,15 +214,15 @@ prefix_apply_kernel(const int64_t *__restrict__ offs, const int64_t *__restrict_
 void launch_stats_chunks(const double *t, const double *x, const int64_t *offs,
                          const int64_t *chunk_base, int64_t B, int64_t n_chunks, int chunk,
                          ChunkPartial *part, cudaStream_t st) {
-    NCF_COUNT_LAUNCH();
-    stats_chunks_kernel<<<(unsigned)n_chunks, kThreads, 0, st>>>(t, x, offs, chunk_base, B, chunk, part);
+    NCF_LAUNCH("stats_chunks_kernel", st,
+    stats_chunks_kernel<<<(unsigned)n_chunks, kThreads, 0, st>>>(t, x, offs, chunk_base, B, chunk, part));
 }
 
 void launch_stats_finish(const double *t, const double *x, const int64_t *offs,
                          const int64_t *chunk_base, int64_t B, const ChunkPartial *part,
                          SeriesStats *stats, cudaStream_t st) {
-    NCF_COUNT_LAUNCH();
-    stats_finish_kernel<<<(unsigned)((B + 127) / 128), 128, 0, st>>>(t, x, offs, chunk_base, B, part, stats);
+    NCF_LAUNCH("stats_finish_kernel", st,
+    stats_finish_kernel<<<(unsigned)((B + 127) / 128), 128, 0, st>>>(t, x, offs, chunk_base, B, part, stats));
 }
 
 void launch_keys_prefix(const double *t, const double *x, const int64_t *offs,
@@ -231,14 +231,14 @@ void launch_keys_prefix(const double *t, const double *x, const int64_t *offs,
                         int64_t *P, int64_t *chunk_sums, int64_t n_total, cudaStream_t st) {
     // chunk must equal kThreads * kItems (= kPrepChunk) for prefix_apply_kernel
     auto *cs = reinterpret_cast<unsigned long long *>(chunk_sums);
-    NCF_COUNT_LAUNCH();
+    NCF_LAUNCH("keys_chunks_kernel", st,
     keys_chunks_kernel<<<(unsigned)n_chunks, kThreads, 0, st>>>(t, x, offs, chunk_base, B, chunk,
-                                                                 stats, fs, Tk, Xq, cs);
-    NCF_COUNT_LAUNCH();
-    scan_chunk_sums_kernel<<<1, 1024, 0, st>>>(cs, n_chunks, cs + n_chunks);
-    NCF_COUNT_LAUNCH();
+                                                                 stats, fs, Tk, Xq, cs));
+    NCF_LAUNCH("scan_chunk_sums_kernel", st,
+    scan_chunk_sums_kernel<<<1, 1024, 0, st>>>(cs, n_chunks, cs + n_chunks));
+    NCF_LAUNCH("prefix_apply_kernel", st,
     prefix_apply_kernel<<<(unsigned)n_chunks, kThreads, 0, st>>>(offs, chunk_base, B, chunk, Xq, cs,
-                                                                  cs + n_chunks, n_total, P);
+                                                                  cs + n_chunks, n_total, P));
 }
 
 }  // namespace ncf

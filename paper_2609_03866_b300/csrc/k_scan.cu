@@ -19,6 +19,7 @@
 // and the numerator sum_j Y_j (P[hi] - P[lo]) is accumulated exactly in
 // 128-bit integers from the quantised standardised values.
 #include <cmath>
+#include <cstdint>
 
 #include "common.cuh"
 
@@ -52,7 +53,29 @@ __device__ __forceinline__ void add128(U128 &a, unsigned long long lo, unsigned 
     a.lo = n;
 }
 
-__global__ void __launch_bounds__(kWarps * 32)
+constexpr int kStageCap = 6144;  // staged window keys per CTA (T and P: 96 KB)
+
+// Window keys T and prefix sums P of the CTA's union window are staged in
+// shared memory when they fit; otherwise the same code reads global memory.
+struct KeyView {
+    const int64_t *T, *P;  // indexable by global point index
+};
+
+// Advance p while key(p) < bound (p <= end).  Sorted keys make the count of
+// true predicates among the next four equal to the advance, so the common
+// small step needs no data-dependent branch.
+__device__ __forceinline__ int64_t advance(const int64_t *__restrict__ T, int64_t p, int64_t end,
+                                           int64_t bound) {
+    if (p + 4 <= end) {
+        const int s = (T[p] < bound) + (T[p + 1] < bound) + (T[p + 2] < bound) + (T[p + 3] < bound);
+        p += s;
+        if (s < 4) return p;
+    }
+    while (p < end && T[p] < bound) ++p;
+    return p;
+}
+
+__global__ void __launch_bounds__(kWarps * 32, 2)
 rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
                  const double *__restrict__ tx, const int64_t *__restrict__ offs_x,
                  const int64_t *__restrict__ Sy, const int64_t *__restrict__ Yq,
@@ -60,38 +83,69 @@ rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
                  const double *__restrict__ lags, int64_t K, int eps, double h, int64_t H,
                  double tscale, int64_t eta, unsigned long long *__restrict__ cnt,
                  unsigned long long *__restrict__ num128) {
+    extern __shared__ int64_t smem[];
+    int64_t *sT = smem, *sP = smem + kStageCap;
+    __shared__ int64_t s_lo[kWarps], s_hi[kWarps];
+    __shared__ int64_t s_range[2];
     const ScanTile tile = tiles[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t k = (int64_t)blockIdx.y * kWarps + warp;
-    if (k >= K) return;
-    const double tau = lags[k];
+    const bool active = k < K;
+    const double tau = active ? lags[k] : 0.0;
     const int64_t Tau = __double2ll_rd(tau * tscale);
     const int64_t dl = (eps > 0 ? Tau : -Tau) - H;
     const int64_t du = (eps > 0 ? Tau : -Tau) + H;
     const int64_t xa = offs_x[tile.b], xb = offs_x[tile.b + 1];
+    // union of the windows of this CTA's lags over its outer points
+    if (lane == 0) {
+        s_lo[warp] = active ? Sy[tile.j0] + dl - eta : INT64_MAX;
+        s_hi[warp] = active ? Sy[tile.j1 - 1] + du + eta : INT64_MIN;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t lo_b = INT64_MAX, hi_b = INT64_MIN;
+        for (int w = 0; w < kWarps; ++w) { lo_b = min(lo_b, s_lo[w]); hi_b = max(hi_b, s_hi[w]); }
+        const int64_t ia = lower_bound_key(Tx, xa, xb, lo_b);
+        const int64_t ib = lower_bound_key(Tx, ia, xb, hi_b);  // last index a pointer can read
+        s_range[0] = ia;
+        s_range[1] = ib;
+    }
+    __syncthreads();
+    // Every pointer stays <= ib (the first key >= the largest band edge), and
+    // the four-wide look-ahead of advance() reads at most three keys past it.
+    const int64_t ia = s_range[0], ib = min(s_range[1], xb);
+    const int64_t t_last = min(ib + 3, xb - 1);
+    const bool staged = (t_last - ia + 1 <= kStageCap) && (ib - ia + 1 <= kStageCap + 1);
+    if (staged) {
+        for (int64_t i = threadIdx.x; i <= t_last - ia; i += blockDim.x) sT[i] = Tx[ia + i];
+        for (int64_t i = threadIdx.x; i <= ib - ia; i += blockDim.x) sP[i] = P[ia + i];
+    }
+    __syncthreads();
+    if (!active) return;
+    const int64_t *T = staged ? sT - ia : Tx;
+    const int64_t *PP = staged ? sP - ia : P;
     const int64_t j0 = tile.j0 + (int64_t)lane * kRunJ;
     const int64_t j1 = min(j0 + kRunJ, tile.j1);
     unsigned long long c = 0;
     U128 acc{0ull, 0ull};
     if (j0 < j1) {
-        int64_t lo = lower_bound_key(Tx, xa, xb, Sy[j0] + dl - eta);
-        int64_t hi = -1;
+        int64_t lo = lower_bound_key(T, ia, ib, Sy[j0] + dl - eta);
+        int64_t hi = lower_bound_key(T, lo, ib, Sy[j0] + du - eta);
         for (int64_t j = j0; j < j1; ++j) {
             const int64_t S = Sy[j];
             const int64_t Lh = S + dl, Uh = S + du;
-            while (lo < xb && Tx[lo] < Lh - eta) ++lo;
-            if (lo < xb && Tx[lo] < Lh + eta) {
+            lo = advance(T, lo, xb, Lh - eta);
+            if (lo < xb && T[lo] < Lh + eta) {  // inside the band: decide in FP64
                 const double lb = __dsub_rn(centre(sy[j], tau, eps), h);
-                while (lo < xb && Tx[lo] < Lh + eta && tx[lo] < lb) ++lo;
+                while (lo < xb && T[lo] < Lh + eta && tx[lo] < lb) ++lo;
             }
-            if (hi < lo) hi = lower_bound_key(Tx, lo, xb, Uh - eta);
-            while (hi < xb && Tx[hi] < Uh - eta) ++hi;
-            if (hi < xb && Tx[hi] < Uh + eta) {
+            hi = advance(T, max(hi, lo), xb, Uh - eta);
+            if (hi < xb && T[hi] < Uh + eta) {
                 const double ub = __dadd_rn(centre(sy[j], tau, eps), h);
-                while (hi < xb && Tx[hi] < Uh + eta && tx[hi] <= ub) ++hi;
+                while (hi < xb && T[hi] < Uh + eta && tx[hi] <= ub) ++hi;
             }
             c += (unsigned long long)(hi - lo);
-            const long long w = (long long)((unsigned long long)P[hi] - (unsigned long long)P[lo]);
+            const long long w = (long long)((unsigned long long)PP[hi] - (unsigned long long)PP[lo]);
             const __int128 prod = (__int128)w * (__int128)Yq[j];
             add128(acc, (unsigned long long)prod, (unsigned long long)(prod >> 64));
         }
@@ -241,16 +295,16 @@ int scan_tile_points() { return kTileJ; }
 void launch_lag0_scale_rect(const unsigned long long *cnt_x, const unsigned long long *num_x,
                             const unsigned long long *cnt_y, const unsigned long long *num_y,
                             int64_t B, double inv_v2, double *scale, cudaStream_t st) {
-    NCF_COUNT_LAUNCH();
+    NCF_LAUNCH("lag0_scale_rect_kernel", st,
     lag0_scale_rect_kernel<<<(unsigned)((B + 127) / 128), 128, 0, st>>>(cnt_x, num_x, cnt_y, num_y, B,
-                                                                         inv_v2, scale);
+                                                                         inv_v2, scale));
 }
 
 void launch_lag0_scale_gauss(const double *num_x, const double *den_x, const double *num_y,
                              const double *den_y, int64_t B, double *scale, cudaStream_t st) {
-    NCF_COUNT_LAUNCH();
+    NCF_LAUNCH("lag0_scale_gauss_kernel", st,
     lag0_scale_gauss_kernel<<<(unsigned)((B + 127) / 128), 128, 0, st>>>(num_x, den_x, num_y, den_y, B,
-                                                                          scale);
+                                                                          scale));
 }
 
 void launch_rect_scan(const int64_t *Tx, const int64_t *P, const double *tx, const int64_t *offs_x,
@@ -260,9 +314,15 @@ void launch_rect_scan(const int64_t *Tx, const int64_t *P, const double *tx, con
                       unsigned long long *cnt, unsigned long long *num128, cudaStream_t st) {
     const int64_t H = (int64_t)std::floor(h * fs.tscale);
     dim3 grid((unsigned)n_tiles, (unsigned)((K + kWarps - 1) / kWarps));
-    NCF_COUNT_LAUNCH();
-    rect_scan_kernel<<<grid, kWarps * 32, 0, st>>>(Tx, P, tx, offs_x, Sy, Yq, sy, tiles, lags, K, eps,
-                                                   h, H, fs.tscale, fs.eta, cnt, num128);
+    const size_t smem = (2 * kStageCap + 1) * sizeof(int64_t);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(rect_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
+    NCF_LAUNCH("rect_scan_kernel", st,
+    rect_scan_kernel<<<grid, kWarps * 32, smem, st>>>(Tx, P, tx, offs_x, Sy, Yq, sy, tiles, lags, K, eps,
+                                                   h, H, fs.tscale, fs.eta, cnt, num128));
 }
 
 void launch_gauss_window(const double *tx, const double *x, const int64_t *offs_x,
@@ -271,27 +331,27 @@ void launch_gauss_window(const double *tx, const double *x, const int64_t *offs_
                          const double *lags, int64_t K, int eps, double h, double Rh,
                          double *num, double *den, unsigned long long *cnt, cudaStream_t st) {
     dim3 grid((unsigned)n_tiles, (unsigned)((K + kWarps - 1) / kWarps));
-    NCF_COUNT_LAUNCH();
+    NCF_LAUNCH("gauss_window_kernel", st,
     gauss_window_kernel<<<grid, kWarps * 32, 0, st>>>(tx, x, offs_x, stx, sy, y, sty, tiles, lags, K,
-                                                      eps, h, Rh, num, den, cnt);
+                                                      eps, h, Rh, num, den, cnt));
 }
 
 void launch_finish_rect(const unsigned long long *cnt, const unsigned long long *num128,
                         int64_t B, int64_t K, double inv_v2, const double *scale,
                         double *c, double *b, int64_t *count, cudaStream_t st) {
     const int64_t n = B * K;
-    NCF_COUNT_LAUNCH();
+    NCF_LAUNCH("finish_rect_kernel", st,
     finish_rect_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cnt, num128, B, K, inv_v2, scale,
-                                                                     c, b, count);
+                                                                     c, b, count));
 }
 
 void launch_finish_gauss(const double *num, const double *den, const unsigned long long *cnt,
                          int64_t B, int64_t K, const double *scale, double *c, double *b,
                          int64_t *count, cudaStream_t st) {
     const int64_t n = B * K;
-    NCF_COUNT_LAUNCH();
+    NCF_LAUNCH("finish_gauss_kernel", st,
     finish_gauss_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(num, den, cnt, B, K, scale, c,
-                                                                      b, count);
+                                                                      b, count));
 }
 
 }  // namespace ncf

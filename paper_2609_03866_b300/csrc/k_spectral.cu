@@ -461,31 +461,35 @@ ncf_status run_typed(const SpectralArgs &a, const Plan &p, char *ws, const doubl
     up(d_gx, gx.data(), p.nq * 8);
     up(d_gphi, gphi.data(), p.nq * 8);
 
-    NCF_COUNT_LAUNCH();
+    NCF_LAUNCH("mode_weight_kernel", st,
     mode_weight_kernel<<<(unsigned)((p.Mp + 255) / 256), 256, 0, st>>>(
         d_gx, d_gphi, p.nq, p.M, p.Mp, p.W, p.nf, p.L, a.h, wgt64,
-        std::is_same<R, float>::value ? reinterpret_cast<float *>(wgt) : nullptr);
+        std::is_same<R, float>::value ? reinterpret_cast<float *>(wgt) : nullptr));
     if (std::is_same<R, double>::value)
         cudaMemcpyAsync(wgt, wgt64, p.Mp * 8, cudaMemcpyDeviceToDevice, st);
-    NCF_COUNT_LAUNCH();
-    twiddle_kernel<V><<<(p.nf + 255) / 256, 256, 0, st>>>(tw, p.nf);
+    NCF_LAUNCH("twiddle_kernel", st,
+    twiddle_kernel<V><<<(p.nf + 255) / 256, 256, 0, st>>>(tw, p.nf));
     {
         dim3 grid((unsigned)p.Mp, (unsigned)((p.Kp + 127) / 128));
-        NCF_COUNT_LAUNCH();
-        lag_table_kernel<R><<<grid, 128, 0, st>>>(d_phi, p.Mp, p.Kp, p.K1, ccf, E);
+        NCF_LAUNCH("lag_table_kernel", st,
+        lag_table_kernel<R><<<grid, 128, 0, st>>>(d_phi, p.Mp, p.Kp, p.K1, ccf, E));
     }
 
     // spreading
     const double a_scale = (double)p.nf / p.L;
     auto spread = [&](const SpecSide &sd, V *grid, const int64_t *chunk_base, int64_t n_chunks) {
         cudaMemsetAsync(grid, 0, B * (size_t)p.nf * sizeof(V), st);
-        NCF_COUNT_LAUNCH();
+        constexpr int TILE = sizeof(R) == 4 ? 4096 : 2048;
         if (p.W == 8)
-            spread_kernel<R, 8, (sizeof(R) == 4 ? 4096 : 2048)><<<(unsigned)n_chunks, kSpreadThreads, 0, st>>>(
-                sd.t, sd.v, sd.d_offs, chunk_base, B, sd.d_stats, d_tc, a_scale, p.nf, (R)p.beta, grid);
+            NCF_LAUNCH("spread_kernel", st,
+                       spread_kernel<R, 8, TILE><<<(unsigned)n_chunks, kSpreadThreads, 0, st>>>(
+                           sd.t, sd.v, sd.d_offs, chunk_base, B, sd.d_stats, d_tc, a_scale, p.nf,
+                           (R)p.beta, grid));
         else
-            spread_kernel<R, 16, (sizeof(R) == 4 ? 4096 : 2048)><<<(unsigned)n_chunks, kSpreadThreads, 0, st>>>(
-                sd.t, sd.v, sd.d_offs, chunk_base, B, sd.d_stats, d_tc, a_scale, p.nf, (R)p.beta, grid);
+            NCF_LAUNCH("spread_kernel", st,
+                       spread_kernel<R, 16, TILE><<<(unsigned)n_chunks, kSpreadThreads, 0, st>>>(
+                           sd.t, sd.v, sd.d_offs, chunk_base, B, sd.d_stats, d_tc, a_scale, p.nf,
+                           (R)p.beta, grid));
     };
     spread(a.x, grid_x, a.x.d_chunk_base, a.x.n_chunks);
     if (ccf) spread(a.y, grid_y, a.y.d_chunk_base, a.y.n_chunks);
@@ -499,10 +503,15 @@ ncf_status run_typed(const SpectralArgs &a, const Plan &p, char *ws, const doubl
             const int rad = rp.radix[q];
             const int64_t items = B * (int64_t)(p.nf / rad);
             const unsigned blocks = (unsigned)((items + 255) / 256);
-            NCF_COUNT_LAUNCH();
-            if (rad == 8) fft_pass_kernel<V, 8><<<blocks, 256, 0, st>>>(in, out, p.lg, Ns, tw, B);
-            else if (rad == 4) fft_pass_kernel<V, 4><<<blocks, 256, 0, st>>>(in, out, p.lg, Ns, tw, B);
-            else fft_pass_kernel<V, 2><<<blocks, 256, 0, st>>>(in, out, p.lg, Ns, tw, B);
+            if (rad == 8)
+                NCF_LAUNCH("fft_pass_kernel", st,
+                           fft_pass_kernel<V, 8><<<blocks, 256, 0, st>>>(in, out, p.lg, Ns, tw, B));
+            else if (rad == 4)
+                NCF_LAUNCH("fft_pass_kernel", st,
+                           fft_pass_kernel<V, 4><<<blocks, 256, 0, st>>>(in, out, p.lg, Ns, tw, B));
+            else
+                NCF_LAUNCH("fft_pass_kernel", st,
+                           fft_pass_kernel<V, 2><<<blocks, 256, 0, st>>>(in, out, p.lg, Ns, tw, B));
             Ns *= rad;
             std::swap(in, out);
         }
@@ -520,23 +529,23 @@ ncf_status run_typed(const SpectralArgs &a, const Plan &p, char *ws, const doubl
     if (lag0_ccf) cudaMemsetAsync(lag0, 0, 4 * B * 8, st);
     {
         dim3 grid((unsigned)((p.Mp + 255) / 256), (unsigned)std::min<int64_t>(B, 65535));
-        NCF_COUNT_LAUNCH();
+        NCF_LAUNCH("spectrum_kernel", st,
         spectrum_kernel<R><<<grid, 256, 0, st>>>(Gx, Gy, p.nf, p.M, p.Mp, B, wgt, Anum, Aden,
-                                                 lag0_ccf ? lag0 : nullptr);
+                                                 lag0_ccf ? lag0 : nullptr));
     }
     cudaMemsetAsync(acc_num, 0, B * p.Kp * 8, st);
     cudaMemsetAsync(acc_den, 0, B * p.Kp * 8, st);
     {
         dim3 grid((unsigned)((p.Kp + kBN - 1) / kBN), (unsigned)((B + kBM - 1) / kBM),
                   (unsigned)((p.M2 + kChunk - 1) / kChunk));
-        NCF_COUNT_LAUNCH();
-        contract_kernel<R><<<grid, 256, 0, st>>>(Anum, Aden, E, B, p.M2, p.Kp, acc_num, acc_den);
+        NCF_LAUNCH("contract_kernel", st,
+        contract_kernel<R><<<grid, 256, 0, st>>>(Anum, Aden, E, B, p.M2, p.Kp, acc_num, acc_den));
     }
     {
         const int mode = a.lag0 ? (ccf ? 2 : 1) : 0;
-        NCF_COUNT_LAUNCH();
+        NCF_LAUNCH("finish_spectral_kernel", st,
         finish_spectral_kernel<<<(unsigned)((B * a.K + 255) / 256), 256, 0, st>>>(
-            acc_num, acc_den, B, a.K, p.Kp, mode, lag0, a.c_out, a.b_out, a.count_out);
+            acc_num, acc_den, B, a.K, p.Kp, mode, lag0, a.c_out, a.b_out, a.count_out));
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -561,7 +570,8 @@ size_t workspace_bytes(const Plan &p, int64_t B, bool ccf) {
 }  // namespace
 
 ncf_status run_spectral(const SpectralArgs &a, char **ws, size_t *ws_cap, char **pinned,
-                        size_t *pinned_cap, cudaStream_t st, std::string *msg) {
+                        size_t *pinned_cap, cudaStream_t st, std::string *msg,
+                        SpectralGeometry *geom) {
     const int64_t B = a.B;
     const bool ccf = !a.acf;
     // per-series centre t_c and the common period L (Algorithm 1 with an
@@ -578,6 +588,7 @@ ncf_status run_spectral(const SpectralArgs &a, char **ws, size_t *ws_cap, char *
         max_span = std::max(max_span, hi - lo);
     }
     const Plan p = make_plan(a, max_span);
+    if (geom) *geom = SpectralGeometry{p.L, p.M, p.nf, p.W};
     if (p.lg > 28) {
         *msg = "spectral grid would exceed 2^28 cells (span / h too large); use the windowed path";
         return NCF_EUNSUPPORTED;

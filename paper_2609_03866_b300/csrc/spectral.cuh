@@ -30,9 +30,13 @@ struct SpectralArgs {
     int sm_count = 148;
 };
 
+// Geometry chosen by the last run_spectral call (reported through ncf_last_plan).
+struct SpectralGeometry { double L; int64_t M, nf, W; };
+
 // Runs the spectral path on `st`; grows *ws (device) and *pinned (host) as
 // needed.  Returns NCF_OK or an error with *msg set.
 ncf_status run_spectral(const SpectralArgs &a, char **ws, size_t *ws_cap, char **pinned,
-                        size_t *pinned_cap, cudaStream_t st, std::string *msg);
+                        size_t *pinned_cap, cudaStream_t st, std::string *msg,
+                        SpectralGeometry *geom);
 
 }  // namespace ncf
