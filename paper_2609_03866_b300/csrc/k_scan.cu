@@ -28,7 +28,7 @@ namespace ncf {
 namespace {
 
 constexpr int kWarps = 8;               // lags per CTA
-constexpr int kRunJ = 16;               // consecutive outer points per lane
+constexpr int kRunJ = 32;               // consecutive outer points per lane
 constexpr int kTileJ = 32 * kRunJ;      // outer points per tile
 
 __device__ __forceinline__ int64_t lower_bound_key(const int64_t *__restrict__ T, int64_t lo,
@@ -55,21 +55,28 @@ __device__ __forceinline__ void add128(U128 &a, unsigned long long lo, unsigned 
 
 constexpr int kStageCap = 6144;  // staged window keys per CTA (T and P: 96 KB)
 
-// Window keys T and prefix sums P of the CTA's union window are staged in
-// shared memory when they fit; otherwise the same code reads global memory.
-struct KeyView {
-    const int64_t *T, *P;  // indexable by global point index
-};
-
-// Advance p while key(p) < bound (p <= end).  Sorted keys make the count of
+// Advance p while key(p) < bound; reads only indices < end, and the caller
+// guarantees the answer is <= end.  Sorted keys make the count of
 // true predicates among the next four equal to the advance, so the common
-// small step needs no data-dependent branch.
+// small step needs no data-dependent branch; a long jump (an outer point
+// that crosses an observing gap moves its window by hundreds of points)
+// gallops: doubling steps, then bisection, O(log jump) loads.
 __device__ __forceinline__ int64_t advance(const int64_t *__restrict__ T, int64_t p, int64_t end,
                                            int64_t bound) {
     if (p + 4 <= end) {
         const int s = (T[p] < bound) + (T[p + 1] < bound) + (T[p + 2] < bound) + (T[p + 3] < bound);
         p += s;
         if (s < 4) return p;
+        // T[p - 1] < bound: gallop
+        int64_t step = 4;
+        int64_t lo = p;          // invariant: T[lo - 1] < bound
+        int64_t hi = p + step;   // candidate upper end
+        while (hi < end && T[hi] < bound) {
+            lo = hi + 1;
+            step <<= 1;
+            hi = lo + step;
+        }
+        return lower_bound_key(T, lo, min(hi, end), bound);
     }
     while (p < end && T[p] < bound) ++p;
     return p;
@@ -122,6 +129,8 @@ rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
     }
     __syncthreads();
     if (!active) return;
+    // every search answer is <= ib, so no read needs an index >= lim
+    const int64_t lim = min(ib + 1, xb);
     const int64_t *T = staged ? sT - ia : Tx;
     const int64_t *PP = staged ? sP - ia : P;
     const int64_t j0 = tile.j0 + (int64_t)lane * kRunJ;
@@ -134,12 +143,12 @@ rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
         for (int64_t j = j0; j < j1; ++j) {
             const int64_t S = Sy[j];
             const int64_t Lh = S + dl, Uh = S + du;
-            lo = advance(T, lo, xb, Lh - eta);
+            lo = advance(T, lo, lim, Lh - eta);
             if (lo < xb && T[lo] < Lh + eta) {  // inside the band: decide in FP64
                 const double lb = __dsub_rn(centre(sy[j], tau, eps), h);
                 while (lo < xb && T[lo] < Lh + eta && tx[lo] < lb) ++lo;
             }
-            hi = advance(T, max(hi, lo), xb, Uh - eta);
+            hi = advance(T, max(hi, lo), lim, Uh - eta);
             if (hi < xb && T[hi] < Uh + eta) {
                 const double ub = __dadd_rn(centre(sy[j], tau, eps), h);
                 while (hi < xb && T[hi] < Uh + eta && tx[hi] <= ub) ++hi;
