@@ -322,10 +322,11 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
                        reinterpret_cast<SeriesStats *>(down + al(B * sizeof(SeriesStats))) + B);
     if ((rc = check_stats(ctx, X, B, acf ? "x" : "x"))) return rc;
     if (!acf && (rc = check_stats(ctx, Y, B, "y"))) return rc;
+    const std::vector<double> lagv(h_lags, h_lags + K);  // the staging buffer is reused below
     double max_tau = 0.0;
     for (int64_t k = 0; k < K; ++k) {
-        if (!std::isfinite(h_lags[k])) return fail(ctx, NCF_ENONFINITE, "lag %lld is not finite", (long long)k);
-        max_tau = std::max(max_tau, std::fabs(h_lags[k]));
+        if (!std::isfinite(lagv[k])) return fail(ctx, NCF_ENONFINITE, "lag %lld is not finite", (long long)k);
+        max_tau = std::max(max_tau, std::fabs(lagv[k]));
     }
     double t_abs = 0.0;
     for (int64_t b = 0; b < B; ++b) {
@@ -340,9 +341,23 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
         auto key_bytes = [&](const Side &sd) {
             return al(sd.n_total * 8) * 2 + al((sd.n_total + 1) * 8) + al((sd.n_chunks + 1) * 8);
         };
-        size_t need2 = key_bytes(X) + (acf ? 0 : key_bytes(Y)) + al(B * K * 8) * 3 + al(B * 8) * 8 + 256;
-        if (lag0) need2 += al(X.n_total / tileJ * sizeof(ScanTile) + B * sizeof(ScanTile) + 256);
+        const int rtile = rect_tile_points();
+        auto ntiles = [&](const std::vector<int64_t> &o) {
+            int64_t n = 0;
+            for (int64_t b = 0; b < B; ++b) n += (o[b + 1] - o[b] + rtile - 1) / rtile;
+            return n;
+        };
+        // independent device and staging regions for the main scan and the two lag-0 scans
+        const size_t rw_main = rect_workspace_bytes(ntiles(O.offs), K);
+        const size_t rw_x = lag0 ? rect_workspace_bytes(ntiles(X.offs), 1) : 0;
+        const size_t rw_y = (lag0 && !acf) ? rect_workspace_bytes(ntiles(Y.offs), 1) : 0;
+        const size_t rs_main = rect_staging_bytes(ntiles(O.offs), K);
+        const size_t rs_x = lag0 ? rect_staging_bytes(ntiles(X.offs), 1) : 0;
+        const size_t rs_y = (lag0 && !acf) ? rect_staging_bytes(ntiles(Y.offs), 1) : 0;
+        size_t need2 = key_bytes(X) + (acf ? 0 : key_bytes(Y)) + al(B * K * 8) * 3 + al(B * 8) * 8 + 1024 +
+                       rw_main + rw_x + rw_y;
         if ((rc = grow(ctx, &ctx->ws2, &ctx->ws2_cap, need2, st))) return rc;
+        if ((rc = grow_pinned(ctx, rs_main + rs_x + rs_y, st))) return rc;
         Arena a2{ctx->ws2, ctx->ws2_cap, 0};
         struct Keys { int64_t *T, *Xq, *P, *cs; };
         auto keys = [&](Side &sd) {
@@ -356,45 +371,42 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
         Keys ky = acf ? kx : keys(Y);
         auto *cnt = a2.take<unsigned long long>(B * K);
         auto *num = a2.take<unsigned long long>(2 * B * K);
-        auto *zero_lag = a2.take<double>(1);
         auto *cnt0 = a2.take<unsigned long long>(2 * B);
         auto *num0 = a2.take<unsigned long long>(4 * B);
         auto *scale = a2.take<double>(B);
-        if (!kx.cs || !ky.cs || !scale) return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
+        char *rws_main = a2.take<char>(rw_main);
+        char *rws_x = lag0 ? a2.take<char>(rw_x) : nullptr;
+        char *rws_y = (lag0 && !acf) ? a2.take<char>(rw_y) : nullptr;
+        if (!kx.cs || !ky.cs || !scale || !rws_main || (lag0 && !rws_x) || (lag0 && !acf && !rws_y))
+            return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
         NCF_CUDA(cudaMemsetAsync(cnt, 0, B * K * 8, st));
         NCF_CUDA(cudaMemsetAsync(num, 0, 2 * B * K * 8, st));
         const int eps = acf ? +1 : -1;
-        launch_rect_scan(kx.T, kx.P, X.t, X.d_offs, ky.T, ky.Xq, O.t, d_tiles, n_tiles, lags, K, eps,
-                         opt->h, fs, cnt, num, st);
+        std::string msg;
+        RectArgs ra{kx.T, kx.P, X.t, X.d_offs, ky.T, ky.Xq, O.t, &O.offs, B, K, lagv.data(), eps,
+                    opt->h, fs, cnt, num};
+        if ((rc = run_rect_scan(ra, rws_main, rw_main, ctx->pinned, rs_main, st, &msg)))
+            return fail(ctx, rc, "%s", msg.c_str());
         const double inv_v2 = std::ldexp(1.0, -2 * fs.p);
         if (lag0) {
             // ACF of each side at lag 0 (Algorithms 4 and 10): scale = c_xx(0) or sqrt(c_xx(0) c_yy(0))
-            NCF_CUDA(cudaMemsetAsync(zero_lag, 0, 8, st));
+            static const double zero = 0.0;
             NCF_CUDA(cudaMemsetAsync(cnt0, 0, 2 * B * 8, st));
             NCF_CUDA(cudaMemsetAsync(num0, 0, 4 * B * 8, st));
-            // tiles over the x side (for a CCF the main tiles cover y)
-            ScanTile *tx_tiles = d_tiles;
-            int64_t ntx = n_tiles;
+            RectArgs rx{kx.T, kx.P, X.t, X.d_offs, kx.T, kx.Xq, X.t, &X.offs, B, 1, &zero, +1, opt->h, fs,
+                        cnt0, num0};
+            if ((rc = run_rect_scan(rx, rws_x, rw_x, ctx->pinned + rs_main, rs_x, st, &msg)))
+                return fail(ctx, rc, "%s", msg.c_str());
             if (!acf) {
-                std::vector<ScanTile> tt = make_tiles(X.offs, B, tileJ);
-                ntx = (int64_t)tt.size();
-                tx_tiles = a2.take<ScanTile>(ntx);
-                if (!tx_tiles) return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
-                // staging after the read-back region is free now (stream synchronised above)
-                if ((rc = grow_pinned(ctx, ntx * sizeof(ScanTile), st))) return rc;
-                std::memcpy(ctx->pinned, tt.data(), ntx * sizeof(ScanTile));
-                NCF_CUDA(cudaMemcpyAsync(tx_tiles, ctx->pinned, ntx * sizeof(ScanTile),
-                                         cudaMemcpyHostToDevice, st));
-                NCF_CUDA(cudaEventRecord(ctx->staged, st));
+                RectArgs ry{ky.T, ky.P, Y.t, Y.d_offs, ky.T, ky.Xq, Y.t, &Y.offs, B, 1, &zero, +1, opt->h,
+                            fs, cnt0 + B, num0 + 2 * B};
+                if ((rc = run_rect_scan(ry, rws_y, rw_y, ctx->pinned + rs_main + rs_x, rs_y, st, &msg)))
+                    return fail(ctx, rc, "%s", msg.c_str());
             }
-            launch_rect_scan(kx.T, kx.P, X.t, X.d_offs, kx.T, kx.Xq, X.t, tx_tiles, ntx, zero_lag, 1,
-                             +1, opt->h, fs, cnt0, num0, st);
-            if (!acf)
-                launch_rect_scan(ky.T, ky.P, Y.t, Y.d_offs, ky.T, ky.Xq, Y.t, d_tiles, n_tiles, zero_lag,
-                                 1, +1, opt->h, fs, cnt0 + B, num0 + 2 * B, st);
             launch_lag0_scale_rect(cnt0, num0, acf ? nullptr : cnt0 + B, acf ? nullptr : num0 + 2 * B,
                                    B, inv_v2, scale, st);
         }
+        NCF_CUDA(cudaEventRecord(ctx->staged, st));
         launch_finish_rect(cnt, num, B, K, inv_v2, lag0 ? scale : nullptr, c_out, b_out, count_out, st);
         NCF_CUDA(cudaGetLastError());
         return NCF_OK;
@@ -464,7 +476,7 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
     sa.max_tau = max_tau;
     sa.lag0 = lag0;
     sa.lags = lags;
-    sa.h_lags = h_lags;
+    sa.h_lags = lagv.data();
     sa.x = {X.t, X.v, X.d_offs, X.d_stats, X.offs.data(), X.stats.data(), X.n_total, X.n_max,
             X.d_chunk_base, X.n_chunks};
     if (!acf)

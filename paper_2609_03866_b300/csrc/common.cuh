@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
+#include <string>
+#include <vector>
 
 #include "ncf.h"
 
@@ -72,12 +74,29 @@ void launch_keys_prefix(const double *t, const double *x, const int64_t *offs,
 
 // ---- real-space scans (k_scan.cu) ----
 struct ScanTile { int32_t b; int32_t pad; int64_t j0, j1; };
-// Exact rectangle pair counts and fixed-point numerators (Algorithms 6 and 8).
-void launch_rect_scan(const int64_t *Tx, const int64_t *P, const double *tx, const int64_t *offs_x,
-                      const int64_t *Sy, const int64_t *Yq, const double *sy,
-                      const ScanTile *tiles, int64_t n_tiles, const double *lags, int64_t K,
-                      int eps, double h, FixedScales fs,
-                      unsigned long long *cnt, unsigned long long *num128, cudaStream_t st);
+// Exact rectangle pair counts and fixed-point numerators (Algorithms 6 and 8),
+// k_rect.cu.  Window side x (keys Tx, prefix sums P, times tx), outer side
+// (keys Sy, quantised values Yq, times sy); cnt / num128 are indexed
+// [series][lag] in the caller's lag order and must be zeroed.
+struct RectArgs {
+    const int64_t *Tx, *P;
+    const double *tx;
+    const int64_t *offs_x;
+    const int64_t *Sy, *Yq;
+    const double *sy;
+    const std::vector<int64_t> *outer_offs;  // host CSR offsets of the outer side
+    int64_t B, K;
+    const double *h_lags;                    // host copy of the lags
+    int eps;
+    double h;
+    FixedScales fs;
+    unsigned long long *cnt, *num128;
+};
+int rect_tile_points();
+size_t rect_workspace_bytes(int64_t n_tiles, int64_t K);
+size_t rect_staging_bytes(int64_t n_tiles, int64_t K);
+ncf_status run_rect_scan(const RectArgs &a, char *ws, size_t ws_cap, char *pinned, size_t pinned_cap,
+                         cudaStream_t st, std::string *msg);
 // Gaussian windowed FP64 scan (Algorithms 5 and 7 with window R h).
 void launch_gauss_window(const double *tx, const double *x, const int64_t *offs_x,
                          const SeriesStats *stx, const double *sy, const double *y,
