@@ -184,6 +184,33 @@ NCF_API ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, cons
                                const double *lags, int64_t K, const ncf_options *opt,
                                double *c_out, double *b_out, int64_t *count_out, void *stream);
 
+/*
+ * Allocation-free variant of the Gaussian windowed estimator (no counterpart
+ * in the paper; it exists for callers that must not allocate device memory
+ * while running, such as real-time or embedded pipelines with a fixed memory
+ * plan, or plug-ins inside a framework whose allocator owns the device).
+ *
+ * Same arguments and results as ncf_corr with kernel = NCF_GAUSSIAN, path =
+ * NCF_PATH_WINDOWED, precision = NCF_FP64, norm = NCF_NORM_NONE (window
+ * [c - R h, c + R h), R = trunc_R, 0 selects 8), for ONE series (s, y NULL:
+ * ACF) or one pair (CCF); all arrays are device pointers, b_out may be NULL.
+ * No context is needed and nothing is allocated: the scratch is a fixed
+ * 64 KiB array compiled into the library, present on every GPU that loads
+ * the library until the process exits.
+ *   Limits: nx, ny <= 262144 points, K <= 1024 lags; larger inputs return
+ *   NCF_EUNSUPPORTED (use ncf_corr).  Other errors as for ncf_corr
+ *   (NCF_EINVAL, NCF_ENOTSORTED, NCF_ENONFINITE, NCF_EDEGENERATE, NCF_ECUDA).
+ *   The first call on a device looks up the scratch array's device address
+ *   (cudaGetSymbolAddress) with that device current; make it before any
+ *   stream capture.  The call synchronises `stream` once (input validation).
+ *   All calls share the one scratch array: calls that may overlap on the GPU
+ *   (other streams or host threads) race and must be serialised by the caller.
+ */
+NCF_API ncf_status ncf_corr_window_static(const double *t, const double *x, int64_t nx,
+                                          const double *s, const double *y, int64_t ny,
+                                          const double *lags, int64_t K, double h, double trunc_R,
+                                          double *c_out, double *b_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif
