@@ -145,6 +145,7 @@ struct Side {
     int64_t n_total = 0, n_chunks = 0, n_max = 0;
     // device
     int64_t *d_offs = nullptr, *d_chunk_base = nullptr;
+    int32_t *d_cs = nullptr;  // series of each chunk
     ChunkPartial *d_part = nullptr;
     SeriesStats *d_stats = nullptr;
     std::vector<SeriesStats> stats;
@@ -265,7 +266,8 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
 
     // ---- pre-statistics workspace ----
     auto side_bytes = [&](const Side &sd) {
-        return al((B + 1) * 8) * 2 + al(sd.n_chunks * sizeof(ChunkPartial)) + al(B * sizeof(SeriesStats));
+        return al((B + 1) * 8) * 2 + al(sd.n_chunks * sizeof(ChunkPartial)) + al(B * sizeof(SeriesStats)) +
+               al(sd.n_chunks * 4);
     };
     size_t need = side_bytes(X) + (acf ? 0 : side_bytes(Y)) + al(n_tiles * sizeof(ScanTile));
     if ((rc = grow(ctx, &ctx->ws, &ctx->ws_cap, need, st))) return rc;
@@ -275,6 +277,7 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
         sd.d_chunk_base = ar.take<int64_t>(B + 1);
         sd.d_part = ar.take<ChunkPartial>(sd.n_chunks);
         sd.d_stats = ar.take<SeriesStats>(B);
+        sd.d_cs = ar.take<int32_t>(sd.n_chunks);
     };
     carve(X);
     if (!acf) carve(Y);
@@ -301,7 +304,8 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
     if ((rc = upload(d_tiles, tiles.data(), n_tiles * sizeof(ScanTile)))) return rc;
 
     auto run_stats = [&](Side &sd) {
-        launch_stats_chunks(sd.t, sd.v, sd.d_offs, sd.d_chunk_base, B, sd.n_chunks, kPrepChunk,
+        launch_chunk_series(sd.d_chunk_base, B, sd.d_cs, st);
+        launch_stats_chunks(sd.t, sd.v, sd.d_offs, sd.d_chunk_base, sd.d_cs, sd.n_chunks, kPrepChunk,
                             sd.d_part, st);
         launch_stats_finish(sd.t, sd.v, sd.d_offs, sd.d_chunk_base, B, sd.d_part, sd.d_stats, st);
     };
@@ -363,7 +367,7 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
         auto keys = [&](Side &sd) {
             Keys kk{a2.take<int64_t>(sd.n_total), a2.take<int64_t>(sd.n_total),
                     a2.take<int64_t>(sd.n_total + 1), a2.take<int64_t>(sd.n_chunks + 1)};
-            launch_keys_prefix(sd.t, sd.v, sd.d_offs, sd.d_chunk_base, B, sd.n_chunks, kPrepChunk,
+            launch_keys_prefix(sd.t, sd.v, sd.d_offs, sd.d_chunk_base, sd.d_cs, sd.n_chunks, kPrepChunk,
                                sd.d_stats, fs, kk.T, kk.Xq, kk.P, kk.cs, sd.n_total, st);
             return kk;
         };
@@ -478,10 +482,10 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
     sa.lags = lags;
     sa.h_lags = lagv.data();
     sa.x = {X.t, X.v, X.d_offs, X.d_stats, X.offs.data(), X.stats.data(), X.n_total, X.n_max,
-            X.d_chunk_base, X.n_chunks};
+            X.d_chunk_base, X.n_chunks, X.d_cs};
     if (!acf)
         sa.y = {Y.t, Y.v, Y.d_offs, Y.d_stats, Y.offs.data(), Y.stats.data(), Y.n_total, Y.n_max,
-                Y.d_chunk_base, Y.n_chunks};
+                Y.d_chunk_base, Y.n_chunks, Y.d_cs};
     sa.c_out = c_out;
     sa.b_out = b_out;
     sa.count_out = count_out;

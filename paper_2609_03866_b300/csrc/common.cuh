@@ -58,9 +58,11 @@ struct Arena {
 
 // ---- statistics and keys (k_prep.cu) ----
 // Chunked statistics: one CTA per chunk of `chunk` points; chunk_base[b] is
-// the first chunk of series b (host-computed, B+1 entries on the device).
+// the first chunk of series b (host-computed, B+1 entries on the device) and
+// cs[g] the series of chunk g (launch_chunk_series fills it).
+void launch_chunk_series(const int64_t *chunk_base, int64_t B, int32_t *cs, cudaStream_t st);
 void launch_stats_chunks(const double *t, const double *x, const int64_t *offs,
-                         const int64_t *chunk_base, int64_t B, int64_t n_chunks, int chunk,
+                         const int64_t *chunk_base, const int32_t *cs, int64_t n_chunks, int chunk,
                          ChunkPartial *part, cudaStream_t st);
 void launch_stats_finish(const double *t, const double *x, const int64_t *offs,
                          const int64_t *chunk_base, int64_t B, const ChunkPartial *part,
@@ -68,7 +70,7 @@ void launch_stats_finish(const double *t, const double *x, const int64_t *offs,
 // Fixed-point keys and the exclusive prefix sum of the quantised standardised values.
 // Writes Tk[total], Xq[total] and P[total + 1].
 void launch_keys_prefix(const double *t, const double *x, const int64_t *offs,
-                        const int64_t *chunk_base, int64_t B, int64_t n_chunks, int chunk,
+                        const int64_t *chunk_base, const int32_t *cs, int64_t n_chunks, int chunk,
                         const SeriesStats *stats, FixedScales fs, int64_t *Tk, int64_t *Xq,
                         int64_t *P, int64_t *chunk_sums, int64_t n_total, cudaStream_t st);
 

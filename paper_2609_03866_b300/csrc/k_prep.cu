@@ -23,13 +23,37 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ int64_t find_series(const int64_t *chunk_base, int64_t B, int64_t g) {
-    int64_t lo = 0, hi = B;  // chunk_base[lo] <= g < chunk_base[hi]
-    while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
-        if (chunk_base[mid] <= g) lo = mid; else hi = mid;
+// cs[g] = series of chunk g (one thread per series writes its chunk range)
+__global__ void chunk_series_kernel(const int64_t *__restrict__ chunk_base, int64_t B,
+                                    int32_t *__restrict__ cs) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    for (int64_t g = chunk_base[b]; g < chunk_base[b + 1]; ++g) cs[g] = (int32_t)b;
+}
+
+// floor(v * 2^q) as int64 from the bit pattern of v (exact: the product is a
+// power-of-two scaling).  Requires |v| 2^q < 2^62.  Integer operations only:
+// FP64 conversion instructions are slow on this GPU.
+__device__ __forceinline__ long long fixed_floor(double v, int q) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const bool neg = (u >> 63) != 0;
+    const int e = (int)((u >> 52) & 0x7FF);
+    if (e == 0) return (neg && (u << 1) != 0) ? -1 : 0;  // zero or subnormal
+    const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = e - 1075 + q;
+    unsigned long long mag;
+    bool rem;
+    if (sh >= 0) {
+        mag = m << sh;
+        rem = false;
+    } else if (sh > -64) {
+        mag = m >> -sh;
+        rem = (m << (64 + sh)) != 0;
+    } else {
+        mag = 0;
+        rem = true;
     }
-    return lo;
+    return neg ? -(long long)(mag + (rem ? 1 : 0)) : (long long)mag;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -40,22 +64,34 @@ __device__ __forceinline__ double warp_sum(double v) {
 __global__ void __launch_bounds__(kThreads)
 stats_chunks_kernel(const double *__restrict__ t, const double *__restrict__ x,
                     const int64_t *__restrict__ offs, const int64_t *__restrict__ chunk_base,
-                    int64_t B, int chunk, ChunkPartial *__restrict__ part) {
+                    const int32_t *__restrict__ cs, int chunk, ChunkPartial *__restrict__ part) {
     const int64_t g = blockIdx.x;
-    const int64_t b = find_series(chunk_base, B, g);
+    const int64_t b = cs[g];
     const int64_t a0 = offs[b], a1 = offs[b + 1];
     const int64_t start = a0 + (g - chunk_base[b]) * (int64_t)chunk;
     const int64_t end = min(start + (int64_t)chunk, a1);
     const double xref = x[a0];
     double s1 = 0.0, s2 = 0.0;
     int flags = 0;
-    for (int64_t i = start + threadIdx.x; i < end; i += blockDim.x) {
-        const double xi = x[i], ti = t[i];
-        if (!isfinite(xi) || !isfinite(ti)) flags |= STAT_NONFINITE;
-        if (i > a0 && t[i - 1] > ti) flags |= STAT_UNSORTED;
-        const double d = xi - xref;
-        s1 += d;
-        s2 = fma(d, d, s2);
+#pragma unroll 4
+    for (int r = 0; r < kPrepChunk / kThreads; ++r) {
+        const int64_t i = start + threadIdx.x + (int64_t)r * kThreads;
+        if (i < end) {
+            const double xi = x[i], ti = t[i];
+            const unsigned long long ux = (unsigned long long)__double_as_longlong(xi);
+            const unsigned long long ut = (unsigned long long)__double_as_longlong(ti);
+            if (((ux >> 52) & 0x7FF) == 0x7FF || ((ut >> 52) & 0x7FF) == 0x7FF) flags |= STAT_NONFINITE;
+            if (i > a0) {
+                // order-preserving integer images of the two times
+                const long long kt = (long long)(ut ^ ((ut >> 63) ? 0x7FFFFFFFFFFFFFFFull : 0ull));
+                const unsigned long long up = (unsigned long long)__double_as_longlong(t[i - 1]);
+                const long long kp = (long long)(up ^ ((up >> 63) ? 0x7FFFFFFFFFFFFFFFull : 0ull));
+                if (kp > kt) flags |= STAT_UNSORTED;
+            }
+            const double d = xi - xref;
+            s1 += d;
+            s2 = fma(d, d, s2);
+        }
     }
     __shared__ double sh1[kThreads / 32], sh2[kThreads / 32];
     __shared__ int shf[kThreads / 32];
@@ -112,21 +148,27 @@ constexpr int kItems = 16;  // elements per thread in the keys/prefix kernels
 __global__ void __launch_bounds__(kThreads)
 keys_chunks_kernel(const double *__restrict__ t, const double *__restrict__ x,
                    const int64_t *__restrict__ offs, const int64_t *__restrict__ chunk_base,
-                   int64_t B, int chunk, const SeriesStats *__restrict__ stats, FixedScales fs,
-                   int64_t *__restrict__ Tk, int64_t *__restrict__ Xq,
+                   const int32_t *__restrict__ cs, int chunk, const SeriesStats *__restrict__ stats,
+                   FixedScales fs, int64_t *__restrict__ Tk, int64_t *__restrict__ Xq,
                    unsigned long long *__restrict__ chunk_sums) {
     const int64_t g = blockIdx.x;
-    const int64_t b = find_series(chunk_base, B, g);
+    const int64_t b = cs[g];
     const int64_t a0 = offs[b], a1 = offs[b + 1];
     const int64_t start = a0 + (g - chunk_base[b]) * (int64_t)chunk;
     const int64_t end = min(start + (int64_t)chunk, a1);
     const double mean = stats[b].mean, inv = stats[b].inv_std;
     unsigned long long acc = 0;
-    for (int64_t i = start + threadIdx.x; i < end; i += blockDim.x) {
-        Tk[i] = __double2ll_rd(t[i] * fs.tscale);
-        const long long q = __double2ll_rn((x[i] - mean) * inv * fs.vscale);
-        Xq[i] = q;
-        acc += (unsigned long long)q;
+#pragma unroll 4
+    for (int r = 0; r < kPrepChunk / kThreads; ++r) {
+        const int64_t i = start + threadIdx.x + (int64_t)r * kThreads;
+        if (i < end) {
+            Tk[i] = fixed_floor(t[i], fs.q);
+            // round(x_std 2^p) = floor(x_std 2^(p+1) + 1) >> 1, half up
+            const long long q2 = fixed_floor((x[i] - mean) * inv, fs.p + 1);
+            const long long q = (q2 + 1) >> 1;
+            Xq[i] = q;
+            acc += (unsigned long long)q;
+        }
     }
     for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     __shared__ unsigned long long sh[kThreads / 32];
@@ -169,12 +211,12 @@ scan_chunk_sums_kernel(unsigned long long *__restrict__ v, int64_t n,
 // Per chunk: P[i] = chunk prefix + exclusive scan of Xq inside the chunk.
 __global__ void __launch_bounds__(kThreads)
 prefix_apply_kernel(const int64_t *__restrict__ offs, const int64_t *__restrict__ chunk_base,
-                    int64_t B, int chunk, const int64_t *__restrict__ Xq,
+                    const int32_t *__restrict__ cs, int chunk, const int64_t *__restrict__ Xq,
                     const unsigned long long *__restrict__ chunk_pref,
                     const unsigned long long *__restrict__ total, int64_t n_total,
                     int64_t *__restrict__ P) {
     const int64_t g = blockIdx.x;
-    const int64_t b = find_series(chunk_base, B, g);
+    const int64_t b = cs[g];
     const int64_t a0 = offs[b], a1 = offs[b + 1];
     const int64_t start = a0 + (g - chunk_base[b]) * (int64_t)chunk;
     const int64_t end = min(start + (int64_t)chunk, a1);
@@ -211,11 +253,16 @@ prefix_apply_kernel(const int64_t *__restrict__ offs, const int64_t *__restrict_
 
 }  // namespace
 
+void launch_chunk_series(const int64_t *chunk_base, int64_t B, int32_t *cs, cudaStream_t st) {
+    NCF_LAUNCH("chunk_series_kernel", st,
+               chunk_series_kernel<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(chunk_base, B, cs));
+}
+
 void launch_stats_chunks(const double *t, const double *x, const int64_t *offs,
-                         const int64_t *chunk_base, int64_t B, int64_t n_chunks, int chunk,
+                         const int64_t *chunk_base, const int32_t *cs, int64_t n_chunks, int chunk,
                          ChunkPartial *part, cudaStream_t st) {
     NCF_LAUNCH("stats_chunks_kernel", st,
-    stats_chunks_kernel<<<(unsigned)n_chunks, kThreads, 0, st>>>(t, x, offs, chunk_base, B, chunk, part));
+    stats_chunks_kernel<<<(unsigned)n_chunks, kThreads, 0, st>>>(t, x, offs, chunk_base, cs, chunk, part));
 }
 
 void launch_stats_finish(const double *t, const double *x, const int64_t *offs,
@@ -226,19 +273,19 @@ void launch_stats_finish(const double *t, const double *x, const int64_t *offs,
 }
 
 void launch_keys_prefix(const double *t, const double *x, const int64_t *offs,
-                        const int64_t *chunk_base, int64_t B, int64_t n_chunks, int chunk,
+                        const int64_t *chunk_base, const int32_t *cs, int64_t n_chunks, int chunk,
                         const SeriesStats *stats, FixedScales fs, int64_t *Tk, int64_t *Xq,
                         int64_t *P, int64_t *chunk_sums, int64_t n_total, cudaStream_t st) {
     // chunk must equal kThreads * kItems (= kPrepChunk) for prefix_apply_kernel
-    auto *cs = reinterpret_cast<unsigned long long *>(chunk_sums);
+    auto *csum = reinterpret_cast<unsigned long long *>(chunk_sums);
     NCF_LAUNCH("keys_chunks_kernel", st,
-    keys_chunks_kernel<<<(unsigned)n_chunks, kThreads, 0, st>>>(t, x, offs, chunk_base, B, chunk,
-                                                                 stats, fs, Tk, Xq, cs));
+               keys_chunks_kernel<<<(unsigned)n_chunks, kThreads, 0, st>>>(t, x, offs, chunk_base, cs, chunk,
+                                                                            stats, fs, Tk, Xq, csum));
     NCF_LAUNCH("scan_chunk_sums_kernel", st,
-    scan_chunk_sums_kernel<<<1, 1024, 0, st>>>(cs, n_chunks, cs + n_chunks));
+               scan_chunk_sums_kernel<<<1, 1024, 0, st>>>(csum, n_chunks, csum + n_chunks));
     NCF_LAUNCH("prefix_apply_kernel", st,
-    prefix_apply_kernel<<<(unsigned)n_chunks, kThreads, 0, st>>>(offs, chunk_base, B, chunk, Xq, cs,
-                                                                  cs + n_chunks, n_total, P));
+               prefix_apply_kernel<<<(unsigned)n_chunks, kThreads, 0, st>>>(offs, chunk_base, cs, chunk, Xq,
+                                                                             csum, csum + n_chunks, n_total, P));
 }
 
 }  // namespace ncf

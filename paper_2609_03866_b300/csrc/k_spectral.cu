@@ -69,6 +69,56 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
     }
 }
 
+// Per-tap polynomial form of the ES kernel for spreading: tap k of a point at
+// fractional offset f0 in [0, 1) has weight phi((f0 + k - W/2) / (W/2)); on that
+// interval phi is interpolated at D+1 Chebyshev nodes in u = 2 f0 - 1 and the
+// interpolant is rewritten in powers of u (coefficient d of tap k at
+// c[k * (D+1) + d]), so the kernel evaluates it with D fused multiply-adds and
+// no special-function instructions.  Max error: 8e-8 (W = 8, D = 8, FP32) and
+// 4e-15 (W = 16, D = 14, FP64) of the peak value 1.
+std::vector<double> es_poly(int W, double beta, int D) {
+    std::vector<double> out((size_t)W * (D + 1));
+    const int n = D + 1;
+    std::vector<double> node(n), val(n), cheb(n), pw(n), tk(n), tkm1(n), tkp1(n);
+    for (int i = 0; i < n; ++i) node[i] = std::cos(kPi * (i + 0.5) / n);
+    for (int k = 0; k < W; ++k) {
+        for (int i = 0; i < n; ++i) {
+            const double f = 0.5 * (node[i] + 1.0);
+            const double z = (f + k - 0.5 * W) / (0.5 * W);
+            const double u = std::max(0.0, 1.0 - z * z);
+            val[i] = std::exp(beta * (std::sqrt(u) - 1.0));
+        }
+        // Chebyshev coefficients of the interpolant
+        for (int j = 0; j < n; ++j) {
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) acc += val[i] * std::cos(kPi * j * (i + 0.5) / n);
+            cheb[j] = acc * (j == 0 ? 1.0 : 2.0) / n;
+        }
+        // sum_j cheb_j T_j(u) in powers of u, with T_{j+1} = 2u T_j - T_{j-1}
+        std::fill(pw.begin(), pw.end(), 0.0);
+        std::fill(tkm1.begin(), tkm1.end(), 0.0);
+        std::fill(tk.begin(), tk.end(), 0.0);
+        tkm1[0] = 1.0;            // T_0
+        if (n > 1) tk[1] = 1.0;   // T_1
+        pw[0] += cheb[0];
+        for (int j = 1; j < n; ++j) {
+            for (int d = 0; d < n; ++d) pw[d] += cheb[j] * tk[d];
+            std::fill(tkp1.begin(), tkp1.end(), 0.0);
+            for (int d = 0; d + 1 < n; ++d) tkp1[d + 1] += 2.0 * tk[d];
+            for (int d = 0; d < n; ++d) tkp1[d] -= tkm1[d];
+            tkm1 = tk;
+            tk = tkp1;
+        }
+        for (int d = 0; d < n; ++d) out[(size_t)k * n + d] = pw[d];
+    }
+    return out;
+}
+
+template <typename R, int W, int D> struct EsPoly { R c[W * (D + 1)]; };
+template <int W> struct PolyDeg;
+template <> struct PolyDeg<8> { static constexpr int D = 8; };
+template <> struct PolyDeg<16> { static constexpr int D = 14; };
+
 // ---------------------------------------------------------------------------
 // tables
 // ---------------------------------------------------------------------------
@@ -131,78 +181,197 @@ __global__ void lag_table_kernel(const unsigned long long *__restrict__ Phi, int
 // spreading (global-memory grids)
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ int64_t find_series(const int64_t *chunk_base, int64_t B, int64_t g) {
-    int64_t lo = 0, hi = B;
-    while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
-        if (chunk_base[mid] <= g) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
-template <typename R> __device__ __forceinline__ R es_kernel(R z, R beta);
-template <> __device__ __forceinline__ float es_kernel<float>(float z, float beta) {
-    const float u = fmaxf(0.0f, fmaf(-z, z, 1.0f));
-    return __expf(beta * (sqrtf(u) - 1.0f));
-}
-template <> __device__ __forceinline__ double es_kernel<double>(double z, double beta) {
-    const double u = fmax(0.0, fma(-z, z, 1.0));
-    return exp(beta * (sqrt(u) - 1.0));
-}
-
 template <typename V> __device__ __forceinline__ void atomic_add_v(V *p, decltype(V{}.x) a, decltype(V{}.x) b) {
     atomicAdd(&p->x, a);
     atomicAdd(&p->y, b);
 }
 
 constexpr int kSpreadThreads = 256;
+constexpr int kSpreadTile = 2048;                          // grid cells of the SMEM tile
+constexpr int kStagePad = kPrepChunk + kPrepChunk / 128;   // staged points, one pad per 128
+
+// ceil(g) and ceil(g) - g for 1 <= g < 2^52 from the bit pattern of g: on this
+// GPU FP64 conversion instructions run at about half the FP64 add rate, while
+// integer shifts and masks run at the full integer rate.
+__device__ __forceinline__ void split_ceil(double g, int &l0, float &f0) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(g);
+    const int E = (int)((u >> 52) & 0x7FF) - 1023;             // g in [2^E, 2^(E+1))
+    const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const unsigned long long fr = m << (12 + E);               // fraction * 2^64
+    l0 = (int)(m >> (52 - E)) + (fr != 0ull);
+    // 1 - fraction (0 when g is an integer), 23 bits, built as a float in [1, 2) minus 1
+    f0 = __uint_as_float(0x3F800000u | (unsigned)((0ull - fr) >> 41)) - 1.0f;
+}
+
+// v as an unevaluated sum hi + lo of two floats (about 48 significant bits),
+// from the bit pattern when the exponent allows, else by conversion.
+__device__ __forceinline__ void split_df(double v, float &hi, float &lo) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((u >> 52) & 0x7FF);
+    if (e >= 949 && e <= 1150) {
+        const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+        const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+        hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29));
+        const float scale = __uint_as_float((unsigned)(e - 948) << 23);  // 2^(e - 1075)
+        const float r = (float)(unsigned)(m & 0x1FFFFFFFull) * scale;
+        lo = sign ? -r : r;
+    } else {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    }
+}
+
+template <typename R> struct PointPhase;
+template <> struct PointPhase<float> {
+    // FP32 form: one FP64 FMA for the phase, everything else in integer/FP32
+    __device__ static void eval(double t, double x, double a_scale, double c_off, float mhi, float mlo,
+                                float inv, int &l0, float &f0, float &xs) {
+        split_ceil(fma(t, a_scale, c_off), l0, f0);
+        float xh, xl;
+        split_df(x, xh, xl);
+        xs = ((xh - mhi) + (xl - mlo)) * inv;
+    }
+};
+template <> struct PointPhase<double> {
+    __device__ static void eval(double t, double x, double a_scale, double c_off, double mean, double,
+                                double inv, int &l0, double &f0, double &xs) {
+        const double gs = fma(t, a_scale, c_off);
+        l0 = (int)ceil(gs);
+        f0 = (double)l0 - gs;
+        xs = (x - mean) * inv;
+    }
+};
 
 // One CTA per prep chunk (kPrepChunk consecutive points of one series).
 // Grid coordinate of a point: g = (t - t_c) n_f / L; the kernel touches the W
-// cells l0 .. l0+W-1 with l0 = ceil(g - W/2) (taken mod n_f).  gs = g - W/2 +
-// n_f is formed with one FP64 FMA (positive, so ceil is a plain conversion).
-template <typename R, int W, int TILE>
+// cells l0 .. l0+W-1 with l0 = ceil(g - W/2) (taken mod n_f), gs = g - W/2 + n_f
+// formed with one FP64 FMA.
+//   phase 1  coalesced loads of (t, x); per point (l0, f0, x_std) staged in SMEM;
+//   phase 2  spreading: lane l of warp w takes points l*128 + w*16 + q, so the
+//            32 lanes of an atomic instruction sit 128 points (several cells)
+//            apart -- sorted points would otherwise hit the same cell 32 times;
+//            the staging pad (one slot per 128 points) keeps these reads free of
+//            bank conflicts;
+//   phase 3  the chunk's tile of cells is added to the series' grid in HBM.
+// A chunk spanning more cells than the tile (a sparse series) adds straight to HBM.
+template <typename R, int W>
 __global__ void __launch_bounds__(kSpreadThreads)
 spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
-              const int64_t *__restrict__ offs, const int64_t *__restrict__ chunk_base, int64_t B,
+              const int64_t *__restrict__ offs, const int64_t *__restrict__ chunk_base,
+              const int32_t *__restrict__ cs,
               const SeriesStats *__restrict__ st, const double *__restrict__ tc, double a_scale,
-              int nf, R beta, typename CT<R>::V *__restrict__ grids) {
+              int nf, const EsPoly<R, W, PolyDeg<W>::D> poly, typename CT<R>::V *__restrict__ grids) {
     using V = typename CT<R>::V;
-    __shared__ V tile[TILE];
+    constexpr int D = PolyDeg<W>::D;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *tile = reinterpret_cast<V *>(smem_raw);
+    R *sf = reinterpret_cast<R *>(tile + kSpreadTile);
+    R *sx = sf + kStagePad;
+    int *sl = reinterpret_cast<int *>(sx + kStagePad);
     const int64_t g = blockIdx.x;
-    const int64_t b = find_series(chunk_base, B, g);
+    const int64_t b = cs[g];
     const int64_t a0 = offs[b], a1 = offs[b + 1];
     const int64_t start = a0 + (g - chunk_base[b]) * (int64_t)kPrepChunk;
-    const int64_t end = min(start + (int64_t)kPrepChunk, a1);
+    const int n = (int)(min(start + (int64_t)kPrepChunk, a1) - start);
     const double c_off = -tc[b] * a_scale - 0.5 * W + nf;
-    const double mean = st[b].mean, inv = st[b].inv_std;
+    const double mean = st[b].mean;
+    R mhi, mlo;
+    if constexpr (sizeof(R) == 4) {
+        float h, l;
+        split_df(mean, h, l);
+        mhi = h;
+        mlo = l;
+    } else {
+        mhi = mean;
+        mlo = 0;
+    }
+    const R inv = (R)st[b].inv_std;
     V *grid = grids + b * (int64_t)nf;
     const int mask = nf - 1;
-    const int l_first = (int)ceil(fma(t[start], a_scale, c_off));
-    const int l_last = (int)ceil(fma(t[end - 1], a_scale, c_off)) + W - 1;
+#pragma unroll 4
+    for (int r = 0; r < kPrepChunk / kSpreadThreads; ++r) {
+        const int p = threadIdx.x + r * kSpreadThreads;
+        if (p < n) {
+            int l0;
+            R f0, xs;
+            PointPhase<R>::eval(t[start + p], x[start + p], a_scale, c_off, mhi, mlo, inv, l0, f0, xs);
+            const int pi = p + (p >> 7);
+            sl[pi] = l0;
+            sf[pi] = f0;
+            sx[pi] = xs;
+        }
+    }
+    __syncthreads();
+    const int l_first = sl[0];
+    const int l_last = sl[(n - 1) + ((n - 1) >> 7)] + W - 1;
     const int span = l_last - l_first + 1;
-    const bool use_tile = span <= TILE;
+    const bool use_tile = span <= kSpreadTile;
     if (use_tile) {
         for (int i = threadIdx.x; i < span; i += blockDim.x) { tile[i].x = 0; tile[i].y = 0; }
-        __syncthreads();
     }
-    const R half = (R)(0.5 * W), inv_half = (R)(2.0 / W);
-    for (int64_t i = start + threadIdx.x; i < end; i += blockDim.x) {
-        const double gs = fma(t[i], a_scale, c_off);
-        const int l0 = (int)ceil(gs);
-        const R f0 = (R)((double)l0 - gs);          // in [0, 1)
-        const R xs = (R)((x[i] - mean) * inv);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // Each lane walks 16 consecutive sorted points and accumulates their taps in
+    // a register window of W cells that slides with the points; a cell is added
+    // to the tile (or the grid) only when the window leaves it.  Dense series put
+    // many points in one cell, so most taps never touch shared memory.
+    R wre[W], wim[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) { wre[k] = 0; wim[k] = 0; }
+    int wbase = 0;
+    bool started = false;
+    auto flush_cell = [&](int cell, R re, R im) {
+        if (re == (R)0 && im == (R)0) return;
+        if (use_tile) {
+            atomicAdd(&tile[cell - l_first].x, re);
+            atomicAdd(&tile[cell - l_first].y, im);
+        } else {
+            atomic_add_v(&grid[cell & mask], re, im);
+        }
+    };
+#pragma unroll 1
+    for (int q = 0; q < kPrepChunk / kSpreadThreads; ++q) {
+        const int p = lane * 128 + warp * 16 + q;
+        if (p >= n) break;
+        const int pi = p + (p >> 7);
+        const int l0 = sl[pi];
+        const R f0 = sf[pi], xs = sx[pi];
+        if (!started) {
+            wbase = l0;
+            started = true;
+        }
+        int dd = l0 - wbase;
+        if (dd >= W) {
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                flush_cell(wbase + k, wre[k], wim[k]);
+                wre[k] = 0;
+                wim[k] = 0;
+            }
+            wbase = l0;
+            dd = 0;
+        }
+        for (; dd > 0; --dd) {  // slide by one cell
+            flush_cell(wbase, wre[0], wim[0]);
+#pragma unroll
+            for (int k = 0; k < W - 1; ++k) { wre[k] = wre[k + 1]; wim[k] = wim[k + 1]; }
+            wre[W - 1] = 0;
+            wim[W - 1] = 0;
+            ++wbase;
+        }
+        const R u = (R)2 * f0 - (R)1;
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            const R z = (f0 + (R)k - half) * inv_half;
-            const R phi = es_kernel<R>(z, beta);
-            if (use_tile) {
-                atomicAdd(&tile[l0 + k - l_first].x, phi * xs);
-                atomicAdd(&tile[l0 + k - l_first].y, phi);
-            } else {
-                atomic_add_v(&grid[(l0 + k) & mask], phi * xs, phi);
-            }
+            R phi = poly.c[k * (D + 1) + D];
+#pragma unroll
+            for (int d = D - 1; d >= 0; --d) phi = fma(phi, u, poly.c[k * (D + 1) + d]);
+            wre[k] = fma(phi, xs, wre[k]);
+            wim[k] += phi;
         }
+    }
+    if (started) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) flush_cell(wbase + k, wre[k], wim[k]);
     }
     if (use_tile) {
         __syncthreads();
@@ -211,6 +380,11 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
             if (v.x != 0 || v.y != 0) atomic_add_v(&grid[(l_first + i) & mask], v.x, v.y);
         }
     }
+}
+
+template <typename R>
+constexpr size_t spread_smem_bytes() {
+    return kSpreadTile * sizeof(typename CT<R>::V) + (size_t)kStagePad * (2 * sizeof(R) + sizeof(int));
 }
 
 // ---------------------------------------------------------------------------
@@ -477,22 +651,39 @@ ncf_status run_typed(const SpectralArgs &a, const Plan &p, char *ws, const doubl
 
     // spreading
     const double a_scale = (double)p.nf / p.L;
-    auto spread = [&](const SpecSide &sd, V *grid, const int64_t *chunk_base, int64_t n_chunks) {
+    auto spread = [&](const SpecSide &sd, V *grid, const int64_t *chunk_base, const int32_t *cs,
+                      int64_t n_chunks) {
         cudaMemsetAsync(grid, 0, B * (size_t)p.nf * sizeof(V), st);
-        constexpr int TILE = sizeof(R) == 4 ? 4096 : 2048;
+        constexpr size_t smem = spread_smem_bytes<R>();
+        EsPoly<R, 8, PolyDeg<8>::D> poly8{};
+        EsPoly<R, 16, PolyDeg<16>::D> poly16{};
+        {
+            const int D = p.W == 8 ? PolyDeg<8>::D : PolyDeg<16>::D;
+            const std::vector<double> c = es_poly(p.W, p.beta, D);
+            for (size_t i = 0; i < c.size(); ++i) {
+                if (p.W == 8) poly8.c[i] = (R)c[i];
+                else poly16.c[i] = (R)c[i];
+            }
+        }
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(spread_kernel<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(spread_kernel<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = true;
+        }
         if (p.W == 8)
             NCF_LAUNCH("spread_kernel", st,
-                       spread_kernel<R, 8, TILE><<<(unsigned)n_chunks, kSpreadThreads, 0, st>>>(
-                           sd.t, sd.v, sd.d_offs, chunk_base, B, sd.d_stats, d_tc, a_scale, p.nf,
-                           (R)p.beta, grid));
+                       spread_kernel<R, 8><<<(unsigned)n_chunks, kSpreadThreads, smem, st>>>(
+                           sd.t, sd.v, sd.d_offs, chunk_base, cs, sd.d_stats, d_tc, a_scale, p.nf,
+                           poly8, grid));
         else
             NCF_LAUNCH("spread_kernel", st,
-                       spread_kernel<R, 16, TILE><<<(unsigned)n_chunks, kSpreadThreads, 0, st>>>(
-                           sd.t, sd.v, sd.d_offs, chunk_base, B, sd.d_stats, d_tc, a_scale, p.nf,
-                           (R)p.beta, grid));
+                       spread_kernel<R, 16><<<(unsigned)n_chunks, kSpreadThreads, smem, st>>>(
+                           sd.t, sd.v, sd.d_offs, chunk_base, cs, sd.d_stats, d_tc, a_scale, p.nf,
+                           poly16, grid));
     };
-    spread(a.x, grid_x, a.x.d_chunk_base, a.x.n_chunks);
-    if (ccf) spread(a.y, grid_y, a.y.d_chunk_base, a.y.n_chunks);
+    spread(a.x, grid_x, a.x.d_chunk_base, a.x.d_cs, a.x.n_chunks);
+    if (ccf) spread(a.y, grid_y, a.y.d_chunk_base, a.y.d_cs, a.y.n_chunks);
 
     // FFT passes (ping-pong with scratch); result returned in *res
     const RadixPlan rp = radix_plan(p.lg);

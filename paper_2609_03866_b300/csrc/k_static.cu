@@ -44,7 +44,8 @@ constexpr size_t kOffTiles = kOffStats + al256(2 * sizeof(SeriesStats));
 constexpr size_t kOffNum = kOffTiles + al256(kMaxTiles * sizeof(ScanTile));
 constexpr size_t kOffDen = kOffNum + al256(kStaticMaxLags * 8);
 constexpr size_t kOffCnt = kOffDen + al256(kStaticMaxLags * 8);
-constexpr size_t kOffEnd = kOffCnt + al256(kStaticMaxLags * 8);
+constexpr size_t kOffCs = kOffCnt + al256(kStaticMaxLags * 8);                // 2 x kMaxChunks int32
+constexpr size_t kOffEnd = kOffCs + al256(2 * kMaxChunks * 4);
 static_assert(kOffEnd <= kStaticScratchBytes, "static scratch layout exceeds its array");
 
 constexpr int kMaxDevices = 64;
@@ -57,6 +58,8 @@ __global__ void static_setup_kernel(unsigned char *scratch, int64_t nx, int64_t 
     auto *offs = reinterpret_cast<int64_t *>(scratch + kOffOffs);
     auto *cb = reinterpret_cast<int64_t *>(scratch + kOffChunkBase);
     auto *tiles = reinterpret_cast<ScanTile *>(scratch + kOffTiles);
+    auto *cs = reinterpret_cast<int32_t *>(scratch + kOffCs);
+    for (int64_t i = threadIdx.x; i < 2 * kMaxChunks; i += blockDim.x) cs[i] = 0;  // one series
     const int64_t n_out = ny > 0 ? ny : nx;
     const int64_t nt = (n_out + tileJ - 1) / tileJ;
     for (int64_t i = threadIdx.x; i < nt; i += blockDim.x)
@@ -112,14 +115,15 @@ extern "C" ncf_status ncf_corr_window_static(const double *t, const double *x, i
     auto *num = reinterpret_cast<double *>(sc + kOffNum);
     auto *den = reinterpret_cast<double *>(sc + kOffDen);
     auto *cnt = reinterpret_cast<unsigned long long *>(sc + kOffCnt);
+    auto *cs = reinterpret_cast<int32_t *>(sc + kOffCs);
     const int tileJ = scan_tile_points();
     const int64_t n_out = acf ? nx : ny;
     NCF_LAUNCH("static_setup_kernel", st, static_setup_kernel<<<1, 256, 0, st>>>(sc, nx, acf ? 0 : ny, tileJ));
     const int64_t chx = (nx + kPrepChunk - 1) / kPrepChunk, chy = (ny + kPrepChunk - 1) / kPrepChunk;
-    launch_stats_chunks(t, x, offs, cb, 1, chx, kPrepChunk, part, st);
+    launch_stats_chunks(t, x, offs, cb, cs, chx, kPrepChunk, part, st);
     launch_stats_finish(t, x, offs, cb, 1, part, stats, st);
     if (!acf) {
-        launch_stats_chunks(s, y, offs + 2, cb + 2, 1, chy, kPrepChunk, part + kMaxChunks, st);
+        launch_stats_chunks(s, y, offs + 2, cb + 2, cs + kMaxChunks, chy, kPrepChunk, part + kMaxChunks, st);
         launch_stats_finish(s, y, offs + 2, cb + 2, 1, part + kMaxChunks, stats + 1, st);
     }
     // validation: read the two statistics records back into host stack memory

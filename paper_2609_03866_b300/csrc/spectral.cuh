@@ -16,6 +16,7 @@ struct SpecSide {
     int64_t n_total = 0, n_max = 0;
     const int64_t *d_chunk_base = nullptr;    // device chunk table of the statistics pass
     int64_t n_chunks = 0;
+    const int32_t *d_cs = nullptr;            // series of each chunk
 };
 
 struct SpectralArgs {
