@@ -105,9 +105,12 @@ __device__ __forceinline__ void mac128(U128 &a, long long w, long long y) {
 // not below `bound`.  Two keys per step for the common short move; a long
 // move (the outer point crossed an observing gap) gallops, then bisects.
 // sK holds sentinels at nK .. nK + 7, and the answer is <= nK.
-__device__ __forceinline__ int advance32(const int32_t *__restrict__ sK, int p, int nK, int32_t bound) {
-    const int a = sK[p] < bound, b = sK[p + 1] < bound;
+__device__ __forceinline__ int advance32(const int32_t *__restrict__ sK, int p, int nK, int32_t bound,
+                                         int32_t &key) {
+    const int32_t k0 = sK[p], k1 = sK[p + 1];
+    const int a = k0 < bound, b = k1 < bound;
     p += a + (a & b);
+    key = a ? k1 : k0;  // the key at the returned position (short move)
     if (a & b) {
         int step = 4;
         for (;;) {
@@ -116,7 +119,9 @@ __device__ __forceinline__ int advance32(const int32_t *__restrict__ sK, int p, 
                 p = idx + 1;
                 step <<= 1;
             } else {
-                return lower_bound32(sK, p, idx, bound);
+                p = lower_bound32(sK, p, idx, bound);
+                key = sK[p];
+                return p;
             }
         }
     }
@@ -213,8 +218,9 @@ rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
             for (int r = r0; r < r1; ++r) {
                 const int32_t sc = sm.sSc[r];
                 const int32_t La = sc + dlc, Ua = sc + duc;
-                lo = advance32(sK, lo, nK, La);
-                if (sK[lo] < sc + dlc2) {  // inside the coarse band: full keys, then FP64
+                int32_t klo, khi;
+                lo = advance32(sK, lo, nK, La, klo);
+                if (klo < sc + dlc2) {  // inside the coarse band: full keys, then FP64
                     const int64_t j = tile.j0 + r;
                     const int64_t Lf = Sy[j] + dl;
                     const double lb = __dsub_rn(centre(sy[j], tau, eps), h);
@@ -223,8 +229,8 @@ rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
                     lo = (int)(p - ia);
                 }
                 if (hi < lo) hi = lo;
-                hi = advance32(sK, hi, nK, Ua);
-                if (sK[hi] < sc + duc2) {
+                hi = advance32(sK, hi, nK, Ua, khi);
+                if (khi < sc + duc2) {
                     const int64_t j = tile.j0 + r;
                     const int64_t Uf = Sy[j] + du;
                     const double ub = __dadd_rn(centre(sy[j], tau, eps), h);
