@@ -544,15 +544,25 @@ contract_kernel(const R *__restrict__ Anum, const R *__restrict__ Aden, const R 
 __global__ void finish_spectral_kernel(const double *__restrict__ acc_num,
                                        const double *__restrict__ acc_den, int64_t B, int64_t K,
                                        int64_t Kp, int lag0_mode, const double *__restrict__ lag0,
+                                       const int *__restrict__ status, const float *__restrict__ dc_num,
+                                       const float *__restrict__ dc_den, int64_t row,
                                        double *__restrict__ c, double *__restrict__ bo,
                                        int64_t *__restrict__ cnt) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * K) return;
+    if (*status != 0) {  // a bounded device wait gave up: no valid result
+        c[i] = __longlong_as_double(0x7ff8000000000000ll);
+        if (bo) bo[i] = c[i];
+        if (cnt) cnt[i] = -1;
+        return;
+    }
     const int64_t b = i / K, k = i - b * K;
-    const double N = acc_num[b * Kp + k], D = acc_den[b * Kp + k];
+    // m = 0 terms kept out of the tensor-core sums (cos 0 = 1, sin 0 = 0)
+    const double n0 = dc_num ? (double)dc_num[b * row] : 0.0, d0 = dc_den ? (double)dc_den[b * row] : 0.0;
+    const double N = acc_num[b * Kp + k] + n0, D = acc_den[b * Kp + k] + d0;
     double ci = N / fmax(D, 1e-16);
     if (lag0_mode == 1) {          // ACF: divide by c(0) from the appended zero lag
-        ci /= acc_num[b * Kp + K] / fmax(acc_den[b * Kp + K], 1e-16);
+        ci /= (acc_num[b * Kp + K] + n0) / fmax(acc_den[b * Kp + K] + d0, 1e-16);
     } else if (lag0_mode == 2) {   // CCF: divide by sqrt(ACF_x(0) ACF_y(0))
         const double sx = lag0[4 * b] / fmax(lag0[4 * b + 1], 1e-16);
         const double sy = lag0[4 * b + 2] / fmax(lag0[4 * b + 3], 1e-16);
@@ -622,6 +632,7 @@ ncf_status run_typed(const SpectralArgs &a, const Plan &p, char *ws, const doubl
     unsigned long long *d_phi = take<unsigned long long>(ws, used, p.Kp);
     double *d_gx = take<double>(ws, used, p.nq);
     double *d_gphi = take<double>(ws, used, p.nq);
+    int *d_status = take<int>(ws, used, 1);
 
     // small host tables -> device (pinned staging)
     size_t off = 0;
@@ -726,17 +737,24 @@ ncf_status run_typed(const SpectralArgs &a, const Plan &p, char *ws, const doubl
     }
     cudaMemsetAsync(acc_num, 0, B * p.Kp * 8, st);
     cudaMemsetAsync(acc_den, 0, B * p.Kp * 8, st);
-    {
+    cudaMemsetAsync(d_status, 0, sizeof(int), st);
+    if constexpr (std::is_same<R, float>::value) {
+        // FP32 form: tensor cores (TF32 split products, FP64 chunk sums)
+        launch_contract_tc(Anum, Aden, E, B, p.M2, p.Kp, acc_num, acc_den, d_status, st);
+    } else {
         dim3 grid((unsigned)((p.Kp + kBN - 1) / kBN), (unsigned)((B + kBM - 1) / kBM),
                   (unsigned)((p.M2 + kChunk - 1) / kChunk));
         NCF_LAUNCH("contract_kernel", st,
-        contract_kernel<R><<<grid, 256, 0, st>>>(Anum, Aden, E, B, p.M2, p.Kp, acc_num, acc_den));
+                   contract_kernel<R><<<grid, 256, 0, st>>>(Anum, Aden, E, B, p.M2, p.Kp, acc_num, acc_den));
     }
     {
         const int mode = a.lag0 ? (ccf ? 2 : 1) : 0;
         NCF_LAUNCH("finish_spectral_kernel", st,
         finish_spectral_kernel<<<(unsigned)((B * a.K + 255) / 256), 256, 0, st>>>(
-            acc_num, acc_den, B, a.K, p.Kp, mode, lag0, a.c_out, a.b_out, a.count_out));
+            acc_num, acc_den, B, a.K, p.Kp, mode, lag0, d_status,
+            std::is_same<R, float>::value ? reinterpret_cast<const float *>(Anum) : nullptr,
+            std::is_same<R, float>::value ? reinterpret_cast<const float *>(Aden) : nullptr, p.M2, a.c_out,
+            a.b_out, a.count_out));
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -754,7 +772,7 @@ size_t workspace_bytes(const Plan &p, int64_t B, bool ccf) {
     s += al(p.nf * sizeof(V));
     s += al(p.Mp * 8) + al(p.Mp * sizeof(R));
     s += al(B * p.M2 * sizeof(R)) * 2 + al(p.M2 * p.Kp * sizeof(R));
-    s += al(B * p.Kp * 8) * 2 + al(4 * B * 8) + al(B * 8) + al(p.Kp * 8) + al(p.nq * 8) * 2;
+    s += al(B * p.Kp * 8) * 2 + al(4 * B * 8) + al(B * 8) + al(p.Kp * 8) + al(p.nq * 8) * 2 + al(4);
     return s + 1024;
 }
 

@@ -34,6 +34,13 @@ struct SpectralArgs {
 // Geometry chosen by the last run_spectral call (reported through ncf_last_plan).
 struct SpectralGeometry { double L; int64_t M, nf, W; };
 
+// Tensor-core contraction of the FP32 form (k_tc.cu): acc_c += A_c E over all
+// modes, TF32 split products, FP32 TMEM accumulation per 512-mode chunk, FP64
+// partial sums.  *status becomes nonzero if a bounded wait gave up.
+bool contract_tc_supported(int64_t M2);
+void launch_contract_tc(const float *Anum, const float *Aden, const float *E, int64_t B, int64_t M2,
+                        int64_t Kp, double *acc_num, double *acc_den, int *status, cudaStream_t st);
+
 // Runs the spectral path on `st`; grows *ws (device) and *pinned (host) as
 // needed.  Returns NCF_OK or an error with *msg set.
 ncf_status run_spectral(const SpectralArgs &a, char **ws, size_t *ws_cap, char **pinned,
