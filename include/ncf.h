@@ -185,6 +185,43 @@ NCF_API ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, cons
                                double *c_out, double *b_out, int64_t *count_out, void *stream);
 
 /*
+ * Plans: the analysis of one batch layout, lag set and options, done once,
+ * for repeated launches that neither synchronise nor allocate, so a launch
+ * can be captured in a CUDA graph.
+ *
+ * ncf_plan_create runs exactly what ncf_corr_batch runs before its kernels
+ * (argument and data validation, statistics read-back, geometry, tables) on
+ * the given data, and allocates the plan's own device memory
+ * (ncf_plan_device_bytes).  Same arguments as ncf_corr_batch; the lags are
+ * copied into the plan.  Returns after synchronising `stream`.
+ *
+ * ncf_plan_execute launches the kernels on `stream` for data laid out like the
+ * data of the plan (same CSR offsets, same lags): statistics and keys are
+ * recomputed from the new t, x (s, y); nothing is allocated or copied from the
+ * host and the host does not wait.  The plan's geometry (period, grid, key
+ * scale) must still fit the new data; device-side checks set bits of a
+ * status word instead of returning an error:
+ *     1  a bounded device wait gave up           4  times beyond the key range
+ *     2  a series outside the periodic domain    8  unsorted / non-finite / constant input
+ * and every output of that launch is NaN (count -1).  ncf_plan_status
+ * synchronises `stream`, stores the word in *flags and returns NCF_OK (0),
+ * NCF_ETIMEOUT (bit 1), NCF_EINVAL (bit 8) or NCF_EUNSUPPORTED (bits 2, 4:
+ * build a new plan).  A plan belongs to the context it was created with and,
+ * like it, is not thread-safe; launches of one plan must not overlap.
+ */
+typedef struct ncf_plan ncf_plan;
+NCF_API ncf_status ncf_plan_create(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                                   const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                                   const double *lags, int64_t K, const ncf_options *opt, void *stream,
+                                   ncf_plan **out);
+NCF_API ncf_status ncf_plan_execute(ncf_plan *plan, const double *t, const double *x, const double *s,
+                                    const double *y, double *c_out, double *b_out, int64_t *count_out,
+                                    void *stream);
+NCF_API ncf_status ncf_plan_status(ncf_plan *plan, void *stream, int32_t *flags);
+NCF_API size_t ncf_plan_device_bytes(const ncf_plan *plan);
+NCF_API void ncf_plan_destroy(ncf_plan *plan);
+
+/*
  * Allocation-free variant of the Gaussian windowed estimator (no counterpart
  * in the paper; it exists for callers that must not allocate device memory
  * while running, such as real-time or embedded pipelines with a fixed memory

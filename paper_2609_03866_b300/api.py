@@ -88,6 +88,17 @@ def lib():
             L.ncf_corr.argtypes = [vp, dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int64, dp, ctypes.c_int64,
                                    ctypes.POINTER(ncf_options), dp, dp, i64p, vp]
             L.ncf_corr.restype = ctypes.c_int
+            L.ncf_plan_create.argtypes = [vp, i64p, dp, dp, i64p, dp, dp, ctypes.c_int64, dp, ctypes.c_int64,
+                                          ctypes.POINTER(ncf_options), vp, ctypes.POINTER(ctypes.c_void_p)]
+            L.ncf_plan_create.restype = ctypes.c_int
+            L.ncf_plan_execute.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64p, vp]
+            L.ncf_plan_execute.restype = ctypes.c_int
+            L.ncf_plan_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
+            L.ncf_plan_status.restype = ctypes.c_int
+            L.ncf_plan_device_bytes.argtypes = [vp]
+            L.ncf_plan_device_bytes.restype = ctypes.c_size_t
+            L.ncf_plan_destroy.argtypes = [vp]
+            L.ncf_plan_destroy.restype = None
             for name in ("ncf_corr_batch", "ncf_corr_batch_host"):
                 fn = getattr(L, name)
                 fn.argtypes = [vp, i64p, dp, dp, i64p, dp, dp, ctypes.c_int64, dp, ctypes.c_int64,
@@ -297,3 +308,66 @@ def corr_batch_host(offs, t, x, lags, kernel="gaussian", h=1.0, offs_y=None, s=N
                                    _ptr(out.get("count")), _stream_handle(stream, dev))
     ctx.check(rc)
     return out
+
+
+class Plan:
+    """A prepared batch evaluation (ncf_plan): built once from data laid out
+    like the data it will be run on; `execute` then only launches kernels on
+    the stream (no host synchronisation, no allocation), so it can be captured
+    in a CUDA graph.  Device-side checks report through `status()`."""
+
+    def __init__(self, offs, t, x, lags, kernel="gaussian", h=1.0, offs_y=None, s=None, y=None,
+                 path="auto", precision="fp64", norm="none", trunc_R=0.0, tol=0.0,
+                 ctx: Context | None = None, stream=None):
+        import torch
+        self.ctx = ctx or default_context()
+        dev = torch.device("cuda", self.ctx.device)
+        t, x, lags = _dev(t, dev), _dev(x, dev), _dev(lags, dev)
+        ox, pox = _host_offs(offs)
+        self.B = ox.size - 1
+        self.K = lags.numel()
+        self.acf = s is None
+        oy, poy = (None, ctypes.c_void_p(0)) if self.acf else _host_offs(offs_y)
+        if not self.acf:
+            s, y = _dev(s, dev), _dev(y, dev)
+        o = make_options(kernel, h, path, precision, norm, trunc_R, tol)
+        self._h = ctypes.c_void_p()
+        rc = lib().ncf_plan_create(self.ctx.handle, pox, _ptr(t), _ptr(x), poy, _ptr(None if self.acf else s),
+                                   _ptr(None if self.acf else y), self.B, _ptr(lags), self.K, ctypes.byref(o),
+                                   _stream_handle(stream, dev), ctypes.byref(self._h))
+        self.ctx.check(rc)
+        self.device = dev
+
+    @property
+    def device_bytes(self) -> int:
+        return int(lib().ncf_plan_device_bytes(self._h))
+
+    def execute(self, t, x, s=None, y=None, out=None, stream=None):
+        import torch
+        if out is None:
+            out = {"c": torch.empty(self.B, self.K, dtype=torch.float64, device=self.device),
+                   "b": torch.empty(self.B, self.K, dtype=torch.float64, device=self.device),
+                   "count": torch.empty(self.B, self.K, dtype=torch.int64, device=self.device)}
+        rc = lib().ncf_plan_execute(self._h, _ptr(t), _ptr(x), _ptr(s), _ptr(y), _ptr(out["c"]),
+                                    _ptr(out.get("b")), _ptr(out.get("count")),
+                                    _stream_handle(stream, self.device))
+        self.ctx.check(rc)
+        return out
+
+    def status(self, stream=None) -> int:
+        """Synchronises the stream; returns the status word of the last launch
+        (0 = valid results)."""
+        f = ctypes.c_int32()
+        lib().ncf_plan_status(self._h, _stream_handle(stream, self.device), ctypes.byref(f))
+        return int(f.value)
+
+    def close(self):
+        if self._h:
+            lib().ncf_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

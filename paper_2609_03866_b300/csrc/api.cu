@@ -213,24 +213,46 @@ FixedScales choose_scales(double m_abs, int64_t n_max) {
     return fs;
 }
 
-}  // namespace
+// ----------------------------------------------------------------------------
+// One evaluation (a batch, a lag set, options): host analysis, device tables
+// and work buffers.  One-shot calls build it in the context's workspace and
+// launch it once; an ncf_plan owns its memory and launches it many times.
+// ----------------------------------------------------------------------------
+struct Eval {
+    bool acf = true, lag0 = false;
+    int64_t B = 0, K = 0;
+    ncf_options opt{};
+    int path = NCF_PATH_AUTO;
+    Side X, Y;
+    std::vector<double> lagv;
+    double max_tau = 0.0, t_abs = 0.0;
+    const double *d_lags = nullptr;  // device lags used by the windowed path
+    int *status = nullptr;           // device status word (plans: guard / bounded waits)
+    // rectangle
+    FixedScales fs{};
+    RectPrepared r_main, r_x, r_y;
+    int64_t *kxT = nullptr, *kxX = nullptr, *kxP = nullptr, *kxC = nullptr;
+    int64_t *kyT = nullptr, *kyX = nullptr, *kyP = nullptr, *kyC = nullptr;
+    unsigned long long *cnt = nullptr, *num = nullptr, *cnt0 = nullptr, *num0 = nullptr;
+    double *scale = nullptr, *zero_lag = nullptr;
+    // Gaussian windowed
+    ScanTile *g_tiles = nullptr, *g_xtiles = nullptr;
+    int64_t g_ntiles = 0, g_nxtiles = 0;
+    double *gnum = nullptr, *gden = nullptr, *gn0 = nullptr, *gd0 = nullptr;
+    unsigned long long *gcnt = nullptr, *gc0 = nullptr;
+    // spectral
+    SpectralPrepared sp;
+    char *spec_ws = nullptr;
+    Side &outer() { return acf ? X : Y; }
+};
 
-// ----------------------------------------------------------------------------
-// The batch driver.  All device pointers come from the caller; offsets are host.
-// ----------------------------------------------------------------------------
-static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const double *t,
-                                  const double *x, const int64_t *offs_y, const double *s,
-                                  const double *y, int64_t B, const double *lags, int64_t K,
-                                  const ncf_options *opt, double *c_out, double *b_out,
-                                  int64_t *count_out, cudaStream_t st) {
-    LaunchScope scope(ctx);
-    ctx->err.clear();
-    // the pinned staging buffer may still feed a copy queued by the previous call
-    if (ctx->staged) NCF_CUDA(cudaEventSynchronize(ctx->staged));
+ncf_status check_args(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                      const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                      const double *lags, int64_t K, const ncf_options *opt, Eval &ev) {
     if (!opt) return fail(ctx, NCF_EINVAL, "options are NULL");
     if (B < 1) return fail(ctx, NCF_EINVAL, "B = %lld (need >= 1)", (long long)B);
     if (K < 1) return fail(ctx, NCF_EINVAL, "K = %lld (need >= 1)", (long long)K);
-    if (!t || !x || !lags || !c_out) return fail(ctx, NCF_EINVAL, "NULL t, x, lags or c_out");
+    if (!t || !x || !lags) return fail(ctx, NCF_EINVAL, "NULL t, x or lags");
     if (!(opt->h > 0.0) || !std::isfinite(opt->h))
         return fail(ctx, NCF_EINVAL, "h = %g (need finite h > 0)", opt->h);
     if (opt->kernel != NCF_GAUSSIAN && opt->kernel != NCF_RECTANGLE)
@@ -254,38 +276,56 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
         return fail(ctx, NCF_EUNSUPPORTED,
                     "rectangle kernel: only the exact windowed scan is provided (its transform "
                     "decays as 1/f, so a truncated spectrum cannot meet the tolerance)");
+    ev.acf = acf;
+    ev.B = B;
+    ev.K = K;
+    ev.opt = *opt;
+    ev.path = path;
+    ev.lag0 = opt->norm == NCF_NORM_LAG0;
+    plan_side(ev.X, offs_x, B);
+    if (!acf) plan_side(ev.Y, offs_y, B);
+    return NCF_OK;
+}
 
-    Side X, Y;
-    X.t = t; X.v = x;
-    plan_side(X, offs_x, B);
-    if (!acf) { Y.t = s; Y.v = y; plan_side(Y, offs_y, B); }
-    Side &O = acf ? X : Y;  // outer side (j): y for a CCF, x itself for an ACF
-    const int tileJ = scan_tile_points();
-    std::vector<ScanTile> tiles = make_tiles(O.offs, B, tileJ);
-    const int64_t n_tiles = (int64_t)tiles.size();
-
-    // ---- pre-statistics workspace ----
-    auto side_bytes = [&](const Side &sd) {
-        return al((B + 1) * 8) * 2 + al(sd.n_chunks * sizeof(ChunkPartial)) + al(B * sizeof(SeriesStats)) +
-               al(sd.n_chunks * 4);
+size_t pre_bytes(const Eval &ev) {
+    auto side = [&](const Side &sd) {
+        return al((ev.B + 1) * 8) * 2 + al(sd.n_chunks * sizeof(ChunkPartial)) +
+               al(ev.B * sizeof(SeriesStats)) + al(sd.n_chunks * 4);
     };
-    size_t need = side_bytes(X) + (acf ? 0 : side_bytes(Y)) + al(n_tiles * sizeof(ScanTile));
-    if ((rc = grow(ctx, &ctx->ws, &ctx->ws_cap, need, st))) return rc;
-    Arena ar{ctx->ws, ctx->ws_cap, 0};
+    return side(ev.X) + (ev.acf ? 0 : side(ev.Y)) + al(4) + al(8) + 1024;
+}
+
+void carve_pre(Eval &ev, char *mem) {
+    Arena ar{mem, SIZE_MAX, 0};
     auto carve = [&](Side &sd) {
-        sd.d_offs = ar.take<int64_t>(B + 1);
-        sd.d_chunk_base = ar.take<int64_t>(B + 1);
+        sd.d_offs = ar.take<int64_t>(ev.B + 1);
+        sd.d_chunk_base = ar.take<int64_t>(ev.B + 1);
         sd.d_part = ar.take<ChunkPartial>(sd.n_chunks);
-        sd.d_stats = ar.take<SeriesStats>(B);
+        sd.d_stats = ar.take<SeriesStats>(ev.B);
         sd.d_cs = ar.take<int32_t>(sd.n_chunks);
     };
-    carve(X);
-    if (!acf) carve(Y);
-    ScanTile *d_tiles = ar.take<ScanTile>(n_tiles);
-    if (!d_tiles) return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
+    carve(ev.X);
+    if (!ev.acf) carve(ev.Y);
+    ev.status = ar.take<int>(1);
+    ev.zero_lag = ar.take<double>(1);
+}
 
-    // ---- pinned staging: uploads then read-backs ----
-    const size_t up_bytes = al((B + 1) * 8) * 4 + al(n_tiles * sizeof(ScanTile));
+void run_stats(Eval &ev, cudaStream_t st) {
+    auto one = [&](Side &sd) {
+        launch_stats_chunks(sd.t, sd.v, sd.d_offs, sd.d_chunk_base, sd.d_cs, sd.n_chunks, kPrepChunk,
+                            sd.d_part, st);
+        launch_stats_finish(sd.t, sd.v, sd.d_offs, sd.d_chunk_base, ev.B, sd.d_part, sd.d_stats, st);
+    };
+    one(ev.X);
+    if (!ev.acf) one(ev.Y);
+}
+
+// Uploads the CSR tables, runs the statistics pass and reads back the
+// per-series statistics and the lags (the one host synchronisation).
+ncf_status analyze(ncf_ctx *ctx, Eval &ev, const double *lags, cudaStream_t st) {
+    const int64_t B = ev.B, K = ev.K;
+    ncf_status rc;
+    const size_t up_bytes = al((B + 1) * 8) * 4;
     const size_t down_bytes = al(B * sizeof(SeriesStats)) * 2 + al(K * 8);
     if ((rc = grow_pinned(ctx, up_bytes + down_bytes, st))) return rc;
     char *hp = ctx->pinned;
@@ -295,212 +335,332 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
         hp += al(bytes);
         return NCF_OK;
     };
-    if ((rc = upload(X.d_offs, X.offs.data(), (B + 1) * 8))) return rc;
-    if ((rc = upload(X.d_chunk_base, X.chunk_base.data(), (B + 1) * 8))) return rc;
-    if (!acf) {
-        if ((rc = upload(Y.d_offs, Y.offs.data(), (B + 1) * 8))) return rc;
-        if ((rc = upload(Y.d_chunk_base, Y.chunk_base.data(), (B + 1) * 8))) return rc;
+    if ((rc = upload(ev.X.d_offs, ev.X.offs.data(), (B + 1) * 8))) return rc;
+    if ((rc = upload(ev.X.d_chunk_base, ev.X.chunk_base.data(), (B + 1) * 8))) return rc;
+    if (!ev.acf) {
+        if ((rc = upload(ev.Y.d_offs, ev.Y.offs.data(), (B + 1) * 8))) return rc;
+        if ((rc = upload(ev.Y.d_chunk_base, ev.Y.chunk_base.data(), (B + 1) * 8))) return rc;
     }
-    if ((rc = upload(d_tiles, tiles.data(), n_tiles * sizeof(ScanTile)))) return rc;
-
-    auto run_stats = [&](Side &sd) {
-        launch_chunk_series(sd.d_chunk_base, B, sd.d_cs, st);
-        launch_stats_chunks(sd.t, sd.v, sd.d_offs, sd.d_chunk_base, sd.d_cs, sd.n_chunks, kPrepChunk,
-                            sd.d_part, st);
-        launch_stats_finish(sd.t, sd.v, sd.d_offs, sd.d_chunk_base, B, sd.d_part, sd.d_stats, st);
-    };
-    run_stats(X);
-    if (!acf) run_stats(Y);
+    launch_chunk_series(ev.X.d_chunk_base, B, ev.X.d_cs, st);
+    if (!ev.acf) launch_chunk_series(ev.Y.d_chunk_base, B, ev.Y.d_cs, st);
+    run_stats(ev, st);
     char *down = ctx->pinned + up_bytes;
-    NCF_CUDA(cudaMemcpyAsync(down, X.d_stats, B * sizeof(SeriesStats), cudaMemcpyDeviceToHost, st));
-    if (!acf)
-        NCF_CUDA(cudaMemcpyAsync(down + al(B * sizeof(SeriesStats)), Y.d_stats, B * sizeof(SeriesStats),
+    NCF_CUDA(cudaMemcpyAsync(down, ev.X.d_stats, B * sizeof(SeriesStats), cudaMemcpyDeviceToHost, st));
+    if (!ev.acf)
+        NCF_CUDA(cudaMemcpyAsync(down + al(B * sizeof(SeriesStats)), ev.Y.d_stats, B * sizeof(SeriesStats),
                                  cudaMemcpyDeviceToHost, st));
     double *h_lags = reinterpret_cast<double *>(down + 2 * al(B * sizeof(SeriesStats)));
     NCF_CUDA(cudaMemcpyAsync(h_lags, lags, K * 8, cudaMemcpyDeviceToHost, st));
     NCF_CUDA(cudaStreamSynchronize(st));
     NCF_CUDA(cudaGetLastError());
-    X.stats.assign(reinterpret_cast<SeriesStats *>(down), reinterpret_cast<SeriesStats *>(down) + B);
-    if (!acf)
-        Y.stats.assign(reinterpret_cast<SeriesStats *>(down + al(B * sizeof(SeriesStats))),
-                       reinterpret_cast<SeriesStats *>(down + al(B * sizeof(SeriesStats))) + B);
-    if ((rc = check_stats(ctx, X, B, acf ? "x" : "x"))) return rc;
-    if (!acf && (rc = check_stats(ctx, Y, B, "y"))) return rc;
-    const std::vector<double> lagv(h_lags, h_lags + K);  // the staging buffer is reused below
-    double max_tau = 0.0;
+    auto *hs = reinterpret_cast<SeriesStats *>(down);
+    ev.X.stats.assign(hs, hs + B);
+    if (!ev.acf) {
+        auto *hy = reinterpret_cast<SeriesStats *>(down + al(B * sizeof(SeriesStats)));
+        ev.Y.stats.assign(hy, hy + B);
+    }
+    if ((rc = check_stats(ctx, ev.X, B, "x"))) return rc;
+    if (!ev.acf && (rc = check_stats(ctx, ev.Y, B, "y"))) return rc;
+    ev.lagv.assign(h_lags, h_lags + K);
+    ev.max_tau = 0.0;
     for (int64_t k = 0; k < K; ++k) {
-        if (!std::isfinite(lagv[k])) return fail(ctx, NCF_ENONFINITE, "lag %lld is not finite", (long long)k);
-        max_tau = std::max(max_tau, std::fabs(lagv[k]));
+        if (!std::isfinite(ev.lagv[k])) return fail(ctx, NCF_ENONFINITE, "lag %lld is not finite", (long long)k);
+        ev.max_tau = std::max(ev.max_tau, std::fabs(ev.lagv[k]));
     }
-    double t_abs = 0.0;
+    ev.t_abs = 0.0;
     for (int64_t b = 0; b < B; ++b) {
-        t_abs = std::max({t_abs, std::fabs(X.stats[b].t_first), std::fabs(X.stats[b].t_last)});
-        if (!acf) t_abs = std::max({t_abs, std::fabs(Y.stats[b].t_first), std::fabs(Y.stats[b].t_last)});
+        ev.t_abs = std::max({ev.t_abs, std::fabs(ev.X.stats[b].t_first), std::fabs(ev.X.stats[b].t_last)});
+        if (!ev.acf)
+            ev.t_abs = std::max({ev.t_abs, std::fabs(ev.Y.stats[b].t_first), std::fabs(ev.Y.stats[b].t_last)});
     }
-    const bool lag0 = opt->norm == NCF_NORM_LAG0;
+    return NCF_OK;
+}
 
-    if (opt->kernel == NCF_RECTANGLE) {
-        // ---- exact rectangle scan on fixed-point keys ----
-        const FixedScales fs = choose_scales(t_abs + max_tau + opt->h + 1.0, std::max(X.n_max, O.n_max));
-        auto key_bytes = [&](const Side &sd) {
-            return al(sd.n_total * 8) * 2 + al((sd.n_total + 1) * 8) + al((sd.n_chunks + 1) * 8);
-        };
-        const int rtile = rect_tile_points();
-        auto ntiles = [&](const std::vector<int64_t> &o) {
-            int64_t n = 0;
-            for (int64_t b = 0; b < B; ++b) n += (o[b + 1] - o[b] + rtile - 1) / rtile;
-            return n;
-        };
-        // independent device and staging regions for the main scan and the two lag-0 scans
-        const size_t rw_main = rect_workspace_bytes(ntiles(O.offs), K);
-        const size_t rw_x = lag0 ? rect_workspace_bytes(ntiles(X.offs), 1) : 0;
-        const size_t rw_y = (lag0 && !acf) ? rect_workspace_bytes(ntiles(Y.offs), 1) : 0;
-        const size_t rs_main = rect_staging_bytes(ntiles(O.offs), K);
-        const size_t rs_x = lag0 ? rect_staging_bytes(ntiles(X.offs), 1) : 0;
-        const size_t rs_y = (lag0 && !acf) ? rect_staging_bytes(ntiles(Y.offs), 1) : 0;
-        size_t need2 = key_bytes(X) + (acf ? 0 : key_bytes(Y)) + al(B * K * 8) * 3 + al(B * 8) * 8 + 1024 +
-                       rw_main + rw_x + rw_y;
-        if ((rc = grow(ctx, &ctx->ws2, &ctx->ws2_cap, need2, st))) return rc;
-        if ((rc = grow_pinned(ctx, rs_main + rs_x + rs_y, st))) return rc;
-        Arena a2{ctx->ws2, ctx->ws2_cap, 0};
-        struct Keys { int64_t *T, *Xq, *P, *cs; };
-        auto keys = [&](Side &sd) {
-            Keys kk{a2.take<int64_t>(sd.n_total), a2.take<int64_t>(sd.n_total),
-                    a2.take<int64_t>(sd.n_total + 1), a2.take<int64_t>(sd.n_chunks + 1)};
-            launch_keys_prefix(sd.t, sd.v, sd.d_offs, sd.d_chunk_base, sd.d_cs, sd.n_chunks, kPrepChunk,
-                               sd.d_stats, fs, kk.T, kk.Xq, kk.P, kk.cs, sd.n_total, st);
-            return kk;
-        };
-        Keys kx = keys(X);
-        Keys ky = acf ? kx : keys(Y);
-        auto *cnt = a2.take<unsigned long long>(B * K);
-        auto *num = a2.take<unsigned long long>(2 * B * K);
-        auto *cnt0 = a2.take<unsigned long long>(2 * B);
-        auto *num0 = a2.take<unsigned long long>(4 * B);
-        auto *scale = a2.take<double>(B);
-        char *rws_main = a2.take<char>(rw_main);
-        char *rws_x = lag0 ? a2.take<char>(rw_x) : nullptr;
-        char *rws_y = (lag0 && !acf) ? a2.take<char>(rw_y) : nullptr;
-        if (!kx.cs || !ky.cs || !scale || !rws_main || (lag0 && !rws_x) || (lag0 && !acf && !rws_y))
-            return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
-        NCF_CUDA(cudaMemsetAsync(cnt, 0, B * K * 8, st));
-        NCF_CUDA(cudaMemsetAsync(num, 0, 2 * B * K * 8, st));
-        const int eps = acf ? +1 : -1;
-        std::string msg;
-        RectArgs ra{kx.T, kx.P, X.t, X.d_offs, ky.T, ky.Xq, O.t, &O.offs, B, K, lagv.data(), eps,
-                    opt->h, fs, cnt, num};
-        if ((rc = run_rect_scan(ra, rws_main, rw_main, ctx->pinned, rs_main, st, &msg)))
-            return fail(ctx, rc, "%s", msg.c_str());
-        const double inv_v2 = std::ldexp(1.0, -2 * fs.p);
-        if (lag0) {
-            // ACF of each side at lag 0 (Algorithms 4 and 10): scale = c_xx(0) or sqrt(c_xx(0) c_yy(0))
-            static const double zero = 0.0;
-            NCF_CUDA(cudaMemsetAsync(cnt0, 0, 2 * B * 8, st));
-            NCF_CUDA(cudaMemsetAsync(num0, 0, 4 * B * 8, st));
-            RectArgs rx{kx.T, kx.P, X.t, X.d_offs, kx.T, kx.Xq, X.t, &X.offs, B, 1, &zero, +1, opt->h, fs,
-                        cnt0, num0};
-            if ((rc = run_rect_scan(rx, rws_x, rw_x, ctx->pinned + rs_main, rs_x, st, &msg)))
-                return fail(ctx, rc, "%s", msg.c_str());
-            if (!acf) {
-                RectArgs ry{ky.T, ky.P, Y.t, Y.d_offs, ky.T, ky.Xq, Y.t, &Y.offs, B, 1, &zero, +1, opt->h,
-                            fs, cnt0 + B, num0 + 2 * B};
-                if ((rc = run_rect_scan(ry, rws_y, rw_y, ctx->pinned + rs_main + rs_x, rs_y, st, &msg)))
-                    return fail(ctx, rc, "%s", msg.c_str());
-            }
-            launch_lag0_scale_rect(cnt0, num0, acf ? nullptr : cnt0 + B, acf ? nullptr : num0 + 2 * B,
-                                   B, inv_v2, scale, st);
-        }
-        NCF_CUDA(cudaEventRecord(ctx->staged, st));
-        launch_finish_rect(cnt, num, B, K, inv_v2, lag0 ? scale : nullptr, c_out, b_out, count_out, st);
-        NCF_CUDA(cudaGetLastError());
-        return NCF_OK;
-    }
-
-    if (path == NCF_PATH_WINDOWED) {
-        // ---- Gaussian windowed FP64 scan ----
-        const double R = opt->trunc_R > 0.0 ? opt->trunc_R : 8.0;
-        const double Rh = R * opt->h;
-        size_t need2 = al(B * K * 8) * 3 + al(B * 8) * 8 + 1024;
-        if (lag0) need2 += al((X.n_total / tileJ + B) * sizeof(ScanTile)) + 256;
-        if ((rc = grow(ctx, &ctx->ws2, &ctx->ws2_cap, need2, st))) return rc;
-        Arena a2{ctx->ws2, ctx->ws2_cap, 0};
-        auto *num = a2.take<double>(B * K);
-        auto *den = a2.take<double>(B * K);
-        auto *cnt = a2.take<unsigned long long>(B * K);
-        auto *zero_lag = a2.take<double>(1);
-        auto *n0 = a2.take<double>(2 * B);
-        auto *d0 = a2.take<double>(2 * B);
-        auto *c0 = a2.take<unsigned long long>(2 * B);
-        auto *scale = a2.take<double>(B);
-        if (!scale) return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
-        NCF_CUDA(cudaMemsetAsync(num, 0, B * K * 8, st));
-        NCF_CUDA(cudaMemsetAsync(den, 0, B * K * 8, st));
-        NCF_CUDA(cudaMemsetAsync(cnt, 0, B * K * 8, st));
-        const int eps = acf ? +1 : -1;
-        launch_gauss_window(X.t, X.v, X.d_offs, X.d_stats, O.t, O.v, O.d_stats, d_tiles, n_tiles, lags, K,
-                            eps, opt->h, Rh, num, den, cnt, st);
-        if (lag0) {
-            NCF_CUDA(cudaMemsetAsync(zero_lag, 0, 8, st));
-            NCF_CUDA(cudaMemsetAsync(n0, 0, 2 * B * 8, st));
-            NCF_CUDA(cudaMemsetAsync(d0, 0, 2 * B * 8, st));
-            NCF_CUDA(cudaMemsetAsync(c0, 0, 2 * B * 8, st));
-            ScanTile *tx_tiles = d_tiles;
-            int64_t ntx = n_tiles;
-            if (!acf) {
-                std::vector<ScanTile> tt = make_tiles(X.offs, B, tileJ);
-                ntx = (int64_t)tt.size();
-                tx_tiles = a2.take<ScanTile>(ntx);
-                if (!tx_tiles) return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
-                if ((rc = grow_pinned(ctx, ntx * sizeof(ScanTile), st))) return rc;
-                std::memcpy(ctx->pinned, tt.data(), ntx * sizeof(ScanTile));
-                NCF_CUDA(cudaMemcpyAsync(tx_tiles, ctx->pinned, ntx * sizeof(ScanTile),
-                                         cudaMemcpyHostToDevice, st));
-                NCF_CUDA(cudaEventRecord(ctx->staged, st));
-            }
-            launch_gauss_window(X.t, X.v, X.d_offs, X.d_stats, X.t, X.v, X.d_stats, tx_tiles, ntx, zero_lag,
-                                1, +1, opt->h, Rh, n0, d0, c0, st);
-            if (!acf)
-                launch_gauss_window(Y.t, Y.v, Y.d_offs, Y.d_stats, Y.t, Y.v, Y.d_stats, d_tiles, n_tiles,
-                                    zero_lag, 1, +1, opt->h, Rh, n0 + B, d0 + B, c0 + B, st);
-            launch_lag0_scale_gauss(n0, d0, acf ? nullptr : n0 + B, acf ? nullptr : d0 + B, B, scale, st);
-        }
-        launch_finish_gauss(num, den, cnt, B, K, lag0 ? scale : nullptr, c_out, b_out, count_out, st);
-        NCF_CUDA(cudaGetLastError());
-        return NCF_OK;
-    }
-
-    // ---- Gaussian spectral path ----
+SpectralArgs spectral_args(const Eval &ev, double *c_out, double *b_out, int64_t *count_out) {
     SpectralArgs sa;
-    sa.acf = acf;
-    sa.B = B;
-    sa.K = K;
-    sa.h = opt->h;
-    sa.fp32 = opt->precision == NCF_FP32;
-    sa.tol = opt->tol > 0.0 ? opt->tol : (sa.fp32 ? 1e-7 : 1e-14);
-    sa.max_tau = max_tau;
-    sa.lag0 = lag0;
-    sa.lags = lags;
-    sa.h_lags = lagv.data();
+    sa.acf = ev.acf;
+    sa.B = ev.B;
+    sa.K = ev.K;
+    sa.h = ev.opt.h;
+    sa.fp32 = ev.opt.precision == NCF_FP32;
+    sa.tol = ev.opt.tol > 0.0 ? ev.opt.tol : (sa.fp32 ? 1e-7 : 1e-14);
+    sa.max_tau = ev.max_tau;
+    sa.lag0 = ev.lag0;
+    sa.h_lags = ev.lagv.data();
+    const Side &X = ev.X, &Y = ev.Y;
     sa.x = {X.t, X.v, X.d_offs, X.d_stats, X.offs.data(), X.stats.data(), X.n_total, X.n_max,
             X.d_chunk_base, X.n_chunks, X.d_cs};
-    if (!acf)
+    if (!ev.acf)
         sa.y = {Y.t, Y.v, Y.d_offs, Y.d_stats, Y.offs.data(), Y.stats.data(), Y.n_total, Y.n_max,
                 Y.d_chunk_base, Y.n_chunks, Y.d_cs};
     sa.c_out = c_out;
     sa.b_out = b_out;
     sa.count_out = count_out;
-    sa.sm_count = ctx->sm_count;
+    return sa;
+}
+
+size_t key_bytes(const Side &sd) {
+    return al(sd.n_total * 8) * 2 + al((sd.n_total + 1) * 8) + al((sd.n_chunks + 1) * 8);
+}
+
+// Sizes of the path-specific device memory and of its host staging.
+ncf_status main_bytes(ncf_ctx *ctx, Eval &ev, size_t *dev, size_t *pin) {
+    const int64_t B = ev.B, K = ev.K;
+    if (ev.opt.kernel == NCF_RECTANGLE) {
+        const Side &O = ev.outer();
+        const size_t rw = rect_workspace_bytes(rect_tiles_of(O.offs, B), K);
+        const size_t rwx = ev.lag0 ? rect_workspace_bytes(rect_tiles_of(ev.X.offs, B), 1) : 0;
+        const size_t rwy = (ev.lag0 && !ev.acf) ? rect_workspace_bytes(rect_tiles_of(ev.Y.offs, B), 1) : 0;
+        *dev = key_bytes(ev.X) + (ev.acf ? 0 : key_bytes(ev.Y)) + al(B * K * 8) * 3 + al(B * 8) * 8 + 1024 +
+               rw + rwx + rwy;
+        *pin = rect_staging_bytes(rect_tiles_of(O.offs, B), K) +
+               (ev.lag0 ? rect_staging_bytes(rect_tiles_of(ev.X.offs, B), 1) : 0) +
+               ((ev.lag0 && !ev.acf) ? rect_staging_bytes(rect_tiles_of(ev.Y.offs, B), 1) : 0);
+        return NCF_OK;
+    }
+    if (ev.path == NCF_PATH_WINDOWED) {
+        const int tj = scan_tile_points();
+        const int64_t nt = (int64_t)make_tiles(ev.outer().offs, B, tj).size();
+        const int64_t nxt = (ev.lag0 && !ev.acf) ? (int64_t)make_tiles(ev.X.offs, B, tj).size() : 0;
+        *dev = al(B * K * 8) * 3 + al(B * 8) * 8 + al(nt * sizeof(ScanTile)) + al(nxt * sizeof(ScanTile)) +
+               al(K * 8) + 1024;
+        *pin = al(nt * sizeof(ScanTile)) + al(nxt * sizeof(ScanTile)) + 256;
+        return NCF_OK;
+    }
     std::string msg;
-    SpectralGeometry geom{0.0, 0, 0, 0};
-    rc = run_spectral(sa, &ctx->ws2, &ctx->ws2_cap, &ctx->pinned, &ctx->pinned_cap, st, &msg, &geom);
+    size_t ws = 0, pb = 0;
+    ncf_status rc = spectral_plan(spectral_args(ev, nullptr, nullptr, nullptr), &ev.sp, &ws, &pb, &msg);
     if (rc) return fail(ctx, rc, "%s", msg.c_str());
-    ctx->plan = ncf_plan_info{geom.L, geom.M, geom.nf, geom.W, B, K};
-    NCF_CUDA(cudaEventRecord(ctx->staged, st));
+    *dev = ws + al(K * 8) + 1024;
+    *pin = pb;
+    return NCF_OK;
+}
+
+// Carves the path-specific memory and uploads / builds its tables.
+ncf_status prepare(ncf_ctx *ctx, Eval &ev, char *mem, size_t cap, char *pinned, size_t pin_cap,
+                   const double *lags, cudaStream_t st) {
+    const int64_t B = ev.B, K = ev.K;
+    Arena a2{mem, cap, 0};
+    std::string msg;
+    ncf_status rc;
+    // a private copy of the lags for the windowed path (plans outlive the caller's array)
+    double *d_lags = a2.take<double>(K);
+    if (!d_lags) return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
+    NCF_CUDA(cudaMemcpyAsync(d_lags, lags, K * 8, cudaMemcpyDeviceToDevice, st));
+    ev.d_lags = d_lags;
+    if (ev.opt.kernel == NCF_RECTANGLE) {
+        Side &X = ev.X, &O = ev.outer();
+        ev.fs = choose_scales(ev.t_abs + ev.max_tau + ev.opt.h + 1.0, std::max(X.n_max, O.n_max));
+        auto keys = [&](const Side &sd, int64_t *&T, int64_t *&Xq, int64_t *&P, int64_t *&C) {
+            T = a2.take<int64_t>(sd.n_total);
+            Xq = a2.take<int64_t>(sd.n_total);
+            P = a2.take<int64_t>(sd.n_total + 1);
+            C = a2.take<int64_t>(sd.n_chunks + 1);
+        };
+        keys(X, ev.kxT, ev.kxX, ev.kxP, ev.kxC);
+        if (ev.acf) {
+            ev.kyT = ev.kxT; ev.kyX = ev.kxX; ev.kyP = ev.kxP; ev.kyC = ev.kxC;
+        } else {
+            keys(ev.Y, ev.kyT, ev.kyX, ev.kyP, ev.kyC);
+        }
+        ev.cnt = a2.take<unsigned long long>(B * K);
+        ev.num = a2.take<unsigned long long>(2 * B * K);
+        ev.cnt0 = a2.take<unsigned long long>(2 * B);
+        ev.num0 = a2.take<unsigned long long>(4 * B);
+        ev.scale = a2.take<double>(B);
+        const size_t rw = rect_workspace_bytes(rect_tiles_of(O.offs, B), K);
+        char *rws = a2.take<char>(rw);
+        if (!rws || !ev.scale) return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
+        const int eps = ev.acf ? +1 : -1;
+        RectArgs ra{ev.kxT, ev.kxP, X.t, X.d_offs, ev.kyT, ev.kyX, O.t, &O.offs, B, K, ev.lagv.data(), eps,
+                    ev.opt.h, ev.fs, ev.cnt, ev.num};
+        size_t poff = 0;
+        const size_t rs = rect_staging_bytes(rect_tiles_of(O.offs, B), K);
+        if ((rc = rect_prepare(ra, rws, rw, pinned, rs, st, &ev.r_main, &msg))) return fail(ctx, rc, "%s", msg.c_str());
+        poff += rs;
+        if (ev.lag0) {
+            static const double zero = 0.0;
+            const size_t rwx = rect_workspace_bytes(rect_tiles_of(X.offs, B), 1);
+            const size_t rsx = rect_staging_bytes(rect_tiles_of(X.offs, B), 1);
+            char *rx = a2.take<char>(rwx);
+            if (!rx) return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
+            RectArgs ax{ev.kxT, ev.kxP, X.t, X.d_offs, ev.kxT, ev.kxX, X.t, &X.offs, B, 1, &zero, +1, ev.opt.h,
+                        ev.fs, ev.cnt0, ev.num0};
+            if ((rc = rect_prepare(ax, rx, rwx, pinned + poff, rsx, st, &ev.r_x, &msg)))
+                return fail(ctx, rc, "%s", msg.c_str());
+            poff += rsx;
+            if (!ev.acf) {
+                Side &Y = ev.Y;
+                const size_t rwy = rect_workspace_bytes(rect_tiles_of(Y.offs, B), 1);
+                const size_t rsy = rect_staging_bytes(rect_tiles_of(Y.offs, B), 1);
+                char *ry = a2.take<char>(rwy);
+                if (!ry) return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
+                RectArgs ay{ev.kyT, ev.kyP, Y.t, Y.d_offs, ev.kyT, ev.kyX, Y.t, &Y.offs, B, 1, &zero, +1,
+                            ev.opt.h, ev.fs, ev.cnt0 + B, ev.num0 + 2 * B};
+                if ((rc = rect_prepare(ay, ry, rwy, pinned + poff, rsy, st, &ev.r_y, &msg)))
+                    return fail(ctx, rc, "%s", msg.c_str());
+            }
+        }
+        (void)pin_cap;
+        return NCF_OK;
+    }
+    if (ev.path == NCF_PATH_WINDOWED) {
+        const int tj = scan_tile_points();
+        std::vector<ScanTile> t1 = make_tiles(ev.outer().offs, B, tj);
+        ev.g_ntiles = (int64_t)t1.size();
+        ev.g_tiles = a2.take<ScanTile>(ev.g_ntiles);
+        ev.gnum = a2.take<double>(B * K);
+        ev.gden = a2.take<double>(B * K);
+        ev.gcnt = a2.take<unsigned long long>(B * K);
+        ev.gn0 = a2.take<double>(2 * B);
+        ev.gd0 = a2.take<double>(2 * B);
+        ev.gc0 = a2.take<unsigned long long>(2 * B);
+        ev.scale = a2.take<double>(B);
+        size_t off = 0;
+        std::memcpy(pinned + off, t1.data(), t1.size() * sizeof(ScanTile));
+        NCF_CUDA(cudaMemcpyAsync(ev.g_tiles, pinned + off, t1.size() * sizeof(ScanTile), cudaMemcpyHostToDevice, st));
+        off += al(t1.size() * sizeof(ScanTile));
+        if (ev.lag0 && !ev.acf) {
+            std::vector<ScanTile> t2 = make_tiles(ev.X.offs, B, tj);
+            ev.g_nxtiles = (int64_t)t2.size();
+            ev.g_xtiles = a2.take<ScanTile>(ev.g_nxtiles);
+            if (!ev.g_xtiles) return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
+            std::memcpy(pinned + off, t2.data(), t2.size() * sizeof(ScanTile));
+            NCF_CUDA(cudaMemcpyAsync(ev.g_xtiles, pinned + off, t2.size() * sizeof(ScanTile), cudaMemcpyHostToDevice,
+                                     st));
+        } else {
+            ev.g_xtiles = ev.g_tiles;
+            ev.g_nxtiles = ev.g_ntiles;
+        }
+        if (!ev.scale) return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
+        return NCF_OK;
+    }
+    ev.spec_ws = mem + a2.used;  // the spectral workspace starts here (256-aligned)
+    spectral_prepare(ev.sp, ev.spec_ws, pinned, st);
+    ctx->plan = ncf_plan_info{ev.sp.L, ev.sp.M, ev.sp.nf, ev.sp.W, B, K};
+    return NCF_OK;
+}
+
+// The per-data kernels of an evaluation; `stats_fresh` skips the statistics
+// pass when `analyze` has just run it on the same data.
+ncf_status launch(ncf_ctx *ctx, Eval &ev, bool stats_fresh, bool guard, double *c_out, double *b_out,
+                  int64_t *count_out, cudaStream_t st) {
+    const int64_t B = ev.B, K = ev.K;
+    std::string msg;
+    ncf_status rc;
+    NCF_CUDA(cudaMemsetAsync(ev.status, 0, sizeof(int), st));
+    if (!stats_fresh) run_stats(ev, st);
+    if (guard) launch_stats_guard(ev.X.d_stats, ev.acf ? nullptr : ev.Y.d_stats, B, ev.status, st);
+    Side &X = ev.X, &O = ev.outer();
+    if (ev.opt.kernel == NCF_RECTANGLE) {
+        launch_keys_prefix(X.t, X.v, X.d_offs, X.d_chunk_base, X.d_cs, X.n_chunks, kPrepChunk, X.d_stats, ev.fs,
+                           ev.kxT, ev.kxX, ev.kxP, ev.kxC, X.n_total, st);
+        if (!ev.acf)
+            launch_keys_prefix(ev.Y.t, ev.Y.v, ev.Y.d_offs, ev.Y.d_chunk_base, ev.Y.d_cs, ev.Y.n_chunks, kPrepChunk,
+                               ev.Y.d_stats, ev.fs, ev.kyT, ev.kyX, ev.kyP, ev.kyC, ev.Y.n_total, st);
+        if (guard) launch_keys_guard(ev.X.d_stats, ev.acf ? nullptr : ev.Y.d_stats, B, ev.t_abs, ev.status, st);
+        NCF_CUDA(cudaMemsetAsync(ev.cnt, 0, B * K * 8, st));
+        NCF_CUDA(cudaMemsetAsync(ev.num, 0, 2 * B * K * 8, st));
+        const int eps = ev.acf ? +1 : -1;
+        RectArgs ra{ev.kxT, ev.kxP, X.t, X.d_offs, ev.kyT, ev.kyX, O.t, &O.offs, B, K, ev.lagv.data(), eps,
+                    ev.opt.h, ev.fs, ev.cnt, ev.num};
+        if ((rc = rect_launch(ra, ev.r_main, st, &msg))) return fail(ctx, rc, "%s", msg.c_str());
+        const double inv_v2 = std::ldexp(1.0, -2 * ev.fs.p);
+        if (ev.lag0) {
+            NCF_CUDA(cudaMemsetAsync(ev.cnt0, 0, 2 * B * 8, st));
+            NCF_CUDA(cudaMemsetAsync(ev.num0, 0, 4 * B * 8, st));
+            static const double zero = 0.0;
+            RectArgs ax{ev.kxT, ev.kxP, X.t, X.d_offs, ev.kxT, ev.kxX, X.t, &X.offs, B, 1, &zero, +1, ev.opt.h,
+                        ev.fs, ev.cnt0, ev.num0};
+            if ((rc = rect_launch(ax, ev.r_x, st, &msg))) return fail(ctx, rc, "%s", msg.c_str());
+            if (!ev.acf) {
+                Side &Y = ev.Y;
+                RectArgs ay{ev.kyT, ev.kyP, Y.t, Y.d_offs, ev.kyT, ev.kyX, Y.t, &Y.offs, B, 1, &zero, +1,
+                            ev.opt.h, ev.fs, ev.cnt0 + B, ev.num0 + 2 * B};
+                if ((rc = rect_launch(ay, ev.r_y, st, &msg))) return fail(ctx, rc, "%s", msg.c_str());
+            }
+            launch_lag0_scale_rect(ev.cnt0, ev.num0, ev.acf ? nullptr : ev.cnt0 + B,
+                                   ev.acf ? nullptr : ev.num0 + 2 * B, B, inv_v2, ev.scale, st);
+        }
+        launch_finish_rect(ev.cnt, ev.num, B, K, inv_v2, ev.lag0 ? ev.scale : nullptr, ev.status, c_out, b_out,
+                           count_out, st);
+    } else if (ev.path == NCF_PATH_WINDOWED) {
+        const double R = ev.opt.trunc_R > 0.0 ? ev.opt.trunc_R : 8.0;
+        const double Rh = R * ev.opt.h;
+        NCF_CUDA(cudaMemsetAsync(ev.gnum, 0, B * K * 8, st));
+        NCF_CUDA(cudaMemsetAsync(ev.gden, 0, B * K * 8, st));
+        NCF_CUDA(cudaMemsetAsync(ev.gcnt, 0, B * K * 8, st));
+        const int eps = ev.acf ? +1 : -1;
+        launch_gauss_window(X.t, X.v, X.d_offs, X.d_stats, O.t, O.v, O.d_stats, ev.g_tiles, ev.g_ntiles, ev.d_lags,
+                            K, eps, ev.opt.h, Rh, ev.gnum, ev.gden, ev.gcnt, st);
+        if (ev.lag0) {
+            NCF_CUDA(cudaMemsetAsync(ev.zero_lag, 0, 8, st));
+            NCF_CUDA(cudaMemsetAsync(ev.gn0, 0, 2 * B * 8, st));
+            NCF_CUDA(cudaMemsetAsync(ev.gd0, 0, 2 * B * 8, st));
+            NCF_CUDA(cudaMemsetAsync(ev.gc0, 0, 2 * B * 8, st));
+            launch_gauss_window(X.t, X.v, X.d_offs, X.d_stats, X.t, X.v, X.d_stats, ev.g_xtiles, ev.g_nxtiles,
+                                ev.zero_lag, 1, +1, ev.opt.h, Rh, ev.gn0, ev.gd0, ev.gc0, st);
+            if (!ev.acf)
+                launch_gauss_window(ev.Y.t, ev.Y.v, ev.Y.d_offs, ev.Y.d_stats, ev.Y.t, ev.Y.v, ev.Y.d_stats,
+                                    ev.g_tiles, ev.g_ntiles, ev.zero_lag, 1, +1, ev.opt.h, Rh, ev.gn0 + B,
+                                    ev.gd0 + B, ev.gc0 + B, st);
+            launch_lag0_scale_gauss(ev.gn0, ev.gd0, ev.acf ? nullptr : ev.gn0 + B, ev.acf ? nullptr : ev.gd0 + B, B,
+                                    ev.scale, st);
+        }
+        launch_finish_gauss(ev.gnum, ev.gden, ev.gcnt, B, K, ev.lag0 ? ev.scale : nullptr, ev.status, c_out, b_out,
+                            count_out, st);
+    } else {
+        SpectralArgs sa = spectral_args(ev, c_out, b_out, count_out);
+        if (guard) spectral_guard(sa, ev.sp, ev.spec_ws, ev.status, st);
+        if ((rc = spectral_launch(sa, ev.sp, ev.spec_ws, ev.status, st, &msg))) return fail(ctx, rc, "%s", msg.c_str());
+    }
     NCF_CUDA(cudaGetLastError());
     return NCF_OK;
 }
 
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// The batch driver.  All device pointers come from the caller; offsets are host.
+// ----------------------------------------------------------------------------
+static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const double *t,
+                                  const double *x, const int64_t *offs_y, const double *s,
+                                  const double *y, int64_t B, const double *lags, int64_t K,
+                                  const ncf_options *opt, double *c_out, double *b_out,
+                                  int64_t *count_out, cudaStream_t st) {
+    LaunchScope scope(ctx);
+    ctx->err.clear();
+    // the pinned staging buffer may still feed a copy queued by the previous call
+    if (ctx->staged) NCF_CUDA(cudaEventSynchronize(ctx->staged));
+    Eval ev;
+    ncf_status rc = check_args(ctx, offs_x, t, x, offs_y, s, y, B, lags, K, opt, ev);
+    if (rc) return rc;
+    if (!c_out) return fail(ctx, NCF_EINVAL, "c_out is NULL");
+    ev.X.t = t; ev.X.v = x;
+    if (!ev.acf) { ev.Y.t = s; ev.Y.v = y; }
+    if ((rc = grow(ctx, &ctx->ws, &ctx->ws_cap, pre_bytes(ev), st))) return rc;
+    carve_pre(ev, ctx->ws);
+    if ((rc = analyze(ctx, ev, lags, st))) return rc;
+    size_t dev = 0, pin = 0;
+    if ((rc = main_bytes(ctx, ev, &dev, &pin))) return rc;
+    if ((rc = grow(ctx, &ctx->ws2, &ctx->ws2_cap, dev, st))) return rc;
+    if ((rc = grow_pinned(ctx, pin, st))) return rc;
+    if ((rc = prepare(ctx, ev, ctx->ws2, ctx->ws2_cap, ctx->pinned, ctx->pinned_cap, lags, st))) return rc;
+    NCF_CUDA(cudaEventRecord(ctx->staged, st));
+    return launch(ctx, ev, /*stats_fresh=*/true, /*guard=*/false, c_out, b_out, count_out, st);
+}
+
 }  // namespace ncf
+
+// ----------------------------------------------------------------------------
+// Plans: the analysis and tables of one evaluation, kept for repeated launches
+// ----------------------------------------------------------------------------
+struct ncf_plan {
+    ncf_ctx *ctx = nullptr;
+    ncf::Eval ev;
+    char *pre = nullptr, *main = nullptr;
+    size_t pre_cap = 0, main_cap = 0;
+};
 
 // ----------------------------------------------------------------------------
 // extern "C" entry points
@@ -689,6 +849,93 @@ ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, const double
         return NCF_ECUDA;
     }
     return NCF_OK;
+}
+
+ncf_status ncf_plan_create(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                           const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                           const double *lags, int64_t K, const ncf_options *opt, void *stream,
+                           ncf_plan **out) {
+    using namespace ncf;
+    if (!ctx || !out) return NCF_EINVAL;
+    *out = nullptr;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return NCF_ECUDA;
+    LaunchScope scope(ctx);
+    ctx->err.clear();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ctx->staged) NCF_CUDA(cudaEventSynchronize(ctx->staged));
+    ncf_plan *p = new ncf_plan();
+    p->ctx = ctx;
+    Eval &ev = p->ev;
+    auto bail = [&](ncf_status rc) {
+        if (p->pre) cudaFree(p->pre);
+        if (p->main) cudaFree(p->main);
+        delete p;
+        return rc;
+    };
+    ncf_status rc = check_args(ctx, offs_x, t, x, offs_y, s, y, B, lags, K, opt, ev);
+    if (rc) return bail(rc);
+    ev.X.t = t; ev.X.v = x;
+    if (!ev.acf) { ev.Y.t = s; ev.Y.v = y; }
+    p->pre_cap = pre_bytes(ev);
+    if (cudaMalloc(&p->pre, p->pre_cap) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(ctx, NCF_ENOMEM, "cudaMalloc of %zu bytes failed", p->pre_cap));
+    }
+    carve_pre(ev, p->pre);
+    if ((rc = analyze(ctx, ev, lags, st))) return bail(rc);
+    size_t dev = 0, pin = 0;
+    if ((rc = main_bytes(ctx, ev, &dev, &pin))) return bail(rc);
+    p->main_cap = dev;
+    if (cudaMalloc(&p->main, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(ctx, NCF_ENOMEM, "cudaMalloc of %zu bytes failed", dev));
+    }
+    if ((rc = grow_pinned(ctx, pin, st))) return bail(rc);
+    if ((rc = prepare(ctx, ev, p->main, dev, ctx->pinned, ctx->pinned_cap, lags, st))) return bail(rc);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(ctx, NCF_ECUDA, "plan set-up failed"));
+    *out = p;
+    return NCF_OK;
+}
+
+ncf_status ncf_plan_execute(ncf_plan *plan, const double *t, const double *x, const double *s,
+                            const double *y, double *c_out, double *b_out, int64_t *count_out,
+                            void *stream) {
+    using namespace ncf;
+    if (!plan || !t || !x || !c_out) return NCF_EINVAL;
+    ncf_ctx *ctx = plan->ctx;
+    Eval &ev = plan->ev;
+    if (!ev.acf && (!s || !y)) return fail(ctx, NCF_EINVAL, "this plan is a CCF: s and y are needed");
+    LaunchScope scope(ctx);
+    ev.X.t = t; ev.X.v = x;
+    if (!ev.acf) { ev.Y.t = s; ev.Y.v = y; }
+    return launch(ctx, ev, /*stats_fresh=*/false, /*guard=*/true, c_out, b_out, count_out, (cudaStream_t)stream);
+}
+
+ncf_status ncf_plan_status(ncf_plan *plan, void *stream, int32_t *flags) {
+    if (!plan || !flags) return NCF_EINVAL;
+    int v = 0;
+    if (cudaMemcpyAsync(&v, plan->ev.status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return NCF_ECUDA;
+    }
+    *flags = v;
+    if (v & ncf::STATUS_TIMEOUT) return NCF_ETIMEOUT;
+    if (v & ncf::STATUS_INPUT) return NCF_EINVAL;
+    if (v != 0) return NCF_EUNSUPPORTED;
+    return NCF_OK;
+}
+
+size_t ncf_plan_device_bytes(const ncf_plan *plan) { return plan ? plan->pre_cap + plan->main_cap : 0; }
+
+void ncf_plan_destroy(ncf_plan *plan) {
+    if (!plan) return;
+    cudaSetDevice(plan->ctx->device);
+    cudaDeviceSynchronize();
+    if (plan->pre) cudaFree(plan->pre);
+    if (plan->main) cudaFree(plan->main);
+    delete plan;
 }
 
 }  // extern "C"

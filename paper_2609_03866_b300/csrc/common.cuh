@@ -26,6 +26,14 @@ struct SeriesStats {
 };
 enum : int32_t { STAT_UNSORTED = 1, STAT_NONFINITE = 2, STAT_DEGENERATE = 4 };
 
+// Bits of the device status word of an evaluation (reported by ncf_plan_status).
+enum : int32_t {
+    STATUS_TIMEOUT = 1,  // a bounded device-side wait gave up
+    STATUS_DOMAIN = 2,   // a series no longer fits the plan's periodic domain
+    STATUS_RANGE = 4,    // times beyond the plan's fixed-point key range
+    STATUS_INPUT = 8     // unsorted, non-finite or zero-variance input
+};
+
 // Partial sums of one chunk of one series (statistics pass).
 struct ChunkPartial {
     double s1, s2;    // sum of (x - x_ref), sum of (x - x_ref)^2
@@ -67,6 +75,12 @@ void launch_stats_chunks(const double *t, const double *x, const int64_t *offs,
 void launch_stats_finish(const double *t, const double *x, const int64_t *offs,
                          const int64_t *chunk_base, int64_t B, const ChunkPartial *part,
                          SeriesStats *stats, cudaStream_t st);
+// Plan guards: set STATUS_INPUT if any series' statistics carry a flag, and
+// STATUS_RANGE if a time magnitude exceeds t_abs (the key scale's bound).
+void launch_stats_guard(const SeriesStats *sx, const SeriesStats *sy, int64_t B, int *status,
+                        cudaStream_t st);
+void launch_keys_guard(const SeriesStats *sx, const SeriesStats *sy, int64_t B, double t_abs, int *status,
+                       cudaStream_t st);
 // Fixed-point keys and the exclusive prefix sum of the quantised standardised values.
 // Writes Tk[total], Xq[total] and P[total + 1].
 void launch_keys_prefix(const double *t, const double *x, const int64_t *offs,
@@ -94,11 +108,21 @@ struct RectArgs {
     FixedScales fs;
     unsigned long long *cnt, *num128;
 };
+// Device tables of one rectangle scan (tiles, sorted lags, lag groups).
+struct RectPrepared {
+    int64_t n_tiles = 0, G = 0;
+    void *tiles = nullptr, *ranges = nullptr;
+    double *slags = nullptr;
+    int64_t *dls = nullptr, *dus = nullptr, *gmin = nullptr, *gmax = nullptr;
+    int32_t *perm = nullptr;
+};
 int rect_tile_points();
+int64_t rect_tiles_of(const std::vector<int64_t> &offs, int64_t B);
 size_t rect_workspace_bytes(int64_t n_tiles, int64_t K);
 size_t rect_staging_bytes(int64_t n_tiles, int64_t K);
-ncf_status run_rect_scan(const RectArgs &a, char *ws, size_t ws_cap, char *pinned, size_t pinned_cap,
-                         cudaStream_t st, std::string *msg);
+ncf_status rect_prepare(const RectArgs &a, char *ws, size_t ws_cap, char *pinned, size_t pinned_cap,
+                        cudaStream_t st, RectPrepared *out, std::string *msg);
+ncf_status rect_launch(const RectArgs &a, const RectPrepared &r, cudaStream_t st, std::string *msg);
 // Gaussian windowed FP64 scan (Algorithms 5 and 7 with window R h).
 void launch_gauss_window(const double *tx, const double *x, const int64_t *offs_x,
                          const SeriesStats *stx, const double *sy, const double *y,
@@ -115,12 +139,14 @@ void launch_lag0_scale_rect(const unsigned long long *cnt_x, const unsigned long
 void launch_lag0_scale_gauss(const double *num_x, const double *den_x, const double *num_y,
                              const double *den_y, int64_t B, double *scale, cudaStream_t st);
 // c = N / max(B, 1e-16) from the scan accumulators; optional lag-0 scaling.
+// status (nullable): a nonzero status word turns every result into NaN
+// (count -1): a device-side check of an executed plan failed.
 void launch_finish_rect(const unsigned long long *cnt, const unsigned long long *num128,
-                        int64_t B, int64_t K, double inv_v2, const double *scale,
+                        int64_t B, int64_t K, double inv_v2, const double *scale, const int *status,
                         double *c, double *b, int64_t *count, cudaStream_t st);
 void launch_finish_gauss(const double *num, const double *den, const unsigned long long *cnt,
-                         int64_t B, int64_t K, const double *scale, double *c, double *b,
-                         int64_t *count, cudaStream_t st);
+                         int64_t B, int64_t K, const double *scale, const int *status, double *c,
+                         double *b, int64_t *count, cudaStream_t st);
 
 }  // namespace ncf
 

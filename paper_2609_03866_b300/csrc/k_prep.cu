@@ -251,7 +251,35 @@ prefix_apply_kernel(const int64_t *__restrict__ offs, const int64_t *__restrict_
     if (g == (int64_t)gridDim.x - 1 && threadIdx.x == 0) P[n_total] = (int64_t)*total;
 }
 
+__global__ void stats_guard_kernel(const SeriesStats *__restrict__ sx, const SeriesStats *__restrict__ sy,
+                                   int64_t B, int *__restrict__ status) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    if (sx[b].flags != 0 || (sy && sy[b].flags != 0)) atomicOr(status, STATUS_INPUT);
+}
+
+__global__ void keys_guard_kernel(const SeriesStats *__restrict__ sx, const SeriesStats *__restrict__ sy,
+                                  int64_t B, double t_abs, int *__restrict__ status) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double m = fmax(fabs(sx[b].t_first), fabs(sx[b].t_last));
+    if (sy) m = fmax(m, fmax(fabs(sy[b].t_first), fabs(sy[b].t_last)));
+    if (!(m <= t_abs)) atomicOr(status, STATUS_RANGE);
+}
+
 }  // namespace
+
+void launch_stats_guard(const SeriesStats *sx, const SeriesStats *sy, int64_t B, int *status,
+                        cudaStream_t st) {
+    NCF_LAUNCH("stats_guard_kernel", st,
+               stats_guard_kernel<<<(unsigned)((B + 127) / 128), 128, 0, st>>>(sx, sy, B, status));
+}
+
+void launch_keys_guard(const SeriesStats *sx, const SeriesStats *sy, int64_t B, double t_abs, int *status,
+                       cudaStream_t st) {
+    NCF_LAUNCH("keys_guard_kernel", st,
+               keys_guard_kernel<<<(unsigned)((B + 127) / 128), 128, 0, st>>>(sx, sy, B, t_abs, status));
+}
 
 void launch_chunk_series(const int64_t *chunk_base, int64_t B, int32_t *cs, cudaStream_t st) {
     NCF_LAUNCH("chunk_series_kernel", st,

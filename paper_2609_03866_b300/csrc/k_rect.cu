@@ -303,11 +303,18 @@ size_t rect_staging_bytes(int64_t n_tiles, int64_t K) {
     return al(n_tiles * sizeof(ScanTile)) + al(K * 8) * 3 + al(K * 4) + al(G * 8) * 2 + 1024;
 }
 
-ncf_status run_rect_scan(const RectArgs &a, char *ws, size_t ws_cap, char *pinned, size_t pinned_cap,
-                         cudaStream_t st, std::string *msg) {
+int64_t rect_tiles_of(const std::vector<int64_t> &offs, int64_t B) {
+    int64_t n = 0;
+    for (int64_t b = 0; b < B; ++b) n += (offs[b + 1] - offs[b] + kRectTile - 1) / kRectTile;
+    return n;
+}
+
+// Host tables of one rectangle scan -> device region `ws`: tiles of outer
+// points, the sorted lags with their integer offsets, and the lag groups.
+ncf_status rect_prepare(const RectArgs &a, char *ws, size_t ws_cap, char *pinned, size_t pinned_cap,
+                        cudaStream_t st, RectPrepared *out, std::string *msg) {
     const int64_t B = a.B, K = a.K;
     const int64_t G = (K + kLagGroup - 1) / kLagGroup;
-    // tiles of outer points
     std::vector<ScanTile> tiles;
     for (int64_t b = 0; b < B; ++b)
         for (int64_t j = (*a.outer_offs)[b]; j < (*a.outer_offs)[b + 1]; j += kRectTile)
@@ -347,25 +354,36 @@ ncf_status run_rect_scan(const RectArgs &a, char *ws, size_t ws_cap, char *pinne
         cudaMemcpyAsync(dst, pinned + off, bytes, cudaMemcpyHostToDevice, st);
         off += al(bytes);
     };
-    auto *d_tiles = reinterpret_cast<ScanTile *>(take(n_tiles * sizeof(ScanTile)));
-    auto *d_ranges = reinterpret_cast<RectRange *>(take(n_tiles * G * sizeof(RectRange)));
-    auto *d_slags = reinterpret_cast<double *>(take(K * 8));
-    auto *d_dls = reinterpret_cast<int64_t *>(take(K * 8));
-    auto *d_dus = reinterpret_cast<int64_t *>(take(K * 8));
-    auto *d_perm = reinterpret_cast<int32_t *>(take(K * 4));
-    auto *d_gmin = reinterpret_cast<int64_t *>(take(G * 8));
-    auto *d_gmax = reinterpret_cast<int64_t *>(take(G * 8));
-    up(d_tiles, tiles.data(), n_tiles * sizeof(ScanTile));
-    up(d_slags, slags.data(), K * 8);
-    up(d_dls, dls.data(), K * 8);
-    up(d_dus, dus.data(), K * 8);
-    up(d_perm, perm.data(), K * 4);
-    up(d_gmin, gmin.data(), G * 8);
-    up(d_gmax, gmax.data(), G * 8);
-    const int64_t nr = n_tiles * G;
+    RectPrepared r;
+    r.n_tiles = n_tiles;
+    r.G = G;
+    r.tiles = take(n_tiles * sizeof(ScanTile));
+    r.ranges = take(n_tiles * G * sizeof(RectRange));
+    r.slags = reinterpret_cast<double *>(take(K * 8));
+    r.dls = reinterpret_cast<int64_t *>(take(K * 8));
+    r.dus = reinterpret_cast<int64_t *>(take(K * 8));
+    r.perm = reinterpret_cast<int32_t *>(take(K * 4));
+    r.gmin = reinterpret_cast<int64_t *>(take(G * 8));
+    r.gmax = reinterpret_cast<int64_t *>(take(G * 8));
+    up(r.tiles, tiles.data(), n_tiles * sizeof(ScanTile));
+    up(r.slags, slags.data(), K * 8);
+    up(r.dls, dls.data(), K * 8);
+    up(r.dus, dus.data(), K * 8);
+    up(r.perm, perm.data(), K * 4);
+    up(r.gmin, gmin.data(), G * 8);
+    up(r.gmax, gmax.data(), G * 8);
+    *out = r;
+    return NCF_OK;
+}
+
+// The data-dependent part: key ranges of every (tile, lag group), then the scan.
+ncf_status rect_launch(const RectArgs &a, const RectPrepared &r, cudaStream_t st, std::string *msg) {
+    const int64_t nr = r.n_tiles * r.G;
+    auto *tiles = reinterpret_cast<const ScanTile *>(r.tiles);
+    auto *ranges = reinterpret_cast<RectRange *>(r.ranges);
     NCF_LAUNCH("rect_range_kernel", st,
                rect_range_kernel<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(
-                   a.Tx, a.offs_x, a.Sy, d_tiles, n_tiles, (int)G, d_gmin, d_gmax, a.fs.eta, d_ranges));
+                   a.Tx, a.offs_x, a.Sy, tiles, r.n_tiles, (int)r.G, r.gmin, r.gmax, a.fs.eta, ranges));
     static bool attr_set = false;
     const size_t smem = sizeof(RectSmem);
     if (!attr_set) {
@@ -374,8 +392,8 @@ ncf_status run_rect_scan(const RectArgs &a, char *ws, size_t ws_cap, char *pinne
     }
     NCF_LAUNCH("rect_scan_kernel", st,
                rect_scan_kernel<<<(unsigned)nr, kRectWarps * 32, smem, st>>>(
-                   a.Tx, a.P, a.tx, a.offs_x, a.Sy, a.Yq, a.sy, d_tiles, (int)G, d_ranges, d_slags,
-                   d_perm, d_dls, d_dus, d_gmin, d_gmax, K, a.eps, a.h, a.fs.eta, a.cnt, a.num128));
+                   a.Tx, a.P, a.tx, a.offs_x, a.Sy, a.Yq, a.sy, tiles, (int)r.G, ranges, r.slags, r.perm,
+                   r.dls, r.dus, r.gmin, r.gmax, a.K, a.eps, a.h, a.fs.eta, a.cnt, a.num128));
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         *msg = std::string("rectangle scan launch failed: ") + cudaGetErrorString(e);

@@ -93,13 +93,23 @@ gauss_window_kernel(const double *__restrict__ tx, const double *__restrict__ x,
     }
 }
 
+__device__ __forceinline__ bool failed_write(const int *status, int64_t i, double *c, double *b,
+                                             int64_t *count) {
+    if (!status || *status == 0) return false;  // a device check failed: no valid result
+    c[i] = __longlong_as_double(0x7ff8000000000000ll);
+    if (b) b[i] = c[i];
+    if (count) count[i] = -1;
+    return true;
+}
+
 __global__ void finish_rect_kernel(const unsigned long long *__restrict__ cnt,
                                    const unsigned long long *__restrict__ num128, int64_t B,
                                    int64_t K, double inv_v2, const double *__restrict__ scale,
-                                   double *__restrict__ c, double *__restrict__ b,
-                                   int64_t *__restrict__ count) {
+                                   const int *__restrict__ status, double *__restrict__ c,
+                                   double *__restrict__ b, int64_t *__restrict__ count) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * K) return;
+    if (failed_write(status, i, c, b, count)) return;
     const unsigned long long n = cnt[i];
     const double N = ((double)(long long)num128[2 * i + 1] * 18446744073709551616.0 +
                       (double)num128[2 * i]) * inv_v2;
@@ -114,10 +124,11 @@ __global__ void finish_rect_kernel(const unsigned long long *__restrict__ cnt,
 __global__ void finish_gauss_kernel(const double *__restrict__ num, const double *__restrict__ den,
                                     const unsigned long long *__restrict__ cnt, int64_t B,
                                     int64_t K, const double *__restrict__ scale,
-                                    double *__restrict__ c, double *__restrict__ b,
-                                    int64_t *__restrict__ count) {
+                                    const int *__restrict__ status, double *__restrict__ c,
+                                    double *__restrict__ b, int64_t *__restrict__ count) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * K) return;
+    if (failed_write(status, i, c, b, count)) return;
     double ci = num[i] / fmax(den[i], 1e-16);
     if (scale) ci /= scale[i / K];
     c[i] = ci;
@@ -180,20 +191,20 @@ void launch_gauss_window(const double *tx, const double *x, const int64_t *offs_
 }
 
 void launch_finish_rect(const unsigned long long *cnt, const unsigned long long *num128,
-                        int64_t B, int64_t K, double inv_v2, const double *scale,
+                        int64_t B, int64_t K, double inv_v2, const double *scale, const int *status,
                         double *c, double *b, int64_t *count, cudaStream_t st) {
     const int64_t n = B * K;
     NCF_LAUNCH("finish_rect_kernel", st,
-    finish_rect_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cnt, num128, B, K, inv_v2, scale,
+    finish_rect_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cnt, num128, B, K, inv_v2, scale, status,
                                                                      c, b, count));
 }
 
 void launch_finish_gauss(const double *num, const double *den, const unsigned long long *cnt,
-                         int64_t B, int64_t K, const double *scale, double *c, double *b,
-                         int64_t *count, cudaStream_t st) {
+                         int64_t B, int64_t K, const double *scale, const int *status, double *c,
+                         double *b, int64_t *count, cudaStream_t st) {
     const int64_t n = B * K;
     NCF_LAUNCH("finish_gauss_kernel", st,
-    finish_gauss_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(num, den, cnt, B, K, scale, c,
+    finish_gauss_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(num, den, cnt, B, K, scale, status, c,
                                                                       b, count));
 }
 

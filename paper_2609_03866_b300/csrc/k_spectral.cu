@@ -196,6 +196,11 @@ constexpr int kStagePad = kPrepChunk + kPrepChunk / 128;   // staged points, one
 __device__ __forceinline__ void split_ceil(double g, int &l0, float &f0) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(g);
     const int E = (int)((u >> 52) & 0x7FF) - 1023;             // g in [2^E, 2^(E+1))
+    if (E < 0 || E > 40 || (u >> 63)) {  // outside any periodic domain (NaN, negative, huge):
+        l0 = 0;                          // a plan's device guard reports it; keep indexing sane
+        f0 = 0.0f;
+        return;
+    }
     const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
     const unsigned long long fr = m << (12 + E);               // fraction * 2^64
     l0 = (int)(m >> (52 - E)) + (fr != 0ull);
@@ -322,7 +327,8 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
     bool started = false;
     auto flush_cell = [&](int cell, R re, R im) {
         if (re == (R)0 && im == (R)0) return;
-        if (use_tile) {
+        // inside the tile for sorted, in-domain points; anything else goes to the grid
+        if (use_tile && (unsigned)(cell - l_first) < (unsigned)span) {
             atomicAdd(&tile[cell - l_first].x, re);
             atomicAdd(&tile[cell - l_first].y, im);
         } else {
@@ -580,17 +586,10 @@ T *take(char *base, size_t &used, size_t count) {
     return p;
 }
 
-struct Plan {
-    double L = 0, beta = 0;
-    int64_t M = 0, Mp = 0, K1 = 0, Kp = 0, M2 = 0;
-    int nf = 0, lg = 0, W = 8, nq = 64;
-};
-
-Plan make_plan(const SpectralArgs &a, double max_span) {
-    Plan p;
+void make_plan(const SpectralArgs &a, double max_span, SpectralPrepared &p) {
     const double tol = a.tol;
-    const double R_alias = std::sqrt(2.0 * std::log(1.0 / (tol * 1e-2)));
-    p.L = max_span + a.max_tau + R_alias * a.h;
+    p.R_alias = std::sqrt(2.0 * std::log(1.0 / (tol * 1e-2)));
+    p.L = max_span + a.max_tau + p.R_alias * a.h;
     const double delta = tol * 1e-3;
     const double mscale = std::sqrt(std::log(1.0 / delta) / (2.0 * kPi * kPi));
     p.M = (int64_t)std::ceil(p.L * mscale / a.h) + 1;
@@ -605,101 +604,126 @@ Plan make_plan(const SpectralArgs &a, double max_span) {
     p.K1 = a.K + 1;                    // + an internal zero lag (lag-0 scale of the ACF)
     p.Kp = (p.K1 + 3) / 4 * 4;
     p.M2 = a.acf ? p.Mp : 2 * p.Mp;
-    return p;
+    p.fp32 = a.fp32;
+    p.acf = a.acf;
+    p.lag0 = a.lag0;
+    p.B = a.B;
+    p.K = a.K;
+    p.h = a.h;
+    p.max_tau = a.max_tau;
 }
 
 template <typename R>
-ncf_status run_typed(const SpectralArgs &a, const Plan &p, char *ws, const double *h_tc,
-                     const unsigned long long *h_phi, const std::vector<double> &gx,
-                     const std::vector<double> &gphi, char *pinned, cudaStream_t st, std::string *msg) {
-    using V = typename CT<R>::V;
-    const int64_t B = a.B;
-    const bool ccf = !a.acf;
-    size_t used = 0;
-    V *grid_x = take<V>(ws, used, B * (size_t)p.nf);
-    V *grid_y = ccf ? take<V>(ws, used, B * (size_t)p.nf) : nullptr;
-    V *scratch = take<V>(ws, used, B * (size_t)p.nf);
-    V *tw = take<V>(ws, used, p.nf);
-    double *wgt64 = take<double>(ws, used, p.Mp);
-    R *wgt = take<R>(ws, used, p.Mp);
-    R *Anum = take<R>(ws, used, B * p.M2);
-    R *Aden = take<R>(ws, used, B * p.M2);
-    R *E = take<R>(ws, used, p.M2 * p.Kp);
-    double *acc_num = take<double>(ws, used, B * p.Kp);
-    double *acc_den = take<double>(ws, used, B * p.Kp);
-    double *lag0 = take<double>(ws, used, 4 * B);
-    double *d_tc = take<double>(ws, used, B);
-    unsigned long long *d_phi = take<unsigned long long>(ws, used, p.Kp);
-    double *d_gx = take<double>(ws, used, p.nq);
-    double *d_gphi = take<double>(ws, used, p.nq);
-    int *d_status = take<int>(ws, used, 1);
+struct Bufs {
+    typename CT<R>::V *grid_x, *grid_y, *scratch, *tw;
+    double *wgt64;
+    R *wgt, *Anum, *Aden, *E;
+    double *acc_num, *acc_den, *lag0, *d_tc;
+    unsigned long long *d_phi;
+    double *d_gx, *d_gphi;
+    size_t used;
+};
 
-    // small host tables -> device (pinned staging)
+// The one layout of the spectral workspace, used by prepare, launch and sizing.
+template <typename R>
+Bufs<R> carve(const SpectralPrepared &p, char *ws) {
+    using V = typename CT<R>::V;
+    const int64_t B = p.B;
+    const bool ccf = !p.acf;
+    Bufs<R> b{};
+    size_t used = 0;
+    b.grid_x = take<V>(ws, used, B * (size_t)p.nf);
+    b.grid_y = ccf ? take<V>(ws, used, B * (size_t)p.nf) : nullptr;
+    b.scratch = take<V>(ws, used, B * (size_t)p.nf);
+    b.tw = take<V>(ws, used, p.nf);
+    b.wgt64 = take<double>(ws, used, p.Mp);
+    b.wgt = take<R>(ws, used, p.Mp);
+    b.Anum = take<R>(ws, used, B * p.M2);
+    b.Aden = take<R>(ws, used, B * p.M2);
+    b.E = take<R>(ws, used, p.M2 * p.Kp);
+    b.acc_num = take<double>(ws, used, B * p.Kp);
+    b.acc_den = take<double>(ws, used, B * p.Kp);
+    b.lag0 = take<double>(ws, used, 4 * B);
+    b.d_tc = take<double>(ws, used, B);
+    b.d_phi = take<unsigned long long>(ws, used, p.Kp);
+    b.d_gx = take<double>(ws, used, p.nq);
+    b.d_gphi = take<double>(ws, used, p.nq);
+    b.used = used + 256;
+    return b;
+}
+
+template <typename R>
+void prepare_typed(const SpectralPrepared &p, char *ws, const double *h_tc,
+                   const unsigned long long *h_phi, const std::vector<double> &gx,
+                   const std::vector<double> &gphi, char *pinned, cudaStream_t st) {
+    using V = typename CT<R>::V;
+    const int64_t B = p.B;
+    const bool ccf = !p.acf;
+    Bufs<R> bf = carve<R>(p, ws);
     size_t off = 0;
     auto up = [&](void *dst, const void *src, size_t bytes) {
         std::memcpy(pinned + off, src, bytes);
         cudaMemcpyAsync(dst, pinned + off, bytes, cudaMemcpyHostToDevice, st);
         off += al(bytes);
     };
-    up(d_tc, h_tc, B * 8);
-    up(d_phi, h_phi, p.Kp * 8);
-    up(d_gx, gx.data(), p.nq * 8);
-    up(d_gphi, gphi.data(), p.nq * 8);
-
+    up(bf.d_tc, h_tc, B * 8);
+    up(bf.d_phi, h_phi, p.Kp * 8);
+    up(bf.d_gx, gx.data(), p.nq * 8);
+    up(bf.d_gphi, gphi.data(), p.nq * 8);
     NCF_LAUNCH("mode_weight_kernel", st,
-    mode_weight_kernel<<<(unsigned)((p.Mp + 255) / 256), 256, 0, st>>>(
-        d_gx, d_gphi, p.nq, p.M, p.Mp, p.W, p.nf, p.L, a.h, wgt64,
-        std::is_same<R, float>::value ? reinterpret_cast<float *>(wgt) : nullptr));
+               mode_weight_kernel<<<(unsigned)((p.Mp + 255) / 256), 256, 0, st>>>(
+                   bf.d_gx, bf.d_gphi, p.nq, p.M, p.Mp, p.W, p.nf, p.L, p.h, bf.wgt64,
+                   std::is_same<R, float>::value ? reinterpret_cast<float *>(bf.wgt) : nullptr));
     if (std::is_same<R, double>::value)
-        cudaMemcpyAsync(wgt, wgt64, p.Mp * 8, cudaMemcpyDeviceToDevice, st);
-    NCF_LAUNCH("twiddle_kernel", st,
-    twiddle_kernel<V><<<(p.nf + 255) / 256, 256, 0, st>>>(tw, p.nf));
-    {
-        dim3 grid((unsigned)p.Mp, (unsigned)((p.Kp + 127) / 128));
-        NCF_LAUNCH("lag_table_kernel", st,
-        lag_table_kernel<R><<<grid, 128, 0, st>>>(d_phi, p.Mp, p.Kp, p.K1, ccf, E));
-    }
+        cudaMemcpyAsync(bf.wgt, bf.wgt64, p.Mp * 8, cudaMemcpyDeviceToDevice, st);
+    NCF_LAUNCH("twiddle_kernel", st, twiddle_kernel<V><<<(p.nf + 255) / 256, 256, 0, st>>>(bf.tw, p.nf));
+    dim3 grid((unsigned)p.Mp, (unsigned)((p.Kp + 127) / 128));
+    NCF_LAUNCH("lag_table_kernel", st,
+               lag_table_kernel<R><<<grid, 128, 0, st>>>(bf.d_phi, p.Mp, p.Kp, p.K1, ccf, bf.E));
+}
 
+template <typename R>
+ncf_status launch_typed(const SpectralArgs &a, const SpectralPrepared &p, char *ws, int *status,
+                        cudaStream_t st, std::string *msg) {
+    using V = typename CT<R>::V;
+    const int64_t B = p.B;
+    const bool ccf = !p.acf;
+    Bufs<R> bf = carve<R>(p, ws);
     // spreading
     const double a_scale = (double)p.nf / p.L;
-    auto spread = [&](const SpecSide &sd, V *grid, const int64_t *chunk_base, const int32_t *cs,
-                      int64_t n_chunks) {
+    constexpr size_t smem = spread_smem_bytes<R>();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(spread_kernel<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(spread_kernel<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    EsPoly<R, 8, PolyDeg<8>::D> poly8{};
+    EsPoly<R, 16, PolyDeg<16>::D> poly16{};
+    for (size_t i = 0; i < p.poly.size(); ++i) {
+        if (p.W == 8) poly8.c[i] = (R)p.poly[i];
+        else poly16.c[i] = (R)p.poly[i];
+    }
+    auto spread = [&](const SpecSide &sd, V *grid) {
         cudaMemsetAsync(grid, 0, B * (size_t)p.nf * sizeof(V), st);
-        constexpr size_t smem = spread_smem_bytes<R>();
-        EsPoly<R, 8, PolyDeg<8>::D> poly8{};
-        EsPoly<R, 16, PolyDeg<16>::D> poly16{};
-        {
-            const int D = p.W == 8 ? PolyDeg<8>::D : PolyDeg<16>::D;
-            const std::vector<double> c = es_poly(p.W, p.beta, D);
-            for (size_t i = 0; i < c.size(); ++i) {
-                if (p.W == 8) poly8.c[i] = (R)c[i];
-                else poly16.c[i] = (R)c[i];
-            }
-        }
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(spread_kernel<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaFuncSetAttribute(spread_kernel<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = true;
-        }
         if (p.W == 8)
             NCF_LAUNCH("spread_kernel", st,
-                       spread_kernel<R, 8><<<(unsigned)n_chunks, kSpreadThreads, smem, st>>>(
-                           sd.t, sd.v, sd.d_offs, chunk_base, cs, sd.d_stats, d_tc, a_scale, p.nf,
-                           poly8, grid));
+                       spread_kernel<R, 8><<<(unsigned)sd.n_chunks, kSpreadThreads, smem, st>>>(
+                           sd.t, sd.v, sd.d_offs, sd.d_chunk_base, sd.d_cs, sd.d_stats, bf.d_tc, a_scale,
+                           p.nf, poly8, grid));
         else
             NCF_LAUNCH("spread_kernel", st,
-                       spread_kernel<R, 16><<<(unsigned)n_chunks, kSpreadThreads, smem, st>>>(
-                           sd.t, sd.v, sd.d_offs, chunk_base, cs, sd.d_stats, d_tc, a_scale, p.nf,
-                           poly16, grid));
+                       spread_kernel<R, 16><<<(unsigned)sd.n_chunks, kSpreadThreads, smem, st>>>(
+                           sd.t, sd.v, sd.d_offs, sd.d_chunk_base, sd.d_cs, sd.d_stats, bf.d_tc, a_scale,
+                           p.nf, poly16, grid));
     };
-    spread(a.x, grid_x, a.x.d_chunk_base, a.x.d_cs, a.x.n_chunks);
-    if (ccf) spread(a.y, grid_y, a.y.d_chunk_base, a.y.d_cs, a.y.n_chunks);
+    spread(a.x, bf.grid_x);
+    if (ccf) spread(a.y, bf.grid_y);
 
-    // FFT passes (ping-pong with scratch); result returned in *res
+    // FFT passes (ping-pong with the scratch grid); returns the buffer holding the result
     const RadixPlan rp = radix_plan(p.lg);
     auto fft = [&](V *grid) -> V * {
-        V *in = grid, *out = scratch;
+        V *in = grid, *out = bf.scratch;
         int Ns = 1;
         for (int q = 0; q < rp.n_pass; ++q) {
             const int rad = rp.radix[q];
@@ -707,55 +731,53 @@ ncf_status run_typed(const SpectralArgs &a, const Plan &p, char *ws, const doubl
             const unsigned blocks = (unsigned)((items + 255) / 256);
             if (rad == 8)
                 NCF_LAUNCH("fft_pass_kernel", st,
-                           fft_pass_kernel<V, 8><<<blocks, 256, 0, st>>>(in, out, p.lg, Ns, tw, B));
+                           fft_pass_kernel<V, 8><<<blocks, 256, 0, st>>>(in, out, p.lg, Ns, bf.tw, B));
             else if (rad == 4)
                 NCF_LAUNCH("fft_pass_kernel", st,
-                           fft_pass_kernel<V, 4><<<blocks, 256, 0, st>>>(in, out, p.lg, Ns, tw, B));
+                           fft_pass_kernel<V, 4><<<blocks, 256, 0, st>>>(in, out, p.lg, Ns, bf.tw, B));
             else
                 NCF_LAUNCH("fft_pass_kernel", st,
-                           fft_pass_kernel<V, 2><<<blocks, 256, 0, st>>>(in, out, p.lg, Ns, tw, B));
+                           fft_pass_kernel<V, 2><<<blocks, 256, 0, st>>>(in, out, p.lg, Ns, bf.tw, B));
             Ns *= rad;
             std::swap(in, out);
         }
         return in;
     };
-    V *Gx = fft(grid_x);
-    if (Gx == scratch && ccf) {
+    V *Gx = fft(bf.grid_x);
+    if (Gx == bf.scratch && ccf) {
         // keep x's transform out of the scratch buffer before y's passes
-        cudaMemcpyAsync(grid_x, scratch, B * (size_t)p.nf * sizeof(V), cudaMemcpyDeviceToDevice, st);
-        Gx = grid_x;
+        cudaMemcpyAsync(bf.grid_x, bf.scratch, B * (size_t)p.nf * sizeof(V), cudaMemcpyDeviceToDevice, st);
+        Gx = bf.grid_x;
     }
-    V *Gy = ccf ? fft(grid_y) : nullptr;
+    V *Gy = ccf ? fft(bf.grid_y) : nullptr;
 
-    const bool lag0_ccf = a.lag0 && ccf;
-    if (lag0_ccf) cudaMemsetAsync(lag0, 0, 4 * B * 8, st);
+    const bool lag0_ccf = p.lag0 && ccf;
+    if (lag0_ccf) cudaMemsetAsync(bf.lag0, 0, 4 * B * 8, st);
     {
         dim3 grid((unsigned)((p.Mp + 255) / 256), (unsigned)std::min<int64_t>(B, 65535));
         NCF_LAUNCH("spectrum_kernel", st,
-        spectrum_kernel<R><<<grid, 256, 0, st>>>(Gx, Gy, p.nf, p.M, p.Mp, B, wgt, Anum, Aden,
-                                                 lag0_ccf ? lag0 : nullptr));
+                   spectrum_kernel<R><<<grid, 256, 0, st>>>(Gx, Gy, p.nf, p.M, p.Mp, B, bf.wgt, bf.Anum,
+                                                            bf.Aden, lag0_ccf ? bf.lag0 : nullptr));
     }
-    cudaMemsetAsync(acc_num, 0, B * p.Kp * 8, st);
-    cudaMemsetAsync(acc_den, 0, B * p.Kp * 8, st);
-    cudaMemsetAsync(d_status, 0, sizeof(int), st);
+    cudaMemsetAsync(bf.acc_num, 0, B * p.Kp * 8, st);
+    cudaMemsetAsync(bf.acc_den, 0, B * p.Kp * 8, st);
     if constexpr (std::is_same<R, float>::value) {
         // FP32 form: tensor cores (TF32 split products, FP64 chunk sums)
-        launch_contract_tc(Anum, Aden, E, B, p.M2, p.Kp, acc_num, acc_den, d_status, st);
+        launch_contract_tc(bf.Anum, bf.Aden, bf.E, B, p.M2, p.Kp, bf.acc_num, bf.acc_den, status, st);
     } else {
         dim3 grid((unsigned)((p.Kp + kBN - 1) / kBN), (unsigned)((B + kBM - 1) / kBM),
                   (unsigned)((p.M2 + kChunk - 1) / kChunk));
         NCF_LAUNCH("contract_kernel", st,
-                   contract_kernel<R><<<grid, 256, 0, st>>>(Anum, Aden, E, B, p.M2, p.Kp, acc_num, acc_den));
+                   contract_kernel<R><<<grid, 256, 0, st>>>(bf.Anum, bf.Aden, bf.E, B, p.M2, p.Kp, bf.acc_num,
+                                                            bf.acc_den));
     }
-    {
-        const int mode = a.lag0 ? (ccf ? 2 : 1) : 0;
-        NCF_LAUNCH("finish_spectral_kernel", st,
-        finish_spectral_kernel<<<(unsigned)((B * a.K + 255) / 256), 256, 0, st>>>(
-            acc_num, acc_den, B, a.K, p.Kp, mode, lag0, d_status,
-            std::is_same<R, float>::value ? reinterpret_cast<const float *>(Anum) : nullptr,
-            std::is_same<R, float>::value ? reinterpret_cast<const float *>(Aden) : nullptr, p.M2, a.c_out,
-            a.b_out, a.count_out));
-    }
+    const int mode = p.lag0 ? (ccf ? 2 : 1) : 0;
+    NCF_LAUNCH("finish_spectral_kernel", st,
+               finish_spectral_kernel<<<(unsigned)((B * p.K + 255) / 256), 256, 0, st>>>(
+                   bf.acc_num, bf.acc_den, B, p.K, p.Kp, mode, bf.lag0, status,
+                   std::is_same<R, float>::value ? reinterpret_cast<const float *>(bf.Anum) : nullptr,
+                   std::is_same<R, float>::value ? reinterpret_cast<const float *>(bf.Aden) : nullptr, p.M2,
+                   a.c_out, a.b_out, a.count_out));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         *msg = std::string("spectral path launch failed: ") + cudaGetErrorString(e);
@@ -764,28 +786,35 @@ ncf_status run_typed(const SpectralArgs &a, const Plan &p, char *ws, const doubl
     return NCF_OK;
 }
 
-template <typename R>
-size_t workspace_bytes(const Plan &p, int64_t B, bool ccf) {
-    using V = typename CT<R>::V;
-    size_t s = 0;
-    s += al(B * (size_t)p.nf * sizeof(V)) * (ccf ? 3 : 2);
-    s += al(p.nf * sizeof(V));
-    s += al(p.Mp * 8) + al(p.Mp * sizeof(R));
-    s += al(B * p.M2 * sizeof(R)) * 2 + al(p.M2 * p.Kp * sizeof(R));
-    s += al(B * p.Kp * 8) * 2 + al(4 * B * 8) + al(B * 8) + al(p.Kp * 8) + al(p.nq * 8) * 2 + al(4);
-    return s + 1024;
+// Checks, on the device, that every series of an executed plan still fits the
+// plan's periodic domain: its span leaves every pair separation at least
+// R_alias h away from +-L (span <= L - max|tau| - R_alias h; the result does not
+// depend on where the series sits), and its points stay within 0.9 L of the
+// plan's centre so that grid coordinates stay positive.
+__global__ void spectral_guard_kernel(const SeriesStats *__restrict__ sx, const SeriesStats *__restrict__ sy,
+                                      const double *__restrict__ tc, int64_t B, double max_span, double reach,
+                                      int *__restrict__ status) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double lo = sx[b].t_first, hi = sx[b].t_last;
+    if (sy) {
+        lo = fmin(lo, sy[b].t_first);
+        hi = fmax(hi, sy[b].t_last);
+    }
+    if (!(hi - lo <= max_span) || !(lo >= tc[b] - reach) || !(hi <= tc[b] + reach))
+        atomicOr(status, STATUS_DOMAIN);
 }
 
 }  // namespace
 
-ncf_status run_spectral(const SpectralArgs &a, char **ws, size_t *ws_cap, char **pinned,
-                        size_t *pinned_cap, cudaStream_t st, std::string *msg,
-                        SpectralGeometry *geom) {
+ncf_status spectral_plan(const SpectralArgs &a, SpectralPrepared *sp, size_t *ws_bytes,
+                         size_t *pinned_bytes, std::string *msg) {
     const int64_t B = a.B;
     const bool ccf = !a.acf;
     // per-series centre t_c and the common period L (Algorithm 1 with an
     // alias margin: L = max span + max|tau| + R h)
-    std::vector<double> tc(B);
+    SpectralPrepared p;
+    p.tc.resize(B);
     double max_span = 0.0;
     for (int64_t b = 0; b < B; ++b) {
         double lo = a.x.h_stats[b].t_first, hi = a.x.h_stats[b].t_last;
@@ -793,59 +822,51 @@ ncf_status run_spectral(const SpectralArgs &a, char **ws, size_t *ws_cap, char *
             lo = std::min(lo, a.y.h_stats[b].t_first);
             hi = std::max(hi, a.y.h_stats[b].t_last);
         }
-        tc[b] = lo + 0.5 * (hi - lo);
+        p.tc[b] = lo + 0.5 * (hi - lo);
         max_span = std::max(max_span, hi - lo);
     }
-    const Plan p = make_plan(a, max_span);
-    if (geom) *geom = SpectralGeometry{p.L, p.M, p.nf, p.W};
+    make_plan(a, max_span, p);
     if (p.lg > 28) {
         *msg = "spectral grid would exceed 2^28 cells (span / h too large); use the windowed path";
         return NCF_EUNSUPPORTED;
     }
     // lag phases in 64-bit fixed point; the appended lag K is zero
-    std::vector<unsigned long long> phi(p.Kp, 0ull);
+    p.phi.assign(p.Kp, 0ull);
     for (int64_t k = 0; k < a.K; ++k) {
         double f = a.h_lags[k] / p.L;
         f -= std::floor(f);
-        phi[k] = (unsigned long long)std::ldexp(f, 64 - 11) << 11;
+        p.phi[k] = (unsigned long long)std::ldexp(f, 64 - 11) << 11;
     }
-    std::vector<double> gx, gw, gphi;
-    gauss_legendre(p.nq, gx, gw);
-    gphi.resize(p.nq);
+    std::vector<double> gw;
+    gauss_legendre(p.nq, p.gx, gw);
+    p.gphi.resize(p.nq);
     for (int q = 0; q < p.nq; ++q)
-        gphi[q] = gw[q] * std::exp(p.beta * (std::sqrt(std::max(0.0, 1.0 - gx[q] * gx[q])) - 1.0));
+        p.gphi[q] = gw[q] * std::exp(p.beta * (std::sqrt(std::max(0.0, 1.0 - p.gx[q] * p.gx[q])) - 1.0));
+    p.poly = es_poly(p.W, p.beta, p.W == 8 ? PolyDeg<8>::D : PolyDeg<16>::D);
+    *ws_bytes = p.fp32 ? carve<float>(p, nullptr).used : carve<double>(p, nullptr).used;
+    *pinned_bytes = al(B * 8) + al(p.Kp * 8) + 2 * al(p.nq * 8);
+    *sp = std::move(p);
+    return NCF_OK;
+}
 
-    const size_t need = a.fp32 ? workspace_bytes<float>(p, B, ccf) : workspace_bytes<double>(p, B, ccf);
-    if (need > *ws_cap) {
-        if (*ws) {
-            cudaStreamSynchronize(st);
-            cudaFree(*ws);
-            *ws = nullptr;
-            *ws_cap = 0;
-        }
-        if (cudaMalloc(ws, need) != cudaSuccess) {
-            cudaGetLastError();
-            *ws = nullptr;
-            *msg = "cudaMalloc of the spectral workspace failed";
-            return NCF_ENOMEM;
-        }
-        *ws_cap = need;
-    }
-    const size_t pin_need = al(B * 8) + al(p.Kp * 8) + 2 * al(p.nq * 8);
-    if (pin_need > *pinned_cap) {
-        cudaStreamSynchronize(st);
-        if (*pinned) cudaFreeHost(*pinned);
-        *pinned = nullptr;
-        *pinned_cap = 0;
-        if (cudaHostAlloc(pinned, pin_need, cudaHostAllocDefault) != cudaSuccess) {
-            cudaGetLastError();
-            *msg = "cudaHostAlloc of the staging buffer failed";
-            return NCF_ENOMEM;
-        }
-        *pinned_cap = pin_need;
-    }
-    if (a.fp32) return run_typed<float>(a, p, *ws, tc.data(), phi.data(), gx, gphi, *pinned, st, msg);
-    return run_typed<double>(a, p, *ws, tc.data(), phi.data(), gx, gphi, *pinned, st, msg);
+void spectral_prepare(const SpectralPrepared &p, char *ws, char *pinned, cudaStream_t st) {
+    if (p.fp32) prepare_typed<float>(p, ws, p.tc.data(), p.phi.data(), p.gx, p.gphi, pinned, st);
+    else prepare_typed<double>(p, ws, p.tc.data(), p.phi.data(), p.gx, p.gphi, pinned, st);
+}
+
+ncf_status spectral_launch(const SpectralArgs &a, const SpectralPrepared &p, char *ws, int *status,
+                           cudaStream_t st, std::string *msg) {
+    if (p.fp32) return launch_typed<float>(a, p, ws, status, st, msg);
+    return launch_typed<double>(a, p, ws, status, st, msg);
+}
+
+void spectral_guard(const SpectralArgs &a, const SpectralPrepared &p, char *ws, int *status,
+                    cudaStream_t st) {
+    const double *d_tc = p.fp32 ? carve<float>(p, ws).d_tc : carve<double>(p, ws).d_tc;
+    const double max_span = (p.L - p.max_tau - p.R_alias * p.h) * (1.0 + 1e-12);
+    NCF_LAUNCH("spectral_guard_kernel", st,
+               spectral_guard_kernel<<<(unsigned)((p.B + 127) / 128), 128, 0, st>>>(
+                   a.x.d_stats, p.acf ? nullptr : a.y.d_stats, d_tc, p.B, max_span, 0.9 * p.L, status));
 }
 
 }  // namespace ncf

@@ -190,7 +190,7 @@ contract_tc_kernel(const float *__restrict__ Anum, const float *__restrict__ Ade
         }
         // every thread waits before the tiles are rewritten (bounded)
         if (!mbar_wait(mb, parity)) {
-            if (tid == 0) atomicExch(status, 1);
+            if (tid == 0) atomicOr(status, STATUS_TIMEOUT);
             fail_sh = 1;
         }
         parity ^= 1u;

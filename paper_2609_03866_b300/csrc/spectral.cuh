@@ -2,6 +2,7 @@
 #pragma once
 
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -31,20 +32,36 @@ struct SpectralArgs {
     int sm_count = 148;
 };
 
-// Geometry chosen by the last run_spectral call (reported through ncf_last_plan).
-struct SpectralGeometry { double L; int64_t M, nf, W; };
+// Geometry and host tables of a spectral evaluation (spectral_plan), kept by
+// one-shot calls and by ncf_plan objects alike.
+struct SpectralPrepared {
+    double L = 0, beta = 0, R_alias = 0, h = 0, max_tau = 0;
+    int64_t M = 0, Mp = 0, K1 = 0, Kp = 0, M2 = 0, B = 0, K = 0;
+    int nf = 0, lg = 0, W = 8, nq = 64;
+    bool fp32 = false, acf = true, lag0 = false;
+    std::vector<double> tc, gx, gphi, poly;
+    std::vector<unsigned long long> phi;
+};
+
+// Host-side planning: geometry, tables, workspace sizes (device, pinned staging).
+ncf_status spectral_plan(const SpectralArgs &a, SpectralPrepared *sp, size_t *ws_bytes,
+                         size_t *pinned_bytes, std::string *msg);
+// Uploads the host tables and builds the device tables (mode weights,
+// twiddles, lag table) in `ws`.
+void spectral_prepare(const SpectralPrepared &p, char *ws, char *pinned, cudaStream_t st);
+// The per-data kernels: spreading, FFT, spectra, contraction, normalisation.
+// *status is read by the normalisation (nonzero -> NaN results).
+ncf_status spectral_launch(const SpectralArgs &a, const SpectralPrepared &p, char *ws, int *status,
+                           cudaStream_t st, std::string *msg);
+// Device check that the series still fit the plan's periodic domain.
+void spectral_guard(const SpectralArgs &a, const SpectralPrepared &p, char *ws, int *status,
+                    cudaStream_t st);
 
 // Tensor-core contraction of the FP32 form (k_tc.cu): acc_c += A_c E over all
-// modes, TF32 split products, FP32 TMEM accumulation per 512-mode chunk, FP64
+// modes, TF32 split products, FP32 TMEM accumulation per 128-mode chunk, FP64
 // partial sums.  *status becomes nonzero if a bounded wait gave up.
 bool contract_tc_supported(int64_t M2);
 void launch_contract_tc(const float *Anum, const float *Aden, const float *E, int64_t B, int64_t M2,
                         int64_t Kp, double *acc_num, double *acc_den, int *status, cudaStream_t st);
-
-// Runs the spectral path on `st`; grows *ws (device) and *pinned (host) as
-// needed.  Returns NCF_OK or an error with *msg set.
-ncf_status run_spectral(const SpectralArgs &a, char **ws, size_t *ws_cap, char **pinned,
-                        size_t *pinned_cap, cudaStream_t st, std::string *msg,
-                        SpectralGeometry *geom);
 
 }  // namespace ncf
