@@ -13,6 +13,7 @@
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -45,6 +46,7 @@ struct ncf_ctx {
     uint64_t launches = 0;
     cudaEvent_t staged = nullptr;  // recorded after staging copies issued past the read-back sync
     NcfProfiler prof;
+    std::map<uint64_t, int> tune_rect;  // autotuned rectangle-scan variant per problem bucket
     ncf_plan_info plan{0.0, 0, 0, 0, 0, 0};
     std::string err;
 };
@@ -271,11 +273,17 @@ ncf_status check_args(ncf_ctx *ctx, const int64_t *offs_x, const double *t, cons
     if (rc) return rc;
     if (!acf && (rc = check_offsets(ctx, offs_y, B, "offs_y"))) return rc;
     int path = opt->path;
-    if (path == NCF_PATH_AUTO) path = (opt->kernel == NCF_RECTANGLE) ? NCF_PATH_WINDOWED : NCF_PATH_SPECTRAL;
     if (opt->kernel == NCF_RECTANGLE && path == NCF_PATH_SPECTRAL)
         return fail(ctx, NCF_EUNSUPPORTED,
                     "rectangle kernel: only the exact windowed scan is provided (its transform "
                     "decays as 1/f, so a truncated spectrum cannot meet the tolerance)");
+    if (opt->kernel == NCF_GAUSSIAN && path == NCF_PATH_WINDOWED && opt->precision == NCF_FP32)
+        return fail(ctx, NCF_EUNSUPPORTED, "the windowed Gaussian path is FP64 only");
+    if (path == NCF_PATH_AUTO) {
+        if (opt->kernel == NCF_RECTANGLE) path = NCF_PATH_WINDOWED;
+        else if (opt->precision == NCF_FP32) path = NCF_PATH_SPECTRAL;
+        // FP64 Gaussian: decided after the statistics pass (choose_path)
+    }
     ev.acf = acf;
     ev.B = B;
     ev.K = K;
@@ -618,6 +626,97 @@ ncf_status launch(ncf_ctx *ctx, Eval &ev, bool stats_fresh, bool guard, double *
     return NCF_OK;
 }
 
+// FP64 Gaussian with NCF_PATH_AUTO: the windowed scan costs one FP64 exp per
+// pair inside the window, O(n K n_window); the spectral path costs the
+// spreading, the FFT and the mode sums, O(n W + n_f log n_f + M K) per series.
+// The crossover in K is the paper's K* (Sec. 5.1); here it is a cost model
+// with constants measured on B300 (windowed 56 ps per pair; FP64 spreading
+// 0.4 ns per point; FP64 FFT 16 B per cell and pass at 5 TB/s; FP64 mode sums
+// at 0.57 T FMA/s).
+void choose_path(Eval &ev) {
+    if (ev.path != NCF_PATH_AUTO) return;
+    const double R = ev.opt.trunc_R > 0.0 ? ev.opt.trunc_R : 8.0;
+    double win = 0.0, spread = 0.0, max_span = 0.0;
+    for (int64_t b = 0; b < ev.B; ++b) {
+        const SeriesStats &sx = ev.X.stats[b];
+        const SeriesStats &so = ev.acf ? sx : ev.Y.stats[b];
+        double lo = sx.t_first, hi = sx.t_last;
+        if (!ev.acf) { lo = std::min(lo, so.t_first); hi = std::max(hi, so.t_last); }
+        max_span = std::max(max_span, hi - lo);
+        const double span = std::max(sx.t_last - sx.t_first, 1e-300);
+        const double in_window = std::min((double)sx.n, (double)sx.n / span * 2.0 * R * ev.opt.h + 1.0);
+        win += (double)so.n * (double)ev.K * in_window;
+        spread += (double)(sx.n + (ev.acf ? 0 : so.n));
+    }
+    const double L = max_span + ev.max_tau + 8.6 * ev.opt.h;
+    const double M = L * 1.408 / ev.opt.h + 1.0;
+    double nf = 1.0;
+    while (nf < 4.0 * M + 16.0) nf *= 2.0;
+    const double passes = std::ceil(std::log2(nf) / 3.0) * (ev.acf ? 1.0 : 2.0);
+    const double t_win = win * 56e-12;
+    const double t_spec = spread * 0.4e-9 + (double)ev.B * nf * 16.0 * 2.0 * passes / 5e12 +
+                          (double)ev.B * M * (ev.K + 1.0) * 2.0 * (ev.acf ? 1.0 : 2.0) / 0.57e12;
+    ev.path = t_win < t_spec ? NCF_PATH_WINDOWED : NCF_PATH_SPECTRAL;
+}
+
+uint64_t rect_tune_key(const Eval &ev) {
+    auto lg = [](double v) { return (uint64_t)std::max(0.0, std::floor(std::log2(std::max(v, 1.0)))); };
+    const Side &O = ev.acf ? ev.X : ev.Y;
+    return lg((double)O.n_total) | (lg((double)O.n_total / (double)ev.B) << 8) | (lg((double)ev.K) << 16) |
+           ((uint64_t)ev.acf << 24);
+}
+
+// Times the rectangle-scan variants once per problem bucket (they give
+// identical, exact results) and keeps the fastest in the context.
+ncf_status tune_rect(ncf_ctx *ctx, Eval &ev, cudaStream_t st) {
+    // NCF_RECT_VARIANT=0|1|2 pins a variant (tests, measurements) and skips the timing
+    if (const char *pin = std::getenv("NCF_RECT_VARIANT")) {
+        const int v = std::atoi(pin);
+        if (v >= 0 && v < kRectVariants) {
+            ev.r_main.variant = ev.r_x.variant = ev.r_y.variant = v;
+            return NCF_OK;
+        }
+    }
+    const uint64_t key = rect_tune_key(ev);
+    auto it = ctx->tune_rect.find(key);
+    if (it != ctx->tune_rect.end()) {
+        ev.r_main.variant = ev.r_x.variant = ev.r_y.variant = it->second;
+        return NCF_OK;
+    }
+    const int64_t B = ev.B, K = ev.K;
+    Side &X = ev.X, &O = ev.outer();
+    launch_keys_prefix(X.t, X.v, X.d_offs, X.d_chunk_base, X.d_cs, X.n_chunks, kPrepChunk, X.d_stats, ev.fs,
+                       ev.kxT, ev.kxX, ev.kxP, ev.kxC, X.n_total, st);
+    if (!ev.acf)
+        launch_keys_prefix(ev.Y.t, ev.Y.v, ev.Y.d_offs, ev.Y.d_chunk_base, ev.Y.d_cs, ev.Y.n_chunks, kPrepChunk,
+                           ev.Y.d_stats, ev.fs, ev.kyT, ev.kyX, ev.kyP, ev.kyC, ev.Y.n_total, st);
+    cudaEvent_t e[kRectVariants + 1];
+    for (auto &x : e) NCF_CUDA(cudaEventCreate(&x));
+    std::string msg;
+    const int eps = ev.acf ? +1 : -1;
+    RectArgs ra{ev.kxT, ev.kxP, X.t, X.d_offs, ev.kyT, ev.kyX, O.t, &O.offs, B, K, ev.lagv.data(), eps,
+                ev.opt.h, ev.fs, ev.cnt, ev.num};
+    NCF_CUDA(cudaEventRecord(e[0], st));
+    for (int v = 0; v < kRectVariants; ++v) {
+        ev.r_main.variant = v;
+        ncf_status rc = rect_launch(ra, ev.r_main, st, &msg);
+        if (rc) return fail(ctx, rc, "%s", msg.c_str());
+        NCF_CUDA(cudaEventRecord(e[v + 1], st));
+    }
+    NCF_CUDA(cudaEventSynchronize(e[kRectVariants]));
+    int best = 1;
+    float best_ms = 1e30f;
+    for (int v = 0; v < kRectVariants; ++v) {
+        float ms = 0.0f;
+        NCF_CUDA(cudaEventElapsedTime(&ms, e[v], e[v + 1]));
+        if (ms < best_ms) { best_ms = ms; best = v; }
+    }
+    for (auto &x : e) cudaEventDestroy(x);
+    ctx->tune_rect[key] = best;
+    ev.r_main.variant = ev.r_x.variant = ev.r_y.variant = best;
+    return NCF_OK;
+}
+
 }  // namespace
 
 // ----------------------------------------------------------------------------
@@ -641,12 +740,14 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
     if ((rc = grow(ctx, &ctx->ws, &ctx->ws_cap, pre_bytes(ev), st))) return rc;
     carve_pre(ev, ctx->ws);
     if ((rc = analyze(ctx, ev, lags, st))) return rc;
+    choose_path(ev);
     size_t dev = 0, pin = 0;
     if ((rc = main_bytes(ctx, ev, &dev, &pin))) return rc;
     if ((rc = grow(ctx, &ctx->ws2, &ctx->ws2_cap, dev, st))) return rc;
     if ((rc = grow_pinned(ctx, pin, st))) return rc;
     if ((rc = prepare(ctx, ev, ctx->ws2, ctx->ws2_cap, ctx->pinned, ctx->pinned_cap, lags, st))) return rc;
     NCF_CUDA(cudaEventRecord(ctx->staged, st));
+    if (ev.opt.kernel == NCF_RECTANGLE && (rc = tune_rect(ctx, ev, st))) return rc;
     return launch(ctx, ev, /*stats_fresh=*/true, /*guard=*/false, c_out, b_out, count_out, st);
 }
 
@@ -883,6 +984,7 @@ ncf_status ncf_plan_create(ncf_ctx *ctx, const int64_t *offs_x, const double *t,
     }
     carve_pre(ev, p->pre);
     if ((rc = analyze(ctx, ev, lags, st))) return bail(rc);
+    choose_path(ev);
     size_t dev = 0, pin = 0;
     if ((rc = main_bytes(ctx, ev, &dev, &pin))) return bail(rc);
     p->main_cap = dev;
@@ -892,6 +994,7 @@ ncf_status ncf_plan_create(ncf_ctx *ctx, const int64_t *offs_x, const double *t,
     }
     if ((rc = grow_pinned(ctx, pin, st))) return bail(rc);
     if ((rc = prepare(ctx, ev, p->main, dev, ctx->pinned, ctx->pinned_cap, lags, st))) return bail(rc);
+    if (ev.opt.kernel == NCF_RECTANGLE && (rc = tune_rect(ctx, ev, st))) return bail(rc);
     if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(ctx, NCF_ECUDA, "plan set-up failed"));
     *out = p;
     return NCF_OK;

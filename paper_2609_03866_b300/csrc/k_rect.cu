@@ -38,7 +38,8 @@ namespace ncf {
 namespace {
 
 constexpr int kRectWarps = 32;                      // outer runs per CTA
-constexpr int kRun = 32;                            // outer points per warp run
+// outer points per warp run: a template parameter, chosen by the autotuner
+// (rect_variant_run); 16, 32 or 64
 constexpr int kRectTile = 2048;                     // outer points per CTA
 constexpr int kLagGroup = 32;                       // lags per CTA (one per lane)
 constexpr int kKeyCap = 10240;                      // staged window entries
@@ -133,6 +134,7 @@ __device__ __forceinline__ double centre(double s, double tau, int eps) {
     return __dadd_rn(s, eps > 0 ? tau : -tau);
 }
 
+template <int kRun>
 __global__ void __launch_bounds__(kRectWarps * 32, 1)
 rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
                  const double *__restrict__ tx, const int64_t *__restrict__ offs_x,
@@ -387,13 +389,22 @@ ncf_status rect_launch(const RectArgs &a, const RectPrepared &r, cudaStream_t st
     static bool attr_set = false;
     const size_t smem = sizeof(RectSmem);
     if (!attr_set) {
-        cudaFuncSetAttribute(rect_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(rect_scan_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(rect_scan_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(rect_scan_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_set = true;
     }
-    NCF_LAUNCH("rect_scan_kernel", st,
-               rect_scan_kernel<<<(unsigned)nr, kRectWarps * 32, smem, st>>>(
-                   a.Tx, a.P, a.tx, a.offs_x, a.Sy, a.Yq, a.sy, tiles, (int)r.G, ranges, r.slags, r.perm,
-                   r.dls, r.dus, r.gmin, r.gmax, a.K, a.eps, a.h, a.fs.eta, a.cnt, a.num128));
+#define NCF_RECT_SCAN(RUN)                                                                              \
+    NCF_LAUNCH("rect_scan_kernel", st,                                                                 \
+               rect_scan_kernel<RUN><<<(unsigned)nr, kRectWarps * 32, smem, st>>>(                     \
+                   a.Tx, a.P, a.tx, a.offs_x, a.Sy, a.Yq, a.sy, tiles, (int)r.G, ranges, r.slags, r.perm, \
+                   r.dls, r.dus, r.gmin, r.gmax, a.K, a.eps, a.h, a.fs.eta, a.cnt, a.num128))
+    switch (r.variant) {
+        case 0: NCF_RECT_SCAN(16); break;
+        case 2: NCF_RECT_SCAN(64); break;
+        default: NCF_RECT_SCAN(32); break;
+    }
+#undef NCF_RECT_SCAN
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         *msg = std::string("rectangle scan launch failed: ") + cudaGetErrorString(e);
