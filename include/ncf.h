@@ -222,6 +222,41 @@ NCF_API size_t ncf_plan_device_bytes(const ncf_plan *plan);
 NCF_API void ncf_plan_destroy(ncf_plan *plan);
 
 /*
+ * Serving: a continuous-batching request loop on one GPU.
+ *
+ * ncf_server_create starts `slots` worker threads, each with its own CUDA
+ * stream and context, on `device`.  ncf_server_submit admits one ACF/CCF
+ * request (HOST buffers, which must stay valid until ncf_server_wait returns
+ * for its ticket) if a slot is free and the estimated device memory of all
+ * admitted requests stays within mem_budget_bytes; otherwise it returns
+ * NCF_EBUSY at once and the caller retries later.  Admitted requests run
+ * concurrently, each exactly as ncf_corr on its own stream, so their kernels
+ * overlap on the device and each result equals the request run alone (up to
+ * floating-point summation order).  ncf_server_poll reports completion;
+ * ncf_server_wait blocks until the request is done, copies c, b, count
+ * (each [K], NULL to skip) to host memory, returns the request's status and
+ * its latency (submit to completion).  ncf_server_latency reports the 50th
+ * and 99th percentile latencies of all completed requests.
+ */
+typedef struct {
+    const double *t, *x;   /* HOST, nx points, t non-decreasing */
+    int64_t nx;
+    const double *s, *y;   /* HOST, ny points (NULL, NULL for an ACF) */
+    int64_t ny;
+    const double *lags;    /* HOST [K] */
+    int64_t K;
+    ncf_options opt;
+} ncf_request;
+typedef struct ncf_server ncf_server;
+NCF_API ncf_status ncf_server_create(int device, size_t mem_budget_bytes, int slots, ncf_server **out);
+NCF_API ncf_status ncf_server_submit(ncf_server *srv, const ncf_request *req, uint64_t *ticket);
+NCF_API ncf_status ncf_server_poll(ncf_server *srv, uint64_t ticket, int *done);
+NCF_API ncf_status ncf_server_wait(ncf_server *srv, uint64_t ticket, double *c_out, double *b_out,
+                                   int64_t *count_out, double *latency_ms);
+NCF_API ncf_status ncf_server_latency(ncf_server *srv, double *p50_ms, double *p99_ms, uint64_t *completed);
+NCF_API void ncf_server_destroy(ncf_server *srv);
+
+/*
  * Allocation-free variant of the Gaussian windowed estimator (no counterpart
  * in the paper; it exists for callers that must not allocate device memory
  * while running, such as real-time or embedded pipelines with a fixed memory

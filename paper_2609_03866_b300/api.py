@@ -371,3 +371,90 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class ncf_request(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_void_p), ("x", ctypes.c_void_p), ("nx", ctypes.c_int64),
+                ("s", ctypes.c_void_p), ("y", ctypes.c_void_p), ("ny", ctypes.c_int64),
+                ("lags", ctypes.c_void_p), ("K", ctypes.c_int64), ("opt", ncf_options)]
+
+
+class Server:
+    """Continuous-batching request loop (ncf_server_*): requests are admitted
+    while others run, as slots and the device-memory budget allow; `submit`
+    raises NcfError(NCF_EBUSY) when they do not (retry later)."""
+
+    EBUSY = 7
+
+    def __init__(self, device=0, mem_budget_bytes=8 << 30, slots=4):
+        L = lib()
+        if not getattr(L, "_server_types", False):
+            vp = ctypes.c_void_p
+            L.ncf_server_create.argtypes = [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]
+            L.ncf_server_create.restype = ctypes.c_int
+            L.ncf_server_submit.argtypes = [vp, ctypes.POINTER(ncf_request), ctypes.POINTER(ctypes.c_uint64)]
+            L.ncf_server_submit.restype = ctypes.c_int
+            L.ncf_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
+            L.ncf_server_poll.restype = ctypes.c_int
+            L.ncf_server_wait.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
+            L.ncf_server_wait.restype = ctypes.c_int
+            L.ncf_server_latency.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_uint64)]
+            L.ncf_server_latency.restype = ctypes.c_int
+            L.ncf_server_destroy.argtypes = [vp]
+            L.ncf_server_destroy.restype = None
+            L._server_types = True
+        self._h = ctypes.c_void_p()
+        rc = L.ncf_server_create(int(device), int(mem_budget_bytes), int(slots), ctypes.byref(self._h))
+        if rc != 0:
+            raise NcfError(rc, status_name(rc), "ncf_server_create failed")
+        self._keep = {}
+
+    def submit(self, t, x, lags, kernel="gaussian", h=1.0, s=None, y=None, path="auto", precision="fp64",
+               norm="none", trunc_R=0.0, tol=0.0):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) if a is not None else None for a in (t, x, s, y, lags)]
+        t, x, s, y, lags = arrs
+        r = ncf_request()
+        r.t, r.x, r.nx = t.ctypes.data, x.ctypes.data, t.size
+        if s is not None:
+            r.s, r.y, r.ny = s.ctypes.data, y.ctypes.data, s.size
+        r.lags, r.K = lags.ctypes.data, lags.size
+        r.opt = make_options(kernel, h, path, precision, norm, trunc_R, tol)
+        tk = ctypes.c_uint64()
+        rc = lib().ncf_server_submit(self._h, ctypes.byref(r), ctypes.byref(tk))
+        if rc != 0:
+            raise NcfError(rc, status_name(rc), "request not admitted")
+        self._keep[tk.value] = (arrs, lags.size)
+        return tk.value
+
+    def done(self, ticket) -> bool:
+        d = ctypes.c_int()
+        lib().ncf_server_poll(self._h, ticket, ctypes.byref(d))
+        return bool(d.value)
+
+    def wait(self, ticket):
+        """Blocks until the request is done; returns dict(c, b, count, latency_ms) (numpy)."""
+        K = self._keep[ticket][1]
+        c, b, n = np.empty(K), np.empty(K), np.empty(K, dtype=np.int64)
+        lat = ctypes.c_double()
+        rc = lib().ncf_server_wait(self._h, ticket, c.ctypes.data, b.ctypes.data, n.ctypes.data, ctypes.byref(lat))
+        self._keep.pop(ticket, None)
+        if rc != 0:
+            raise NcfError(rc, status_name(rc), f"request {ticket} failed")
+        return {"c": c, "b": b, "count": n, "latency_ms": lat.value}
+
+    def latency(self):
+        p50, p99, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+        lib().ncf_server_latency(self._h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(n))
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "completed": int(n.value)}
+
+    def close(self):
+        if self._h:
+            lib().ncf_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,80 @@
+"""Serving loop (ncf_server_*): continuous admission by slots and device-memory
+budget; each result equals the same request run alone."""
+import numpy as np
+import pytest
+
+from paper_2609_03866_b300 import api, synth
+from tests._gpu import max_abs, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests():
+    rng = np.random.default_rng(9)
+    reqs = []
+    for i in range(12):
+        kernel = ["gaussian", "rectangle"][i % 2]
+        prec = "fp32" if (kernel == "gaussian" and i % 4 == 0) else "fp64"
+        K = int(rng.choice([16, 64, 128]))
+        if i % 3 == 2:
+            w = synth.ou_ccf(nA=int(rng.integers(2000, 20000)), nB=int(rng.integers(2000, 15000)), K=K,
+                             series=i)
+            reqs.append(dict(t=w.t, x=w.x, s=w.s, y=w.y, lags=w.lags, kernel=kernel, h=0.5, precision=prec))
+        else:
+            w = synth.light_curves(B=1, n_lo=1000, n_hi=60000, K=K, seed=synth.BASE_SEED + i)
+            reqs.append(dict(t=w.t, x=w.x, lags=w.lags, kernel=kernel, h=0.5, precision=prec))
+    return reqs
+
+
+def test_results_in_the_mix_equal_results_alone():
+    reqs = _requests()
+    alone = []
+    for r in reqs:
+        kw = {k: v for k, v in r.items() if k not in ("t", "x", "lags")}
+        alone.append(to_np(api.corr(r["t"], r["x"], r["lags"], **kw)))
+    srv = api.Server(slots=4, mem_budget_bytes=16 << 30)
+    tickets = []
+    pending = list(range(len(reqs)))
+    while pending:                      # continuous admission: retry when busy
+        i = pending[0]
+        r = reqs[i]
+        kw = {k: v for k, v in r.items() if k not in ("t", "x", "lags")}
+        try:
+            tickets.append((i, srv.submit(r["t"], r["x"], r["lags"], **kw)))
+            pending.pop(0)
+        except api.NcfError as e:
+            assert e.status == api.Server.EBUSY
+            done = [tk for _, tk in tickets if srv.done(tk)]
+            if not done:
+                import time
+                time.sleep(0.001)
+    for i, tk in tickets:
+        got = srv.wait(tk)
+        ref = alone[i]
+        tol = 1e-5 if reqs[i]["precision"] == "fp32" else 1e-10
+        assert max_abs(got["c"], ref["c"]) < tol, i
+        if reqs[i]["kernel"] == "rectangle":
+            assert np.array_equal(got["count"], ref["count"])
+        assert got["latency_ms"] > 0
+    lat = srv.latency()
+    assert lat["completed"] == len(reqs) and lat["p99_ms"] >= lat["p50_ms"] > 0
+    srv.close()
+
+
+def test_admission_budget_and_invalid_requests():
+    w = synth.light_curves(B=1, n_lo=5000, n_hi=5001, K=32)
+    srv = api.Server(slots=2, mem_budget_bytes=1 << 16)   # 64 KiB: too small for any request
+    with pytest.raises(api.NcfError) as e:
+        srv.submit(w.t, w.x, w.lags, kernel="rectangle", h=0.5)
+    assert e.value.status == api.Server.EBUSY
+    srv.close()
+    srv = api.Server(slots=2, mem_budget_bytes=1 << 30)
+    with pytest.raises(api.NcfError) as e:
+        srv.submit(w.t[:1], w.x[:1], w.lags)
+    assert e.value.name == "NCF_EINVAL"
+    # a request whose data are invalid is admitted and fails with its own status
+    tk = srv.submit(w.t[::-1].copy(), w.x, w.lags, kernel="rectangle", h=0.5)
+    with pytest.raises(api.NcfError) as e:
+        srv.wait(tk)
+    assert e.value.name == "NCF_ENOTSORTED"
+    srv.close()
