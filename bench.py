@@ -155,6 +155,82 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def serve_run(api, w, device, n_req=192, slots=4, seed=11):
+    """Request stream through the serving loop: single light curves, all 256
+    lags, Gaussian (FP32 form) and rectangle (exact scan) alternating.
+    Closed loop (slots requests kept in flight) gives the throughput; an open
+    Poisson stream at 70 % of it gives the latency a client sees (queueing on
+    the client while no slot is free + the server's submit-to-done time)."""
+    rng = np.random.default_rng(seed)
+    srv = api.Server(device=device, slots=slots, mem_budget_bytes=8 << 30)
+    idx = rng.integers(0, w.B, size=n_req)
+    offs = w.offs
+
+    def req(i):
+        b = int(idx[i % n_req])
+        sl = slice(int(offs[b]), int(offs[b + 1]))
+        if i % 2 == 0:
+            return dict(t=w.t[sl], x=w.x[sl], lags=w.lags, kernel="gaussian", h=H, path="spectral",
+                        precision="fp32")
+        return dict(t=w.t[sl], x=w.x[sl], lags=w.lags, kernel="rectangle", h=H)
+
+    def submit(r):
+        try:
+            return srv.submit(r.pop("t"), r.pop("x"), r.pop("lags"), **r)
+        except api.NcfError as e:
+            if e.status != api.Server.EBUSY:
+                raise
+            return None
+
+    for i in range(2 * slots):              # warm every slot's workspace
+        tk = None
+        while tk is None:
+            tk = submit(req(i))
+        srv.wait(tk)
+    # closed loop
+    t0 = time.perf_counter()
+    inflight, nxt = [], 0
+    while nxt < n_req or inflight:
+        while nxt < n_req and len(inflight) < slots:
+            tk = submit(req(nxt))
+            if tk is None:
+                break
+            inflight.append(tk)
+            nxt += 1
+        done = [tk for tk in inflight if srv.done(tk)]
+        for tk in done:
+            srv.wait(tk)
+            inflight.remove(tk)
+        if not done:
+            time.sleep(50e-6)
+    dt_closed = time.perf_counter() - t0
+    rate = n_req / dt_closed
+    # open Poisson stream at 70 % of the closed-loop rate
+    arr = np.cumsum(rng.exponential(1.0 / (0.7 * rate), size=n_req))
+    lat, inflight, nxt = [], {}, 0
+    t0 = time.perf_counter()
+    while nxt < n_req or inflight:
+        now = time.perf_counter() - t0
+        while nxt < n_req and arr[nxt] <= now:
+            tk = submit(req(nxt))
+            if tk is None:
+                break
+            inflight[tk] = (time.perf_counter() - t0) - arr[nxt]
+            nxt += 1
+        done = [tk for tk in inflight if srv.done(tk)]
+        for tk in done:
+            lat.append(inflight.pop(tk) * 1e3 + srv.wait(tk)["latency_ms"])
+        if not done:
+            time.sleep(50e-6)
+    srv.close()
+    K = w.lags.size
+    return {"requests": n_req, "slots": slots, "requests_per_s": rate, "value": rate * K,
+            "unit": "series*lags/s", "closed_loop_s": dt_closed,
+            "poisson_rate_per_s": 0.7 * rate, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)),
+            "mix": "single light curves x 256 lags, Gaussian FP32 form / rectangle exact scan alternating"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -164,6 +240,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch", type=int, default=B_SERIES, help="series per rank (profiling runs)")
     args = ap.parse_args()
 
@@ -287,6 +364,10 @@ def main():
         e2e = {"value": 2.0 * B * K * n_e2e * world / dt, "unit": "series*lags/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
 
+    serve = None
+    if not args.no_serve:
+        serve = serve_run(api, w, local)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -320,7 +401,7 @@ def main():
     per_launch_s = ms / nl / 1e3
     share = {k: round(v[1] / sum(u[1] for u in prof.values()), 4) for k, v in prof.items()}
     nf, M = plan["grid"], plan["modes"]
-    if name == "rect_scan_kernel":
+    if name.startswith("rect_scan"):
         # integer ALU: 16 int32 operations per (outer point, lag) item (two
         # 64-bit bound adds, two 64-bit window compares, one 64-bit window
         # difference, one 64x64->128-bit multiply-accumulate)
@@ -360,6 +441,7 @@ def main():
         "roofline": roof,
         "e2e": e2e,
         "fp64_plain": fp64,
+        "serving": serve,
         "accuracy": acc,
         "cpu_baseline": cpu,
     }

@@ -419,8 +419,8 @@ ncf_status main_bytes(ncf_ctx *ctx, Eval &ev, size_t *dev, size_t *pin) {
         const size_t rw = rect_workspace_bytes(rect_tiles_of(O.offs, B), K);
         const size_t rwx = ev.lag0 ? rect_workspace_bytes(rect_tiles_of(ev.X.offs, B), 1) : 0;
         const size_t rwy = (ev.lag0 && !ev.acf) ? rect_workspace_bytes(rect_tiles_of(ev.Y.offs, B), 1) : 0;
-        *dev = key_bytes(ev.X) + (ev.acf ? 0 : key_bytes(ev.Y)) + al(B * K * 8) * 3 + al(B * 8) * 8 + 1024 +
-               rw + rwx + rwy;
+        *dev = al(K * 8) + key_bytes(ev.X) + (ev.acf ? 0 : key_bytes(ev.Y)) + al(B * K * 8) * 3 +
+               al(B * 8) * 8 + 1024 + rw + rwx + rwy;
         *pin = rect_staging_bytes(rect_tiles_of(O.offs, B), K) +
                (ev.lag0 ? rect_staging_bytes(rect_tiles_of(ev.X.offs, B), 1) : 0) +
                ((ev.lag0 && !ev.acf) ? rect_staging_bytes(rect_tiles_of(ev.Y.offs, B), 1) : 0);
@@ -669,7 +669,7 @@ uint64_t rect_tune_key(const Eval &ev) {
 // Times the rectangle-scan variants once per problem bucket (they give
 // identical, exact results) and keeps the fastest in the context.
 ncf_status tune_rect(ncf_ctx *ctx, Eval &ev, cudaStream_t st) {
-    // NCF_RECT_VARIANT=0|1|2 pins a variant (tests, measurements) and skips the timing
+    // NCF_RECT_VARIANT=0|1|2|3 pins a variant (tests, measurements) and skips the timing
     if (const char *pin = std::getenv("NCF_RECT_VARIANT")) {
         const int v = std::atoi(pin);
         if (v >= 0 && v < kRectVariants) {

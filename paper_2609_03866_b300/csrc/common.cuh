@@ -110,14 +110,14 @@ struct RectArgs {
 };
 // Device tables of one rectangle scan (tiles, sorted lags, lag groups).
 struct RectPrepared {
-    int variant = 1;  // outer points per warp run: 0 -> 16, 1 -> 32, 2 -> 64 (autotuned)
+    int variant = 1;  // lags on lanes with runs of 16 / 32 / 64 outer points (0-2), points on lanes (3); autotuned
     int64_t n_tiles = 0, G = 0;
     void *tiles = nullptr, *ranges = nullptr;
     double *slags = nullptr;
     int64_t *dls = nullptr, *dus = nullptr, *gmin = nullptr, *gmax = nullptr;
     int32_t *perm = nullptr;
 };
-constexpr int kRectVariants = 3;
+constexpr int kRectVariants = 4;
 int rect_tile_points();
 int64_t rect_tiles_of(const std::vector<int64_t> &offs, int64_t B);
 size_t rect_workspace_bytes(int64_t n_tiles, int64_t K);

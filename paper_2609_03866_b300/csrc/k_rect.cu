@@ -25,6 +25,7 @@
 // across warps in shared memory and added to the output with integer
 // atomics.  A CTA whose union does not fit runs the same scan on global keys.
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -288,6 +289,468 @@ rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Points-on-lanes scan.  Lane l of warp w owns the outer points
+// w*256 + l + 32 q (q < 8) of the tile, so at every step the 32 lanes of a warp
+// hold 32 consecutive outer points: their window edges sit at neighbouring
+// positions of the staged keys (conflict-free shared-memory access) and the
+// loop over the lags of the group is warp-uniform.  A window edge is found in
+// O(1): a rank table over uniform bins of the coarse key range gives the first
+// key of the edge's bin, and a short walk inside the bin finishes.  The group's
+// lags are split into sub-groups whose key union fits the staging area; a
+// single lag whose union does not fit runs on the global keys.
+//
+// Staged entries.  Entry i of a sub-group holds the coarse key of window point
+// ia + i (relative to the segment's smallest query) and the prefix sum
+// P[ia + i] as three limbs p0, p1 (21 bits, unsigned) and p2 = P >> 42 (22 bits,
+// signed), so one 16-byte load at a window edge yields both the key the edge
+// search compares and the prefix sum the numerator needs.
+//
+// Numerators.  With p <= 61 - 1.5 log2(n_max) and |x_std| <= sqrt(n) the
+// quantised values satisfy |Y| < 2^61 and every window sum |w| < 2^62.  The
+// limb differences of w = P[hi] - P[lo] are d0, d1 in (-2^21, 2^21) and d2 (the
+// top-limb difference taken modulo 2^22, exact because |w| < 2^62), and
+// Y = y1 2^31 + y0 (y0 in [0, 2^31), |y1| < 2^30), so the six 32 x 32 -> 64-bit
+// products y_a d_b are below 2^52 each; they are accumulated in six int64 sums
+// (2^11 items of headroom, 8 are used) and combined to 128 bits once per
+// (lane, lag), then reduced across the warp.  Lane k of each warp keeps lag k's
+// running sum.
+// ---------------------------------------------------------------------------
+constexpr int kPtWarps = 8;
+constexpr int kPtM = kRectTile / (kPtWarps * 32);  // outer points per lane
+constexpr int kPtBatch = 4;                         // points of a lane handled together (load ILP)
+constexpr int kPtCap = 4000;                        // staged entries per sub-group
+constexpr int kPtBinsLog = 13;
+constexpr int kPtBins = 1 << kPtBinsLog;            // rank-table bins
+static_assert(kPtBins % (kPtWarps * 32) == 0, "bins split evenly over the threads");
+static_assert(16 * (kPtCap + 1) <= 65535, "rank-table entries are 16-bit byte offsets");
+static_assert(kPtM % kPtBatch == 0, "whole batches");
+
+struct PtSub {
+    int ka, kb, global, pad;
+    int64_t ia, ib, dmin, dmax;
+};
+
+struct __align__(16) PtSmem {
+    int4 sE[kPtCap + 1];                // {key, p0, p1, p2}; entry nK carries the sentinel key
+    uint16_t sT[kPtBins];               // byte offset into sE of the bin's first entry
+    int4 lc[kLagGroup];                 // lag offsets relative to vmin: dlc, dlc2, duc, duc2
+    int64_t klo[kLagGroup], khi[kLagGroup];
+    PtSub sub[kLagGroup];
+    int2 seg[16];                       // stack of outer-point segments [pa, pb) still to do
+    int n_sub, n_seg;
+    unsigned int pc[kPtWarps][32];
+    unsigned long long pl[kPtWarps][32], ph[kPtWarps][32];
+};
+constexpr unsigned kOffE = offsetof(PtSmem, sE);
+constexpr unsigned kOffT = offsetof(PtSmem, sT);
+
+__device__ __forceinline__ int4 pt_ent(const unsigned char *S, unsigned off) {
+    return *reinterpret_cast<const int4 *>(S + kOffE + off);
+}
+__device__ __forceinline__ unsigned pt_bin(const unsigned char *S, int32_t v, int bsh) {
+    return *reinterpret_cast<const uint16_t *>(S + kOffT + 2u * (unsigned)(v >> bsh));
+}
+
+// Window edges inside the coarse band: full keys, then the FP64 predicate of
+// Algorithm 6 on the caller's own values.  Out of line, so that none of its
+// loads are hoisted into the common path.  lo, hi are staged indices.
+__device__ __noinline__ int2 pt_band(const int64_t *__restrict__ Tx, const double *__restrict__ tx,
+                                     const int64_t *__restrict__ Sy, const double *__restrict__ sy,
+                                     const int64_t *__restrict__ dls, const int64_t *__restrict__ dus,
+                                     const double *__restrict__ slags, int64_t j, int64_t k, int eps,
+                                     double h, int64_t eta, int64_t ia_s, int64_t lim, int lo, int hi,
+                                     int fix_lo, int fix_hi) {
+    const int64_t Sj = Sy[j];
+    const double cj = centre(sy[j], slags[k], eps);
+    if (fix_lo) {
+        const int64_t Lf = Sj + dls[k];
+        const double lb = __dsub_rn(cj, h);
+        int64_t p = ia_s + lo;
+        while (p < lim && Tx[p] < Lf + eta && (Tx[p] < Lf - eta || tx[p] < lb)) ++p;
+        lo = (int)(p - ia_s);
+    }
+    if (hi < lo) hi = lo;
+    if (fix_hi || hi == lo) {
+        const int64_t Uf = Sj + dus[k];
+        const double ub = __dadd_rn(cj, h);
+        int64_t p = ia_s + hi;
+        while (p < lim && Tx[p] < Uf + eta && (Tx[p] < Uf - eta || tx[p] <= ub)) ++p;
+        hi = (int)(p - ia_s);
+    }
+    return make_int2(lo, hi);
+}
+
+struct PtAcc { long long a00, a01, a02, a10, a11, a12; };
+
+__device__ __forceinline__ void pt_mac(PtAcc &A, const int4 &el, const int4 &eh, int32_t y0, int32_t y1) {
+    const int32_t d0 = eh.y - el.y, d1 = eh.z - el.z;
+    const int32_t d2 = (int32_t)((unsigned)(eh.w - el.w) << 10) >> 10;  // modulo 2^22, sign-extended
+    // 32 x 32 -> 64-bit multiply-adds in one instruction each
+#define NCF_MADW(acc, a, b) asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b))
+    NCF_MADW(A.a00, y0, d0);
+    NCF_MADW(A.a01, y0, d1);
+    NCF_MADW(A.a02, y0, d2);
+    NCF_MADW(A.a10, y1, d0);
+    NCF_MADW(A.a11, y1, d1);
+    NCF_MADW(A.a12, y1, d2);
+#undef NCF_MADW
+}
+
+// a 2^e added to the 128-bit two's-complement value (lo, hi), 0 < e < 64
+template <int e>
+__device__ __forceinline__ void pt_add_shifted(unsigned long long &lo, unsigned long long &hi, long long a) {
+    const unsigned long long l = (unsigned long long)a << e;
+    const unsigned long long h = (unsigned long long)(a >> (64 - e));
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(l), "l"(h));
+}
+
+__device__ __forceinline__ U128 pt_combine(const PtAcc &A) {
+    unsigned long long lo = (unsigned long long)A.a00;
+    unsigned long long hi = (unsigned long long)(A.a00 >> 63) + ((unsigned long long)A.a12 << 9);  // a12 2^73
+    pt_add_shifted<21>(lo, hi, A.a01);
+    pt_add_shifted<31>(lo, hi, A.a10);
+    pt_add_shifted<42>(lo, hi, A.a02);
+    pt_add_shifted<52>(lo, hi, A.a11);
+    return U128{lo, hi};
+}
+
+__device__ __forceinline__ void add128x(U128 &a, const U128 &b) {
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(b.lo), "l"(b.hi));
+}
+__device__ __forceinline__ U128 shfl_xor128(const U128 &v, int o) {
+    return U128{__shfl_xor_sync(0xffffffffu, v.lo, o), __shfl_xor_sync(0xffffffffu, v.hi, o)};
+}
+__device__ __forceinline__ void warp_sum128(U128 &a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+        const unsigned long long hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+        add128(a, lo, hi);
+    }
+}
+
+struct PtLagArgs {
+    const int64_t *Tx, *Sy, *dls, *dus;
+    const double *tx, *sy, *slags;
+    int64_t j0, k, ia_s, lim, eta;
+    double h;
+    int eps, bsh, pa, pb;
+};
+
+// One lag over this lane's outer points of the segment [pa, pb) (the whole
+// full tile when kFull).  Points are handled kPtBatch at a time: the bin and
+// entry loads of a batch are issued together, then the short walks, one test
+// for the (rare) band, and the numerators.
+template <bool kFull>
+__device__ __forceinline__ void pt_lag(const unsigned char *S, const int32_t (&sc)[kPtM],
+                                       const int32_t (&y0)[kPtM], const int32_t (&y1)[kPtM], int pbase,
+                                       int32_t sca, int4 L, const PtLagArgs &g, unsigned &c, PtAcc &A) {
+#pragma unroll
+    for (int q0 = 0; q0 < kPtM; q0 += kPtBatch) {
+        int32_t s[kPtBatch];
+        bool ok[kPtBatch];
+#pragma unroll
+        for (int i = 0; i < kPtBatch; ++i) {
+            const int pt = pbase + 32 * (q0 + i);
+            ok[i] = kFull || (pt >= g.pa && pt < g.pb);
+            s[i] = ok[i] ? sc[q0 + i] : sca;  // a point outside the segment queries in range, counts nothing
+        }
+        unsigned ol[kPtBatch], oh[kPtBatch];
+        int4 el[kPtBatch], eh[kPtBatch];
+#pragma unroll
+        for (int i = 0; i < kPtBatch; ++i) {
+            ol[i] = pt_bin(S, s[i] + L.x, g.bsh);
+            oh[i] = pt_bin(S, s[i] + L.z, g.bsh);
+        }
+#pragma unroll
+        for (int i = 0; i < kPtBatch; ++i) {
+            el[i] = pt_ent(S, ol[i]);
+            eh[i] = pt_ent(S, oh[i]);
+        }
+        bool band = false;
+#pragma unroll
+        for (int i = 0; i < kPtBatch; ++i) {
+            const int32_t vl = s[i] + L.x, vh = s[i] + L.z;
+            while (el[i].x < vl) el[i] = pt_ent(S, ol[i] += 16u);
+            while (eh[i].x < vh) eh[i] = pt_ent(S, oh[i] += 16u);
+            band |= ok[i] && ((el[i].x < s[i] + L.y) || (eh[i].x < s[i] + L.w));
+        }
+        if (band) {
+#pragma unroll
+            for (int i = 0; i < kPtBatch; ++i) {
+                const bool fl = el[i].x < s[i] + L.y, fh = eh[i].x < s[i] + L.w;
+                if (ok[i] && (fl || fh)) {
+                    const int2 r = pt_band(g.Tx, g.tx, g.Sy, g.sy, g.dls, g.dus, g.slags,
+                                           g.j0 + pbase + 32 * (q0 + i), g.k, g.eps, g.h, g.eta, g.ia_s, g.lim,
+                                           (int)(ol[i] >> 4), (int)(oh[i] >> 4), fl, fh);
+                    ol[i] = 16u * (unsigned)r.x;
+                    oh[i] = 16u * (unsigned)r.y;
+                    el[i] = pt_ent(S, ol[i]);
+                    eh[i] = pt_ent(S, oh[i]);
+                }
+            }
+        }
+        // off the band, oh >= ol: the upper query is not below the lower one
+#pragma unroll
+        for (int i = 0; i < kPtBatch; ++i) {
+            if (kFull || ok[i]) {
+                c += oh[i] - ol[i];
+                pt_mac(A, el[i], eh[i], y0[q0 + i], y1[q0 + i]);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kPtWarps * 32, 2)
+rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
+                    const double *__restrict__ tx, const int64_t *__restrict__ offs_x,
+                    const int64_t *__restrict__ Sy, const int64_t *__restrict__ Yq,
+                    const double *__restrict__ sy, const ScanTile *__restrict__ tiles, int G,
+                    const RectRange *__restrict__ ranges, const double *__restrict__ slags,
+                    const int32_t *__restrict__ perm, const int64_t *__restrict__ dls,
+                    const int64_t *__restrict__ dus, const int64_t *__restrict__ gmin,
+                    const int64_t *__restrict__ gmax, int64_t K, int eps,
+                    double h, int64_t eta, unsigned long long *__restrict__ cnt,
+                    unsigned long long *__restrict__ num128) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PtSmem &sm = *reinterpret_cast<PtSmem *>(smem_raw);
+    const unsigned char *S = smem_raw;
+    const int64_t tI = blockIdx.x / G;
+    const int g = (int)(blockIdx.x - tI * G);
+    const ScanTile tile = tiles[tI];
+    const RectRange rg = ranges[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tid = threadIdx.x;
+    const int64_t xb = offs_x[tile.b + 1];
+    const int tn = (int)(tile.j1 - tile.j0);
+    const int64_t S0 = Sy[tile.j0], Slast = Sy[tile.j1 - 1];
+    const int64_t k0 = (int64_t)g * kLagGroup;
+    const int nk = (int)min((int64_t)kLagGroup, K - k0);
+    const int64_t ia = rg.ia, ib = min(rg.ib, xb);
+    // coarse shift: every coarse value of the CTA below 2^29 (as in the lags-on-lanes scan)
+    int sh = 0;
+    {
+        const int64_t span = (Slast - S0) + (gmax[g] - gmin[g]) + 4 * eta + 16;
+        const int bits = 64 - __clzll((unsigned long long)max(span, (int64_t)1));
+        sh = max(0, bits - 28);
+    }
+    // this lane's outer points: coarse offsets and the two limbs of Y
+    int32_t sc[kPtM], y0[kPtM], y1[kPtM];
+    const int pbase = warp * 32 * kPtM + lane;
+#pragma unroll
+    for (int q = 0; q < kPtM; ++q) {
+        const int pt = pbase + 32 * q;
+        const int64_t Y = pt < tn ? Yq[tile.j0 + pt] : 0;
+        sc[q] = pt < tn ? (int32_t)((Sy[tile.j0 + pt] - S0) >> sh) : 0;
+        y0[q] = (int32_t)(Y & 0x7fffffffll);
+        y1[q] = (int32_t)(Y >> 31);
+    }
+    if (tid == 0) {
+        sm.seg[0] = make_int2(0, tn);
+        sm.n_seg = 1;
+    }
+    unsigned int my_c = 0;
+    U128 my{0ull, 0ull};
+    for (;;) {
+        __syncthreads();
+        const int n_seg = sm.n_seg;
+        if (n_seg == 0) break;
+        const int2 seg = sm.seg[n_seg - 1];
+        const int pa = seg.x, pb = seg.y;
+        __syncthreads();  // every thread has read the segment before warp 0 edits the stack
+        // plan the segment: lag sub-groups whose key unions fit the staging area,
+        // or a split of the segment when one lag's union does not fit
+        if (warp == 0) {
+            if (pa == 0 && pb == tn && ib - ia + 1 <= kPtCap) {
+                if (lane == 0) {
+                    sm.sub[0] = PtSub{0, nk, 0, 0, ia, ib, gmin[g], gmax[g]};
+                    sm.n_sub = 1;
+                    sm.n_seg = n_seg - 1;
+                }
+            } else {
+                const int64_t Sa = Sy[tile.j0 + pa], Sb = Sy[tile.j0 + pb - 1];
+                int big = 0, wide = 0;
+                if (lane < nk) {
+                    const int64_t dl = dls[k0 + lane], du = dus[k0 + lane];
+                    const int64_t lo = lower_bound64(Tx, ia, ib, Sa + dl - eta);
+                    const int64_t hi = lower_bound64(Tx, lo, ib, Sb + du + eta);
+                    sm.klo[lane] = lo;
+                    sm.khi[lane] = hi;
+                    big = hi - lo + 1 > kPtCap;
+                    // a single outer point's window already fills half the area:
+                    // splitting would not help, the lag runs on the global keys
+                    if (big) wide = lower_bound64(Tx, lo, ib, Sa + du + eta) - lo + 1 > kPtCap / 2;
+                }
+                const bool split = __any_sync(0xffffffffu, big && !wide) && pb - pa > 32;
+                __syncwarp();
+                if (lane == 0) {
+                    if (split) {
+                        const int mid = pa + ((((pb - pa) >> 1) + 31) & ~31);
+                        sm.seg[n_seg - 1] = make_int2(mid, pb);
+                        sm.seg[n_seg] = make_int2(pa, mid);
+                        sm.n_seg = n_seg + 1;
+                        sm.n_sub = 0;
+                    } else {
+                        int n = 0, a = 0;
+                        while (a < nk) {
+                            int64_t lo = sm.klo[a], hi = sm.khi[a];
+                            int64_t dmn = dls[k0 + a], dmx = dus[k0 + a];
+                            int b = a + 1;
+                            const int gl = (hi - lo + 1 > kPtCap) ? 1 : 0;
+                            while (!gl && b < nk) {
+                                const int64_t nlo = min(lo, sm.klo[b]), nhi = max(hi, sm.khi[b]);
+                                if (nhi - nlo + 1 > kPtCap) break;
+                                lo = nlo;
+                                hi = nhi;
+                                dmn = min(dmn, dls[k0 + b]);
+                                dmx = max(dmx, dus[k0 + b]);
+                                ++b;
+                            }
+                            sm.sub[n++] = PtSub{a, b, gl, 0, lo, hi, dmn, dmx};
+                            a = b;
+                        }
+                        sm.n_sub = n;
+                        sm.n_seg = n_seg - 1;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        const int n_sub = sm.n_sub;
+        const bool full = pa == 0 && pb == kRectTile;
+        // coarse offsets of the segment's first and last outer points
+        const int32_t sca = (int32_t)((Sy[tile.j0 + pa] - S0) >> sh);
+        const int32_t scb = (int32_t)((Sy[tile.j0 + pb - 1] - S0) >> sh);
+        for (int s = 0; s < n_sub; ++s) {
+            const PtSub sb = sm.sub[s];
+            const int64_t lim = min(sb.ib + 1, xb);
+            if (!sb.global) {
+                const int64_t base = S0 + sb.dmin - eta;
+                const int64_t t_last = min(sb.ib, xb - 1);
+                const int nK = (int)(t_last - sb.ia + 1);
+                // queries of the segment lie in [vmin, vmax]; keys and lag offsets
+                // are stored relative to vmin, the bins cover [0, vmax - vmin]
+                const int32_t vmin = sca + (int32_t)((S0 + sb.dmin - eta - base) >> sh);
+                const int32_t vmax = scb + (int32_t)((S0 + sb.dmax + eta - base) >> sh) + 2;
+                const int vbits = 32 - __clz(max(vmax - vmin, 1));
+                const int bsh = max(0, vbits - kPtBinsLog);
+                // entries 0 .. nK: keys (nK: the sentinel) and the limbs of P[ia + i]
+                for (int i = tid; i <= max(nK, 0); i += blockDim.x) {
+                    int32_t key = kSentinel;
+                    if (i < nK) {
+                        const int64_t v = ((Tx[sb.ia + i] - base) >> sh) - vmin;
+                        key = (int32_t)max(min(v, (int64_t)(1 << 30)), (int64_t)-1);
+                    }
+                    const int64_t pv = P[sb.ia + i];
+                    sm.sE[i] = make_int4(key, (int32_t)(pv & 0x1fffff), (int32_t)((pv >> 21) & 0x1fffff),
+                                         (int32_t)(pv >> 42));
+                }
+                if (tid < sb.kb - sb.ka) {
+                    const int k = (int)k0 + sb.ka + tid;
+                    const int64_t dl = dls[k], du = dus[k];
+                    sm.lc[sb.ka + tid] = make_int4((int32_t)((S0 + dl - eta - base) >> sh) - vmin,
+                                                   (int32_t)((S0 + dl + eta - base) >> sh) + 2 - vmin,
+                                                   (int32_t)((S0 + du - eta - base) >> sh) - vmin,
+                                                   (int32_t)((S0 + du + eta - base) >> sh) + 2 - vmin);
+                }
+                __syncthreads();
+                // rank table: sT[b] = 16 x (first index with key >= b << bsh); each
+                // thread merges 32 consecutive bins against the keys
+                {
+                    constexpr int kPer = kPtBins / (kPtWarps * 32);
+                    const int b0 = tid * kPer;
+                    const int32_t v0 = b0 << bsh;
+                    int lo = 0, hi = max(nK, 0);
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sm.sE[mid].x < v0) lo = mid + 1; else hi = mid;
+                    }
+                    int p = lo;
+#pragma unroll 4
+                    for (int b = b0; b < b0 + kPer; ++b) {
+                        const int32_t v = b << bsh;
+                        while (sm.sE[p].x < v) ++p;
+                        sm.sT[b] = (uint16_t)(16 * p);
+                    }
+                }
+                __syncthreads();
+                PtLagArgs ga{Tx, Sy, dls, dus, tx, sy, slags, tile.j0, 0, sb.ia, lim, eta, h, eps, bsh, pa, pb};
+                for (int kl = sb.ka; kl < sb.kb; ++kl) {
+                    const int4 L = sm.lc[kl];
+                    ga.k = k0 + kl;
+                    unsigned int c = 0;
+                    PtAcc A{0, 0, 0, 0, 0, 0};
+                    if (full)
+                        pt_lag<true>(S, sc, y0, y1, pbase, sca, L, ga, c, A);
+                    else
+                        pt_lag<false>(S, sc, y0, y1, pbase, sca, L, ga, c, A);
+                    c = __reduce_add_sync(0xffffffffu, c >> 4);
+                    U128 acc = pt_combine(A);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) add128x(acc, shfl_xor128(acc, o));
+                    if (lane == kl) {
+                        my_c += c;
+                        add128x(my, acc);
+                    }
+                }
+                __syncthreads();  // the staging area is rewritten next
+            } else {
+                // one lag whose union does not fit: binary searches on the global keys
+                for (int kl = sb.ka; kl < sb.kb; ++kl) {
+                    const int64_t dl = dls[k0 + kl], du = dus[k0 + kl];
+                    const double tau = slags[k0 + kl];
+                    unsigned int c = 0;
+                    U128 acc{0ull, 0ull};
+                    for (int q = 0; q < kPtM; ++q) {
+                        const int pt = pbase + 32 * q;
+                        if (pt < pa || pt >= pb) continue;
+                        const int64_t j = tile.j0 + pt;
+                        const int64_t Lf = Sy[j] + dl, Uf = Sy[j] + du;
+                        int64_t lo = lower_bound64(Tx, sb.ia, sb.ib, Lf - eta);
+                        if (lo < lim && Tx[lo] < Lf + eta) {
+                            const double lb = __dsub_rn(centre(sy[j], tau, eps), h);
+                            while (lo < lim && Tx[lo] < Lf + eta && tx[lo] < lb) ++lo;
+                        }
+                        int64_t hi = max(lo, lower_bound64(Tx, lo, sb.ib, Uf - eta));
+                        if (hi < lim && Tx[hi] < Uf + eta) {
+                            const double ub = __dadd_rn(centre(sy[j], tau, eps), h);
+                            while (hi < lim && Tx[hi] < Uf + eta && tx[hi] <= ub) ++hi;
+                        }
+                        c += (unsigned int)(hi - lo);
+                        const long long w = (long long)((unsigned long long)P[hi] - (unsigned long long)P[lo]);
+                        mac128(acc, w, Yq[j]);
+                    }
+                    c = __reduce_add_sync(0xffffffffu, c);
+                    warp_sum128(acc);
+                    if (lane == kl) {
+                        my_c += c;
+                        add128(my, acc.lo, acc.hi);
+                    }
+                }
+            }
+        }
+    }
+    sm.pc[warp][lane] = my_c;
+    sm.pl[warp][lane] = my.lo;
+    sm.ph[warp][lane] = my.hi;
+    __syncthreads();
+    if (warp == 0 && lane < nk) {
+        unsigned long long cs = 0;
+        U128 a{0ull, 0ull};
+        for (int w = 0; w < kPtWarps; ++w) {
+            cs += sm.pc[w][lane];
+            add128(a, sm.pl[w][lane], sm.ph[w][lane]);
+        }
+        const int64_t k = k0 + lane;
+        const int64_t slot = (int64_t)tile.b * K + (perm ? perm[k] : k);
+        atomicAdd(cnt + slot, cs);
+        const unsigned long long old = atomicAdd(num128 + 2 * slot, a.lo);
+        const unsigned long long carry = (old + a.lo < old) ? 1ull : 0ull;
+        atomicAdd(num128 + 2 * slot + 1, a.hi + carry);
+    }
+}
+
 size_t al(size_t b) { return (b + 255) & ~size_t(255); }
 
 }  // namespace
@@ -392,6 +855,8 @@ ncf_status rect_launch(const RectArgs &a, const RectPrepared &r, cudaStream_t st
         cudaFuncSetAttribute(rect_scan_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(rect_scan_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(rect_scan_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(rect_scan_pt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(PtSmem));
         attr_set = true;
     }
 #define NCF_RECT_SCAN(RUN)                                                                              \
@@ -402,6 +867,12 @@ ncf_status rect_launch(const RectArgs &a, const RectPrepared &r, cudaStream_t st
     switch (r.variant) {
         case 0: NCF_RECT_SCAN(16); break;
         case 2: NCF_RECT_SCAN(64); break;
+        case 3:
+            NCF_LAUNCH("rect_scan_pt_kernel", st,
+                       rect_scan_pt_kernel<<<(unsigned)nr, kPtWarps * 32, sizeof(PtSmem), st>>>(
+                           a.Tx, a.P, a.tx, a.offs_x, a.Sy, a.Yq, a.sy, tiles, (int)r.G, ranges, r.slags,
+                           r.perm, r.dls, r.dus, r.gmin, r.gmax, a.K, a.eps, a.h, a.fs.eta, a.cnt, a.num128));
+            break;
         default: NCF_RECT_SCAN(32); break;
     }
 #undef NCF_RECT_SCAN
