@@ -244,9 +244,8 @@ def main():
     ap.add_argument("--batch", type=int, default=B_SERIES, help="series per rank (profiling runs)")
     args = ap.parse_args()
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2609_03866_b300 import shard
+    rank, world, local = shard.dist_env()
     if args.impl == "reference":
         return reference_arm(args, rank, world)
 
@@ -264,7 +263,7 @@ def main():
             dist.barrier()
 
     # ---- workload (each rank its own batch: weak scaling) ----
-    w = synth.light_curves(B=args.batch, K=K_LAGS, seed=synth.BASE_SEED + rank)
+    w = synth.light_curves(B=args.batch, K=K_LAGS, seed=shard.rank_seed(synth.BASE_SEED, rank))
     offs = w.offs
     t = torch.from_numpy(w.t).to(dev)
     x = torch.from_numpy(w.x).to(dev)
@@ -307,10 +306,7 @@ def main():
     ctx.profile(False)
     step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = shard.max_over_ranks(total_ms, device=dev)
     units = 2.0 * B * K * args.steps * world
     value = units / (total_ms / 1e3)
 
