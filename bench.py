@@ -41,6 +41,13 @@ METRIC = "series*lags/s, batched FP32 form (Gaussian) + exact rectangle scan, 40
 WORKLOAD = "light_curves: 4096 series, n log-uniform [200, 2e5], 256 lags on [0, 200] d, Gaussian h=0.5 + rectangle h=0.5"
 
 
+# DRAM bytes per launch of a kernel at the default workload (4096 light curves x 256
+# lags), dram__bytes_read.sum + dram__bytes_write.sum from one single-pass ncu capture of
+# this command.  Reported as the roofline's traffic only for that workload; update or
+# remove an entry whenever its kernel changes.
+MEASURED_TRAFFIC = {("rect_scan_pt_kernel", 4096): 3.02e9 + 32.2e6}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -421,6 +428,7 @@ def main():
         roof = {"bound": "hbm", "achieved": byts / per_launch_s / 1e9, "peak": hbm, "unit": "GB/s",
                 "frac": byts / per_launch_s / 1e9 / hbm, "traffic": None, "kernel": name,
                 "peak_source": src}
+    roof["traffic"] = MEASURED_TRAFFIC.get((name, B))
     roof["share"] = share
 
     line = {
