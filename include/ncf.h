@@ -237,18 +237,30 @@ NCF_API void ncf_plan_destroy(ncf_plan *plan);
  * (each [K], NULL to skip) to host memory, returns the request's status and
  * its latency (submit to completion).  ncf_server_latency reports the 50th
  * and 99th percentile latencies of all completed requests.
+ *
+ * Resident series: ncf_server_put copies a series (host t, x; n >= 2 points)
+ * once into device memory owned by the server, charged to the memory budget
+ * until ncf_server_drop, and returns its handle (NCF_EBUSY when the budget
+ * cannot hold it).  A request names resident series through x_series /
+ * y_series; their host pointers and sizes are then ignored and nothing is
+ * copied per request.  ncf_server_drop returns NCF_EBUSY while an admitted
+ * request still uses the series, NCF_EINVAL for an unknown handle.
  */
 typedef struct {
-    const double *t, *x;   /* HOST, nx points, t non-decreasing */
+    const double *t, *x;   /* HOST, nx points, t non-decreasing (ignored when x_series != 0) */
     int64_t nx;
-    const double *s, *y;   /* HOST, ny points (NULL, NULL for an ACF) */
+    const double *s, *y;   /* HOST, ny points (NULL, NULL for an ACF; ignored when y_series != 0) */
     int64_t ny;
     const double *lags;    /* HOST [K] */
     int64_t K;
     ncf_options opt;
+    uint64_t x_series;     /* 0, or a resident series used as (t, x) */
+    uint64_t y_series;     /* 0, or a resident series used as (s, y): a CCF */
 } ncf_request;
 typedef struct ncf_server ncf_server;
 NCF_API ncf_status ncf_server_create(int device, size_t mem_budget_bytes, int slots, ncf_server **out);
+NCF_API ncf_status ncf_server_put(ncf_server *srv, const double *t, const double *x, int64_t n, uint64_t *series);
+NCF_API ncf_status ncf_server_drop(ncf_server *srv, uint64_t series);
 NCF_API ncf_status ncf_server_submit(ncf_server *srv, const ncf_request *req, uint64_t *ticket);
 NCF_API ncf_status ncf_server_poll(ncf_server *srv, uint64_t ticket, int *done);
 NCF_API ncf_status ncf_server_wait(ncf_server *srv, uint64_t ticket, double *c_out, double *b_out,

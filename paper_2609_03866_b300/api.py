@@ -376,7 +376,8 @@ class Plan:
 class ncf_request(ctypes.Structure):
     _fields_ = [("t", ctypes.c_void_p), ("x", ctypes.c_void_p), ("nx", ctypes.c_int64),
                 ("s", ctypes.c_void_p), ("y", ctypes.c_void_p), ("ny", ctypes.c_int64),
-                ("lags", ctypes.c_void_p), ("K", ctypes.c_int64), ("opt", ncf_options)]
+                ("lags", ctypes.c_void_p), ("K", ctypes.c_int64), ("opt", ncf_options),
+                ("x_series", ctypes.c_uint64), ("y_series", ctypes.c_uint64)]
 
 
 class Server:
@@ -401,6 +402,10 @@ class Server:
             L.ncf_server_latency.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_uint64)]
             L.ncf_server_latency.restype = ctypes.c_int
+            L.ncf_server_put.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
+            L.ncf_server_put.restype = ctypes.c_int
+            L.ncf_server_drop.argtypes = [vp, ctypes.c_uint64]
+            L.ncf_server_drop.restype = ctypes.c_int
             L.ncf_server_destroy.argtypes = [vp]
             L.ncf_server_destroy.restype = None
             L._server_types = True
@@ -410,14 +415,34 @@ class Server:
             raise NcfError(rc, status_name(rc), "ncf_server_create failed")
         self._keep = {}
 
+    def put(self, t, x) -> int:
+        """Copies a series to device memory held by the server (charged to its
+        budget) and returns its handle for submit(x_series=..., y_series=...)."""
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        h = ctypes.c_uint64()
+        rc = lib().ncf_server_put(self._h, t.ctypes.data, x.ctypes.data, t.size, ctypes.byref(h))
+        if rc != 0:
+            raise NcfError(rc, status_name(rc), "ncf_server_put failed")
+        return h.value
+
+    def drop(self, series: int):
+        rc = lib().ncf_server_drop(self._h, int(series))
+        if rc != 0:
+            raise NcfError(rc, status_name(rc), "ncf_server_drop failed")
+
     def submit(self, t, x, lags, kernel="gaussian", h=1.0, s=None, y=None, path="auto", precision="fp64",
-               norm="none", trunc_R=0.0, tol=0.0):
+               norm="none", trunc_R=0.0, tol=0.0, x_series=0, y_series=0):
+        """t, x (or x_series) and, for a CCF, s, y (or y_series); t, x may be None
+        when x_series names a resident series."""
         arrs = [np.ascontiguousarray(a, dtype=np.float64) if a is not None else None for a in (t, x, s, y, lags)]
         t, x, s, y, lags = arrs
         r = ncf_request()
-        r.t, r.x, r.nx = t.ctypes.data, x.ctypes.data, t.size
+        if t is not None:
+            r.t, r.x, r.nx = t.ctypes.data, x.ctypes.data, t.size
         if s is not None:
             r.s, r.y, r.ny = s.ctypes.data, y.ctypes.data, s.size
+        r.x_series, r.y_series = int(x_series), int(y_series)
         r.lags, r.K = lags.ctypes.data, lags.size
         r.opt = make_options(kernel, h, path, precision, norm, trunc_R, tol)
         tk = ctypes.c_uint64()

@@ -15,6 +15,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -22,6 +24,7 @@
 #include "spectral.cuh"
 
 #include <map>
+#include <mutex>
 
 // Per-context kernel profiler: CUDA events around every launch while enabled.
 struct NcfProfiler {
@@ -46,7 +49,6 @@ struct ncf_ctx {
     uint64_t launches = 0;
     cudaEvent_t staged = nullptr;  // recorded after staging copies issued past the read-back sync
     NcfProfiler prof;
-    std::map<uint64_t, int> tune_rect;  // autotuned rectangle-scan variant per problem bucket
     ncf_plan_info plan{0.0, 0, 0, 0, 0, 0};
     std::string err;
 };
@@ -666,8 +668,13 @@ uint64_t rect_tune_key(const Eval &ev) {
            ((uint64_t)ev.acf << 24);
 }
 
+// Autotuned rectangle-scan variant per (device, problem bucket), shared by
+// every context of the process (server slots, plans, one-shot calls).
+std::mutex g_tune_mu;
+std::map<std::pair<int, uint64_t>, int> g_tune_rect;
+
 // Times the rectangle-scan variants once per problem bucket (they give
-// identical, exact results) and keeps the fastest in the context.
+// identical, exact results) and keeps the fastest for the process.
 ncf_status tune_rect(ncf_ctx *ctx, Eval &ev, cudaStream_t st) {
     // NCF_RECT_VARIANT=0|1|2|3 pins a variant (tests, measurements) and skips the timing
     if (const char *pin = std::getenv("NCF_RECT_VARIANT")) {
@@ -677,11 +684,14 @@ ncf_status tune_rect(ncf_ctx *ctx, Eval &ev, cudaStream_t st) {
             return NCF_OK;
         }
     }
-    const uint64_t key = rect_tune_key(ev);
-    auto it = ctx->tune_rect.find(key);
-    if (it != ctx->tune_rect.end()) {
-        ev.r_main.variant = ev.r_x.variant = ev.r_y.variant = it->second;
-        return NCF_OK;
+    const std::pair<int, uint64_t> key{ctx->device, rect_tune_key(ev)};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_rect.find(key);
+        if (it != g_tune_rect.end()) {
+            ev.r_main.variant = ev.r_x.variant = ev.r_y.variant = it->second;
+            return NCF_OK;
+        }
     }
     const int64_t B = ev.B, K = ev.K;
     Side &X = ev.X, &O = ev.outer();
@@ -712,7 +722,10 @@ ncf_status tune_rect(ncf_ctx *ctx, Eval &ev, cudaStream_t st) {
         if (ms < best_ms) { best_ms = ms; best = v; }
     }
     for (auto &x : e) cudaEventDestroy(x);
-    ctx->tune_rect[key] = best;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_rect[key] = best;
+    }
     ev.r_main.variant = ev.r_x.variant = ev.r_y.variant = best;
     return NCF_OK;
 }

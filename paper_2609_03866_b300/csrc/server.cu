@@ -12,7 +12,9 @@
 // ones differ at most by summation order).
 //
 // Host buffers of a request (t, x, s, y, lags) must stay valid until
-// ncf_server_wait has returned for its ticket.
+// ncf_server_wait has returned for its ticket.  Series that many requests
+// share can be made resident (ncf_server_put): they are copied to the device
+// once, charged to the budget, and requests name them by handle.
 #include <algorithm>
 #include <cmath>
 #include <chrono>
@@ -31,9 +33,19 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// A series held in device memory for the server's lifetime (or until dropped).
+struct Resident {
+    double *t = nullptr, *x = nullptr;
+    int64_t n = 0;
+    double t_first = 0.0, t_last = 0.0;  // host copies for the admission estimate
+    size_t bytes = 0;
+    int refs = 0;                         // admitted requests using it
+};
+
 struct Request {
     uint64_t ticket = 0;
     ncf_request req{};
+    const Resident *rx = nullptr, *ry = nullptr;
     size_t est_bytes = 0;
     Clock::time_point t_submit, t_start, t_done;
     bool done = false;
@@ -56,17 +68,19 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 // Upper estimate of the device memory one request needs (inputs, outputs and
 // the context workspace of its path), read from its host buffers; used for
 // admission against the server's budget.
-size_t estimate_bytes(const ncf_request &r) {
-    const bool acf = r.s == nullptr;
-    const double n = (double)r.nx + (acf ? 0.0 : (double)r.ny);
+size_t estimate_bytes(const ncf_request &r, const Resident *rx, const Resident *ry) {
+    const bool acf = r.s == nullptr && ry == nullptr;
+    const int64_t nx = rx ? rx->n : r.nx, ny = acf ? 0 : (ry ? ry->n : r.ny);
+    const double n = (double)nx + (double)ny;
+    const double copied = (double)(rx ? 0 : nx) + (double)(ry ? 0 : ny);
     const double K = (double)r.K;
-    double bytes = 16.0 * n + 32.0 * K + 64.0 * n + 4096.0;  // inputs, outputs, statistics, keys, tables
+    double bytes = 16.0 * copied + 32.0 * K + 64.0 * n + 4096.0;  // inputs, outputs, statistics, keys, tables
     const bool spectral = r.opt.kernel == NCF_GAUSSIAN && r.opt.path != NCF_PATH_WINDOWED;
     if (spectral) {
-        double lo = r.t[0], hi = r.t[r.nx - 1];
+        double lo = rx ? rx->t_first : r.t[0], hi = rx ? rx->t_last : r.t[nx - 1];
         if (!acf) {
-            lo = std::min(lo, r.s[0]);
-            hi = std::max(hi, r.s[r.ny - 1]);
+            lo = std::min(lo, ry ? ry->t_first : r.s[0]);
+            hi = std::max(hi, ry ? ry->t_last : r.s[ny - 1]);
         }
         double max_tau = 0.0;
         for (int64_t k = 0; k < r.K; ++k) max_tau = std::max(max_tau, std::fabs(r.lags[k]));
@@ -98,15 +112,18 @@ struct ncf_server {
     std::condition_variable cv_work, cv_done;
     std::vector<double> latencies_ms;
     uint64_t completed = 0;
+    std::map<uint64_t, Resident> resident;
+    uint64_t next_series = 1;
 };
 
 namespace {
 
 void run_one(ncf_server *srv, Slot &sl, Request &rq) {
     const ncf_request &r = rq.req;
-    const bool acf = r.s == nullptr;
-    const int64_t nx = r.nx, ny = acf ? 0 : r.ny, K = r.K;
-    const size_t need = align256(nx * 8) * 2 + align256(ny * 8) * 2 + align256(K * 8) + align256(K * 8) * 2 +
+    const bool acf = r.s == nullptr && rq.ry == nullptr;
+    const int64_t nx = rq.rx ? rq.rx->n : r.nx, ny = acf ? 0 : (rq.ry ? rq.ry->n : r.ny), K = r.K;
+    const int64_t cx = rq.rx ? 0 : nx, cy = rq.ry ? 0 : ny;  // points copied for this request
+    const size_t need = align256(cx * 8) * 2 + align256(cy * 8) * 2 + align256(K * 8) + align256(K * 8) * 2 +
                         align256(K * 8);
     if (need > sl.dcap) {
         if (sl.dbuf) cudaFree(sl.dbuf);
@@ -122,16 +139,29 @@ void run_one(ncf_server *srv, Slot &sl, Request &rq) {
     }
     char *p = reinterpret_cast<char *>(sl.dbuf);
     auto take = [&](size_t bytes) { char *q = p; p += align256(bytes); return reinterpret_cast<double *>(q); };
-    double *dt = take(nx * 8), *dx = take(nx * 8);
-    double *ds = acf ? nullptr : take(ny * 8), *dy = acf ? nullptr : take(ny * 8);
+    double *dt, *dx, *ds = nullptr, *dy = nullptr;
+    if (rq.rx) {
+        dt = rq.rx->t;
+        dx = rq.rx->x;
+    } else {
+        dt = take(nx * 8);
+        dx = take(nx * 8);
+        cudaMemcpyAsync(dt, r.t, nx * 8, cudaMemcpyHostToDevice, sl.st);
+        cudaMemcpyAsync(dx, r.x, nx * 8, cudaMemcpyHostToDevice, sl.st);
+    }
+    if (!acf) {
+        if (rq.ry) {
+            ds = rq.ry->t;
+            dy = rq.ry->x;
+        } else {
+            ds = take(ny * 8);
+            dy = take(ny * 8);
+            cudaMemcpyAsync(ds, r.s, ny * 8, cudaMemcpyHostToDevice, sl.st);
+            cudaMemcpyAsync(dy, r.y, ny * 8, cudaMemcpyHostToDevice, sl.st);
+        }
+    }
     double *dl = take(K * 8), *dc = take(K * 8), *db = take(K * 8);
     int64_t *dn = reinterpret_cast<int64_t *>(take(K * 8));
-    cudaMemcpyAsync(dt, r.t, nx * 8, cudaMemcpyHostToDevice, sl.st);
-    cudaMemcpyAsync(dx, r.x, nx * 8, cudaMemcpyHostToDevice, sl.st);
-    if (!acf) {
-        cudaMemcpyAsync(ds, r.s, ny * 8, cudaMemcpyHostToDevice, sl.st);
-        cudaMemcpyAsync(dy, r.y, ny * 8, cudaMemcpyHostToDevice, sl.st);
-    }
     cudaMemcpyAsync(dl, r.lags, K * 8, cudaMemcpyHostToDevice, sl.st);
     rq.status = ncf_corr(sl.ctx, dt, dx, nx, ds, dy, ny, dl, K, &r.opt, dc, db, dn, sl.st);
     if (rq.status != NCF_OK) {
@@ -212,17 +242,79 @@ ncf_status ncf_server_create(int device, size_t mem_budget_bytes, int slots, ncf
     return NCF_OK;
 }
 
+ncf_status ncf_server_put(ncf_server *srv, const double *t, const double *x, int64_t n, uint64_t *series) {
+    if (!srv || !t || !x || n < 2 || !series) return NCF_EINVAL;
+    const size_t bytes = align256((size_t)n * 8) * 2;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (srv->reserved + bytes > srv->budget) return NCF_EBUSY;
+        srv->reserved += bytes;  // held while copying
+    }
+    Resident r;
+    r.n = n;
+    r.t_first = t[0];
+    r.t_last = t[n - 1];
+    r.bytes = bytes;
+    char *mem = nullptr;
+    cudaSetDevice(srv->device);
+    if (cudaMalloc(&mem, bytes) != cudaSuccess ||
+        cudaMemcpy(mem, t, (size_t)n * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(mem + align256((size_t)n * 8), x, (size_t)n * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        if (mem) cudaFree(mem);
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->reserved -= bytes;
+        return NCF_ENOMEM;
+    }
+    r.t = reinterpret_cast<double *>(mem);
+    r.x = reinterpret_cast<double *>(mem + align256((size_t)n * 8));
+    std::lock_guard<std::mutex> lk(srv->mu);
+    *series = srv->next_series++;
+    srv->resident[*series] = r;
+    return NCF_OK;
+}
+
+ncf_status ncf_server_drop(ncf_server *srv, uint64_t series) {
+    if (!srv) return NCF_EINVAL;
+    double *mem = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        auto it = srv->resident.find(series);
+        if (it == srv->resident.end()) return NCF_EINVAL;
+        if (it->second.refs > 0) return NCF_EBUSY;
+        mem = it->second.t;
+        srv->reserved -= it->second.bytes;
+        srv->resident.erase(it);
+    }
+    cudaSetDevice(srv->device);
+    cudaFree(mem);
+    return NCF_OK;
+}
+
 ncf_status ncf_server_submit(ncf_server *srv, const ncf_request *req, uint64_t *ticket) {
-    if (!srv || !req || !ticket || !req->t || !req->x || !req->lags || req->nx < 2 || req->K < 1 ||
-        ((req->s == nullptr) != (req->y == nullptr)) || (req->s && req->ny < 2))
+    if (!srv || !req || !ticket || !req->lags || req->K < 1) return NCF_EINVAL;
+    if (!req->x_series && (!req->t || !req->x || req->nx < 2)) return NCF_EINVAL;
+    if (!req->y_series && ((req->s == nullptr) != (req->y == nullptr) || (req->s && req->ny < 2)))
         return NCF_EINVAL;
     auto rq = std::make_shared<Request>();
     rq->req = *req;
-    rq->est_bytes = estimate_bytes(*req);
     std::lock_guard<std::mutex> lk(srv->mu);
+    if (req->x_series) {
+        auto it = srv->resident.find(req->x_series);
+        if (it == srv->resident.end()) return NCF_EINVAL;
+        rq->rx = &it->second;
+    }
+    if (req->y_series) {
+        auto it = srv->resident.find(req->y_series);
+        if (it == srv->resident.end()) return NCF_EINVAL;
+        rq->ry = &it->second;
+    }
+    rq->est_bytes = estimate_bytes(*req, rq->rx, rq->ry);
     const int in_flight = (int)srv->queue.size() + srv->busy;
     if (in_flight >= (int)srv->slots.size() || srv->reserved + rq->est_bytes > srv->budget) return NCF_EBUSY;
     srv->reserved += rq->est_bytes;
+    if (req->x_series) ++srv->resident[req->x_series].refs;
+    if (req->y_series) ++srv->resident[req->y_series].refs;
     rq->ticket = srv->next_ticket++;
     rq->t_submit = Clock::now();
     srv->requests[rq->ticket] = rq;
@@ -253,6 +345,8 @@ ncf_status ncf_server_wait(ncf_server *srv, uint64_t ticket, double *c_out, doub
         srv->cv_done.wait(lk, [&] { return rq->done; });
         srv->requests.erase(it);
         srv->reserved -= rq->est_bytes;
+        if (rq->req.x_series) --srv->resident[rq->req.x_series].refs;
+        if (rq->req.y_series) --srv->resident[rq->req.y_series].refs;
     }
     if (rq->status != NCF_OK) return rq->status;
     const size_t K = (size_t)rq->req.K;
@@ -298,6 +392,7 @@ void ncf_server_destroy(ncf_server *srv) {
         if (sl.ctx) ncf_destroy(sl.ctx);
         if (sl.st) cudaStreamDestroy(sl.st);
     }
+    for (auto &kv : srv->resident) cudaFree(kv.second.t);
     delete srv;
 }
 

@@ -78,3 +78,43 @@ def test_admission_budget_and_invalid_requests():
         srv.wait(tk)
     assert e.value.name == "NCF_ENOTSORTED"
     srv.close()
+
+
+def test_resident_series_give_the_same_results_and_hold_budget():
+    w = synth.light_curves(B=1, n_lo=30000, n_hi=30001, K=64)
+    c = synth.ou_ccf(nA=20000, nB=16000, K=48)
+    srv = api.Server(slots=2, mem_budget_bytes=4 << 30)
+    hx = srv.put(w.t, w.x)
+    ha, hb = srv.put(c.t, c.x), srv.put(c.s, c.y)
+    cases = [
+        (dict(t=None, x=None, lags=w.lags, kernel="rectangle", h=0.5, x_series=hx),
+         dict(t=w.t, x=w.x, lags=w.lags, kernel="rectangle", h=0.5)),
+        (dict(t=None, x=None, lags=w.lags, kernel="gaussian", h=0.5, precision="fp32", x_series=hx),
+         dict(t=w.t, x=w.x, lags=w.lags, kernel="gaussian", h=0.5, precision="fp32")),
+        (dict(t=None, x=None, lags=c.lags, kernel="rectangle", h=0.5, x_series=ha, y_series=hb),
+         dict(t=c.t, x=c.x, s=c.s, y=c.y, lags=c.lags, kernel="rectangle", h=0.5)),
+        (dict(t=None, x=None, lags=c.lags, kernel="gaussian", h=0.5, x_series=ha, y_series=hb),
+         dict(t=c.t, x=c.x, s=c.s, y=c.y, lags=c.lags, kernel="gaussian", h=0.5)),
+    ]
+    for res, host in cases:
+        a = srv.wait(srv.submit(**res))
+        b = srv.wait(srv.submit(**host))
+        assert np.array_equal(a["count"], b["count"])
+        # FP32 spreading adds into the grid with atomics: last-bit differences between runs
+        assert max_abs(a["c"], b["c"]) <= (1e-6 if res.get("precision") == "fp32" else 1e-12)
+    # a series in use cannot be dropped; afterwards it can, and the handle is gone
+    tk = srv.submit(None, None, w.lags, kernel="rectangle", h=0.5, x_series=hx)
+    with pytest.raises(api.NcfError) as e:
+        srv.drop(hx)
+    assert e.value.name == "NCF_EBUSY"
+    srv.wait(tk)
+    srv.drop(hx)
+    with pytest.raises(api.NcfError) as e:
+        srv.submit(None, None, w.lags, kernel="rectangle", h=0.5, x_series=hx)
+    assert e.value.name == "NCF_EINVAL"
+    srv.close()
+    tiny = api.Server(slots=1, mem_budget_bytes=1 << 16)
+    with pytest.raises(api.NcfError) as e:
+        tiny.put(w.t, w.x)
+    assert e.value.name == "NCF_EBUSY"
+    tiny.close()
