@@ -184,6 +184,36 @@ NCF_API ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, cons
                                const double *lags, int64_t K, const ncf_options *opt,
                                double *c_out, double *b_out, int64_t *count_out, void *stream);
 
+
+/*
+ * Bootstrap replicates of one ACF (s = y = NULL) or CCF, for per-lag sampling
+ * uncertainties.  The paper recommends weighing an estimate against its
+ * sampling variance by resampling or Monte-Carlo over realisations (Sec. 4,
+ * "Monte-Carlo over independent realizations"; Sec. 6) but provides no
+ * resampler; this entry point has no counterpart in it.
+ *
+ * Replicate r (0 <= r < n_boot) resamples the nx points of (t, x) with
+ * replacement, keeping time order, and for a CCF the ny points of (s, y)
+ * independently, then evaluates the estimator with *opt exactly as
+ * ncf_corr_batch would on the batch of replicates.  Draw j of replicate r on
+ * the x side is point floor(nx * u / 2^64), u = the SplitMix64 output number
+ * c = 2^32 r + j of the stream started at `seed` (output c is
+ * mix(seed + (c + 1) 0x9E3779B97F4A7C15) with the mixing of Steele, Lea and
+ * Flood); the y side uses the stream started at ~seed.
+ *
+ * All arrays are DEVICE pointers: t, x [nx] and s, y [ny] (t, s
+ * non-decreasing), lags [K], outputs c_out, b_out, count_out [n_boot][K]
+ * (b_out and count_out may be NULL).  nx, ny, n_boot < 2^32.  The replicates
+ * live in a context buffer of 16 (nx + ny) n_boot + 4 max(nx, ny) n_boot
+ * bytes.  Errors: NCF_EINVAL for NULL pointers or sizes out of range, the
+ * statuses of ncf_corr_batch otherwise (NCF_EDEGENERATE when a replicate
+ * drew a single distinct value, which short series make likely).
+ */
+NCF_API ncf_status ncf_corr_bootstrap(ncf_ctx *ctx, const double *t, const double *x, int64_t nx,
+                                      const double *s, const double *y, int64_t ny,
+                                      const double *lags, int64_t K, const ncf_options *opt,
+                                      int64_t n_boot, uint64_t seed, double *c_out, double *b_out,
+                                      int64_t *count_out, void *stream);
 /*
  * Plans: the analysis of one batch layout, lag set and options, done once,
  * for repeated launches that neither synchronise nor allocate, so a launch

@@ -240,3 +240,45 @@ def exact_gaussian(t, x, lags, h, s=None, y=None):
         dens.append(d)
         cs.append(n / max(d, mp.mpf("1e-16")))
     return nums, dens, cs
+
+
+# ---------------------------------------------------------------------------
+# Bootstrap replicates (the resampling the paper recommends for sampling
+# uncertainties, Sec. 4 "Monte-Carlo over independent realizations" and
+# Sec. 6).  Own implementation of the counter-based generator from its
+# published definition: SplitMix64 (Steele, Lea and Flood, "Fast splittable
+# pseudorandom number generators", OOPSLA 2014; constants of Vigna's reference
+# code), output number c of the stream started at `seed` being
+# mix(seed + (c + 1) * 0x9E3779B97F4A7C15 mod 2^64); an index in [0, n) is the
+# high word of u * n (Lemire's multiply-high reduction).  Pure Python integers.
+# ---------------------------------------------------------------------------
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int, c: int) -> int:
+    """Output number c (0-based) of the SplitMix64 stream started at seed."""
+    z = (seed + (c + 1) * 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def bootstrap_indices(n: int, seed: int, r: int) -> np.ndarray:
+    """The n point indices of bootstrap replicate r, drawn with replacement
+    (draw j = floor(n u / 2^64), u = output 2^32 r + j) and sorted, so the
+    replicate keeps time order."""
+    idx = [(splitmix64(seed & _M64, (r << 32) | j) * n) >> 64 for j in range(n)]
+    return np.sort(np.asarray(idx, dtype=np.int64), kind="stable")
+
+
+def bootstrap_corr(t, x, lags, r, seed, kernel="gaussian", h=1.0, s=None, y=None, method="windowed",
+                   trunc_R=0.0, norm="none"):
+    """The estimator on bootstrap replicate r: x side from the stream `seed`,
+    y side (a CCF) from the stream ~seed."""
+    t, x = np.asarray(t, dtype=np.float64), np.asarray(x, dtype=np.float64)
+    ix = bootstrap_indices(t.size, seed, r)
+    if s is None:
+        return corr(t[ix], x[ix], lags, kernel, h, norm=norm, method=method, trunc_R=trunc_R)
+    s, y = np.asarray(s, dtype=np.float64), np.asarray(y, dtype=np.float64)
+    iy = bootstrap_indices(s.size, ~seed & _M64, r)
+    return corr(t[ix], x[ix], lags, kernel, h, s=s[iy], y=y[iy], norm=norm, method=method, trunc_R=trunc_R)

@@ -243,6 +243,39 @@ def corr(t, x, lags, kernel="gaussian", h=1.0, s=None, y=None, path="auto", prec
     return {"c": c, "b": b, "count": cnt}
 
 
+def corr_bootstrap(t, x, lags, n_boot, seed=0, kernel="gaussian", h=1.0, s=None, y=None, path="auto",
+                   precision="fp64", norm="none", trunc_R=0.0, tol=0.0, ctx: Context | None = None, stream=None):
+    """n_boot bootstrap replicates of one ACF (s, y omitted) or CCF, resampled on the
+    GPU (ncf_corr_bootstrap).  Returns dict(c, b, count) of device tensors [n_boot, K]."""
+    import torch
+    L = lib()
+    if not getattr(L, "_boot_types", False):
+        vp = ctypes.c_void_p
+        L.ncf_corr_bootstrap.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, ctypes.c_int64,
+                                         ctypes.POINTER(ncf_options), ctypes.c_int64, ctypes.c_uint64, vp, vp, vp,
+                                         vp]
+        L.ncf_corr_bootstrap.restype = ctypes.c_int
+        L._boot_types = True
+    ctx = ctx or default_context()
+    dev = torch.device("cuda", ctx.device)
+    t, x, lags = _dev(t, dev), _dev(x, dev), _dev(lags, dev)
+    acf = s is None
+    if not acf:
+        s, y = _dev(s, dev), _dev(y, dev)
+    K = lags.numel()
+    rows = max(int(n_boot), 0)  # the library rejects n_boot < 1 itself
+    out = {"c": torch.empty(rows, K, dtype=torch.float64, device=dev),
+           "b": torch.empty(rows, K, dtype=torch.float64, device=dev),
+           "count": torch.empty(rows, K, dtype=torch.int64, device=dev)}
+    o = make_options(kernel, h, path, precision, norm, trunc_R, tol)
+    rc = L.ncf_corr_bootstrap(ctx.handle, _ptr(t), _ptr(x), t.numel(), _ptr(None if acf else s),
+                              _ptr(None if acf else y), 0 if acf else s.numel(), _ptr(lags), K, ctypes.byref(o),
+                              int(n_boot), int(seed) & ((1 << 64) - 1), _ptr(out["c"]), _ptr(out["b"]),
+                              _ptr(out["count"]), _stream_handle(stream, dev))
+    ctx.check(rc)
+    return out
+
+
 def _host_offs(offs):
     o = np.ascontiguousarray(np.asarray(offs.cpu() if hasattr(offs, "cpu") else offs, dtype=np.int64))
     return o, ctypes.c_void_p(o.ctypes.data)

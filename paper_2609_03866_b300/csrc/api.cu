@@ -46,6 +46,8 @@ struct ncf_ctx {
     size_t pinned_cap = 0;
     char *hbuf = nullptr;        // device copies of host inputs (ncf_corr_batch_host)
     size_t hbuf_cap = 0;
+    char *boot = nullptr;        // bootstrap replicates and their multiplicities
+    size_t boot_cap = 0;
     uint64_t launches = 0;
     cudaEvent_t staged = nullptr;  // recorded after staging copies issued past the read-back sync
     NcfProfiler prof;
@@ -83,8 +85,9 @@ namespace ncf {
 namespace {
 
 struct LaunchScope {
-    explicit LaunchScope(ncf_ctx *c) { tls_ctx = c; }
-    ~LaunchScope() { tls_ctx = nullptr; }
+    ncf_ctx *prev;
+    explicit LaunchScope(ncf_ctx *c) : prev(tls_ctx) { tls_ctx = c; }
+    ~LaunchScope() { tls_ctx = prev; }
 };
 
 ncf_status fail(ncf_ctx *ctx, ncf_status s, const char *fmt, ...) {
@@ -839,6 +842,7 @@ void ncf_destroy(ncf_ctx *ctx) {
     if (ctx->staged) cudaEventDestroy(ctx->staged);
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
     delete ctx;
+    if (ctx->boot) cudaFree(ctx->boot);
 }
 
 ncf_status ncf_last_plan(const ncf_ctx *ctx, ncf_plan_info *out) {
@@ -914,6 +918,47 @@ ncf_status ncf_corr_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *t, 
     if (cudaSetDevice(ctx->device) != cudaSuccess) return NCF_ECUDA;
     return ncf::corr_batch_impl(ctx, offs_x, t, x, offs_y, s, y, B, lags, K, opt, c_out, b_out, count_out,
                                 (cudaStream_t)stream);
+}
+
+ncf_status ncf_corr_bootstrap(ncf_ctx *ctx, const double *t, const double *x, int64_t nx, const double *s,
+                              const double *y, int64_t ny, const double *lags, int64_t K, const ncf_options *opt,
+                              int64_t n_boot, uint64_t seed, double *c_out, double *b_out, int64_t *count_out,
+                              void *stream) {
+    using ncf::al;
+    if (!ctx) return NCF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return NCF_ECUDA;
+    const bool acf = (s == nullptr && y == nullptr);
+    if (!t || !x || !lags || !c_out || !opt || nx < 2 || K < 1 || n_boot < 1 || (!acf && (!s || !y || ny < 2)) ||
+        nx >= ((int64_t)1 << 32) || ny >= ((int64_t)1 << 32) || n_boot >= ((int64_t)1 << 32)) {
+        ctx->err = "ncf_corr_bootstrap: NULL pointer, fewer than 2 points, no lags, no replicate, or a size "
+                   "of 2^32 or more";
+        return NCF_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nyy = acf ? 0 : ny;
+    const size_t need = al((size_t)(nx * n_boot) * 8) * 2 + al((size_t)(nyy * n_boot) * 8) * 2 +
+                        al((size_t)(std::max(nx, nyy) * n_boot) * 4);
+    ncf::LaunchScope scope(ctx);
+    ncf_status rc = ncf::grow(ctx, &ctx->boot, &ctx->boot_cap, need, st);
+    if (rc) return rc;
+    char *p = ctx->boot;
+    auto take = [&](size_t bytes) { char *q = p; p += al(bytes); return q; };
+    double *bt = reinterpret_cast<double *>(take((size_t)(nx * n_boot) * 8));
+    double *bx = reinterpret_cast<double *>(take((size_t)(nx * n_boot) * 8));
+    double *bs = acf ? nullptr : reinterpret_cast<double *>(take((size_t)(nyy * n_boot) * 8));
+    double *by = acf ? nullptr : reinterpret_cast<double *>(take((size_t)(nyy * n_boot) * 8));
+    int32_t *cnt = reinterpret_cast<int32_t *>(take((size_t)(std::max(nx, nyy) * n_boot) * 4));
+    // the y side draws from its own stream, seed XOR all-ones
+    ncf::launch_bootstrap(t, x, nx, n_boot, seed, cnt, bt, bx, ctx->sm_count, st);
+    if (!acf) ncf::launch_bootstrap(s, y, ny, n_boot, ~seed, cnt, bs, by, ctx->sm_count, st);
+    if (cudaGetLastError() != cudaSuccess) return ncf::fail(ctx, NCF_ECUDA, "bootstrap kernels failed to launch");
+    std::vector<int64_t> ox(n_boot + 1), oy(acf ? 0 : n_boot + 1);
+    for (int64_t r = 0; r <= n_boot; ++r) {
+        ox[r] = r * nx;
+        if (!acf) oy[r] = r * ny;
+    }
+    return ncf::corr_batch_impl(ctx, ox.data(), bt, bx, acf ? nullptr : oy.data(), bs, by, n_boot, lags, K, opt,
+                                c_out, b_out, count_out, st);
 }
 
 ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,

@@ -131,6 +131,12 @@ void launch_gauss_window(const double *tx, const double *x, const int64_t *offs_
                          const SeriesStats *sty, const ScanTile *tiles, int64_t n_tiles,
                          const double *lags, int64_t K, int eps, double h, double Rh,
                          double *num, double *den, unsigned long long *cnt, cudaStream_t st);
+// Bootstrap replicates (k_boot.cu): n_boot resamples with replacement of the n
+// points (t, x), each in time order, written to bt, bx [n_boot][n]; cnt is
+// scratch of n * n_boot int32.  Draw j of replicate r is SplitMix64 output
+// 2^32 r + j of the stream `seed`, reduced to an index by multiply-high.
+void launch_bootstrap(const double *t, const double *x, int64_t n, int64_t n_boot, uint64_t seed, int32_t *cnt,
+                      double *bt, double *bx, int sm_count, cudaStream_t st);
 // Outer points per scan tile.
 int scan_tile_points();
 // Pearson scale per series from lag-0 ACF accumulators of x (and y for a CCF):
