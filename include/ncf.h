@@ -186,6 +186,35 @@ NCF_API ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, cons
 
 
 /*
+ * Classic-FFT estimator for data on a regular grid (the paper's dedicated FFT
+ * path for regularly sampled series, Table 1 and Sec. 5.2): every time is a
+ * whole multiple of one step, t_i = m_x[i] dt and s_j = m_y[j] dt, so a pair's
+ * separation is d dt for an integer d and Eq. kernel_estimator becomes
+ * N(tau) = sum_d R(d) b(d dt - tau), B(tau) = sum_d C(d) b(d dt - tau), with R
+ * the raw correlation of the standardised values and C the number of pairs at
+ * separation d, both from FFTs of the zero-padded lattice; the cost does not
+ * grow with K.  Gaussian (untruncated to within 1.3e-14: separations beyond
+ * 8 h are dropped) or rectangle (|fl(d dt - tau)| <= h in FP64; exact int64
+ * pair counts), NORM_NONE or NORM_LAG0, FP64 throughout; opt->path and
+ * opt->precision are ignored.  It equals the general estimator on the times
+ * m dt except where a rectangle bound falls exactly on a pair separation
+ * (there the general path tests the rounded times, this path the lattice).
+ *
+ * DEVICE pointers: m_x [nx] (int64 lattice indices, non-decreasing; equal
+ * indices are distinct samples at one time), x [nx]; for a CCF m_y, y [ny]
+ * on the same lattice (both NULL for an ACF); lags [K] (any order); outputs
+ * c_out, b_out (nullable), count_out (nullable; 0 for the Gaussian) [K].  The
+ * lattice span plus the lags' reach, (max m - min m) + (max|tau| + reach)/dt,
+ * must stay below 2^29 cells (NCF_EUNSUPPORTED otherwise).  Errors: NCF_EINVAL,
+ * NCF_ENOTSORTED, NCF_ENONFINITE, NCF_EDEGENERATE, NCF_ENOMEM, NCF_ECUDA.  One
+ * host synchronisation (statistics and lags are read back to size the grid).
+ */
+NCF_API ncf_status ncf_corr_regular(ncf_ctx *ctx, const int64_t *m_x, const double *x, int64_t nx,
+                                    const int64_t *m_y, const double *y, int64_t ny, double dt,
+                                    const double *lags, int64_t K, const ncf_options *opt,
+                                    double *c_out, double *b_out, int64_t *count_out, void *stream);
+
+/*
  * Bootstrap replicates of one ACF (s = y = NULL) or CCF, for per-lag sampling
  * uncertainties.  The paper recommends weighing an estimate against its
  * sampling variance by resampling or Monte-Carlo over realisations (Sec. 4,

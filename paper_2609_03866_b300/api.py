@@ -243,6 +243,39 @@ def corr(t, x, lags, kernel="gaussian", h=1.0, s=None, y=None, path="auto", prec
     return {"c": c, "b": b, "count": cnt}
 
 
+def corr_regular(m, x, dt, lags, kernel="gaussian", h=1.0, m_y=None, y=None, norm="none",
+                 ctx: Context | None = None, stream=None):
+    """Classic-FFT estimator for regularly sampled data (ncf_corr_regular): times
+    m * dt with integer lattice indices m (non-decreasing).  Returns dict(c, b,
+    count) of device tensors in the order of `lags`."""
+    import torch
+    L = lib()
+    if not getattr(L, "_reg_types", False):
+        vp = ctypes.c_void_p
+        L.ncf_corr_regular.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp, ctypes.c_int64, ctypes.c_double, vp,
+                                       ctypes.c_int64, ctypes.POINTER(ncf_options), vp, vp, vp, vp]
+        L.ncf_corr_regular.restype = ctypes.c_int
+        L._reg_types = True
+    ctx = ctx or default_context()
+    dev = torch.device("cuda", ctx.device)
+    mi = torch.as_tensor(np.ascontiguousarray(m, dtype=np.int64) if not hasattr(m, "device") else m).to(dev)
+    x, lags = _dev(x, dev), _dev(lags, dev)
+    ccf = y is not None
+    if ccf:
+        my = torch.as_tensor(np.ascontiguousarray(m_y, dtype=np.int64) if not hasattr(m_y, "device") else m_y).to(dev)
+        y = _dev(y, dev)
+    K = lags.numel()
+    out = {"c": torch.empty(K, dtype=torch.float64, device=dev), "b": torch.empty(K, dtype=torch.float64, device=dev),
+           "count": torch.empty(K, dtype=torch.int64, device=dev)}
+    o = make_options(kernel, h, "auto", "fp64", norm, 0.0, 0.0)
+    rc = L.ncf_corr_regular(ctx.handle, _ptr(mi), _ptr(x), mi.numel(), _ptr(my if ccf else None),
+                            _ptr(y if ccf else None), my.numel() if ccf else 0, float(dt), _ptr(lags), K,
+                            ctypes.byref(o), _ptr(out["c"]), _ptr(out["b"]), _ptr(out["count"]),
+                            _stream_handle(stream, dev))
+    ctx.check(rc)
+    return out
+
+
 def corr_bootstrap(t, x, lags, n_boot, seed=0, kernel="gaussian", h=1.0, s=None, y=None, path="auto",
                    precision="fp64", norm="none", trunc_R=0.0, tol=0.0, ctx: Context | None = None, stream=None):
     """n_boot bootstrap replicates of one ACF (s, y omitted) or CCF, resampled on the

@@ -961,6 +961,48 @@ ncf_status ncf_corr_bootstrap(ncf_ctx *ctx, const double *t, const double *x, in
                                 c_out, b_out, count_out, st);
 }
 
+ncf_status ncf_corr_regular(ncf_ctx *ctx, const int64_t *m_x, const double *x, int64_t nx, const int64_t *m_y,
+                            const double *y, int64_t ny, double dt, const double *lags, int64_t K,
+                            const ncf_options *opt, double *c_out, double *b_out, int64_t *count_out, void *stream) {
+    if (!ctx) return NCF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return NCF_ECUDA;
+    const bool ccf = m_y != nullptr || y != nullptr;
+    if (!m_x || !x || !lags || !c_out || !opt || nx < 2 || K < 1 || (ccf && (!m_y || !y || ny < 2)) ||
+        !(dt > 0.0) || !std::isfinite(dt) || !(opt->h > 0.0) || !std::isfinite(opt->h) ||
+        (opt->kernel != NCF_GAUSSIAN && opt->kernel != NCF_RECTANGLE) ||
+        (opt->norm != NCF_NORM_NONE && opt->norm != NCF_NORM_LAG0)) {
+        ctx->err = "ncf_corr_regular: NULL pointer, fewer than 2 points, no lags, dt or h not positive, or an "
+                   "unknown kernel or normalisation";
+        return NCF_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    ncf::LaunchScope scope(ctx);
+    ncf_status rc;
+    if ((rc = ncf::grow(ctx, &ctx->ws, &ctx->ws_cap, ncf::regular_stats_bytes(), st))) return rc;
+    if ((rc = ncf::grow_pinned(ctx, std::max<size_t>(4096, (size_t)K * 8), st))) return rc;
+    // the lags' reach sizes the lattice: read them back with the statistics
+    std::vector<double> hl(K);
+    if (cudaMemcpyAsync(hl.data(), lags, K * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return ncf::fail(ctx, NCF_ECUDA, "ncf_corr_regular: reading the lags failed");
+    std::string msg;
+    int64_t m0 = 0, m1 = 0;
+    rc = ncf::regular_stats(m_x, x, nx, ccf ? m_y : nullptr, y, ny, ctx->ws, ctx->pinned, &m0, &m1, st, &msg);
+    if (rc) return ncf::fail(ctx, rc, "%s", msg.c_str());
+    double max_tau = 0.0;
+    for (double v : hl) {
+        if (!std::isfinite(v)) return ncf::fail(ctx, NCF_EINVAL, "ncf_corr_regular: non-finite lag");
+        max_tau = std::max(max_tau, std::fabs(v));
+    }
+    const double reach = opt->kernel == NCF_RECTANGLE ? opt->h : 8.0 * opt->h;
+    const int lg = ncf::regular_lg(m1 - m0, max_tau, reach, dt);
+    if (lg == 0) return ncf::fail(ctx, NCF_EUNSUPPORTED, "ncf_corr_regular: lattice span plus lag reach over 2^29");
+    if ((rc = ncf::grow(ctx, &ctx->ws2, &ctx->ws2_cap, ncf::regular_workspace_bytes(lg, ccf, K), st))) return rc;
+    rc = ncf::regular_launch(m_x, x, nx, ccf ? m_y : nullptr, y, ny, ctx->ws, m0, lg, dt, lags, K, opt->kernel,
+                             opt->h, opt->norm == NCF_NORM_LAG0, ctx->ws2, c_out, b_out, count_out, st, &msg);
+    if (rc) return ncf::fail(ctx, rc, "%s", msg.c_str());
+    return NCF_OK;
+}
+
 ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
                                const int64_t *offs_y, const double *s, const double *y, int64_t B,
                                const double *lags, int64_t K, const ncf_options *opt, double *c_out,

@@ -137,6 +137,17 @@ void launch_gauss_window(const double *tx, const double *x, const int64_t *offs_
 // 2^32 r + j of the stream `seed`, reduced to an index by multiply-high.
 void launch_bootstrap(const double *t, const double *x, int64_t n, int64_t n_boot, uint64_t seed, int32_t *cnt,
                       double *bt, double *bx, int sm_count, cudaStream_t st);
+// Classic-FFT estimator on a regular lattice t = m dt (k_regular.cu).
+size_t regular_stats_bytes();
+int regular_lg(int64_t span, double max_tau, double reach, double dt);
+size_t regular_workspace_bytes(int lg, bool ccf, int64_t K);
+ncf_status regular_stats(const int64_t *mx, const double *x, int64_t nx, const int64_t *my, const double *y,
+                         int64_t ny, char *stat_buf, char *pinned, int64_t *m0, int64_t *m1, cudaStream_t st,
+                         std::string *msg);
+ncf_status regular_launch(const int64_t *mx, const double *x, int64_t nx, const int64_t *my, const double *y,
+                          int64_t ny, const char *stat_buf, int64_t m0, int lg, double dt, const double *lags,
+                          int64_t K, int kernel, double h, int lag0, char *ws, double *c_out, double *b_out,
+                          int64_t *count_out, cudaStream_t st, std::string *msg);
 // Outer points per scan tile.
 int scan_tile_points();
 // Pearson scale per series from lag-0 ACF accumulators of x (and y for a CCF):

@@ -75,7 +75,9 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
 // interpolant is rewritten in powers of u (coefficient d of tap k at
 // c[k * (D+1) + d]), so the kernel evaluates it with D fused multiply-adds and
 // no special-function instructions.  Max error: 8e-8 (W = 8, D = 8, FP32) and
-// 4e-15 (W = 16, D = 14, FP64) of the peak value 1.
+// 4e-15 (W = 16, D = 14, FP64) of the peak value 1.  The Chebyshev nodes are
+// symmetric and phi is even, so tap W-1-k's interpolant is tap k's at -u; the
+// kernel uses the first W/2 taps' coefficients only.
 std::vector<double> es_poly(int W, double beta, int D) {
     std::vector<double> out((size_t)W * (D + 1));
     const int n = D + 1;
@@ -257,7 +259,9 @@ template <> struct PointPhase<double> {
 //            apart -- sorted points would otherwise hit the same cell 32 times;
 //            the staging pad (one slot per 128 points) keeps these reads free of
 //            bank conflicts;
-//   phase 3  the chunk's tile of cells is added to the series' grid in HBM.
+//   phase 3  the chunk's tile of cells goes to the series' grid in HBM: plain
+//            stores for the interior, atomic adds for the W-cell edges shared
+//            with the neighbouring chunks.
 // A chunk spanning more cells than the tile (a sparse series) adds straight to HBM.
 template <typename R, int W>
 __global__ void __launch_bounds__(kSpreadThreads)
@@ -365,14 +369,24 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
             wim[W - 1] = 0;
             ++wbase;
         }
+        // taps k and W-1-k are one polynomial at u and -u (phi is even): its even
+        // and odd parts in v = u^2 give both with about half the multiply-adds
         const R u = (R)2 * f0 - (R)1;
+        const R v = u * u;
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-            R phi = poly.c[k * (D + 1) + D];
+        for (int k = 0; k < W / 2; ++k) {
+            const R *c = poly.c + k * (D + 1);
+            constexpr int De = D & ~1, Do = (D - 1) | 1;  // highest even / odd power
+            R e = c[De], o = c[Do];
 #pragma unroll
-            for (int d = D - 1; d >= 0; --d) phi = fma(phi, u, poly.c[k * (D + 1) + d]);
-            wre[k] = fma(phi, xs, wre[k]);
-            wim[k] += phi;
+            for (int d = De - 2; d >= 0; d -= 2) e = fma(e, v, c[d]);
+#pragma unroll
+            for (int d = Do - 2; d >= 1; d -= 2) o = fma(o, v, c[d]);
+            const R pk = fma(u, o, e), pm = fma(-u, o, e);
+            wre[k] = fma(pk, xs, wre[k]);
+            wim[k] += pk;
+            wre[W - 1 - k] = fma(pm, xs, wre[W - 1 - k]);
+            wim[W - 1 - k] += pm;
         }
     }
     if (started) {
@@ -381,9 +395,20 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
     }
     if (use_tile) {
         __syncthreads();
+        // Sorted points: a neighbouring chunk's cells overlap this tile only in its
+        // first and last W cells, so the interior is this chunk's alone and goes to
+        // the (zeroed) grid with plain stores; the edges are added atomically.
         for (int i = threadIdx.x; i < span; i += blockDim.x) {
             const V v = tile[i];
-            if (v.x != 0 || v.y != 0) atomic_add_v(&grid[(l_first + i) & mask], v.x, v.y);
+            if (v.x == 0 && v.y == 0) continue;
+            V *dst = &grid[(l_first + i) & mask];
+            if (i >= W && i < span - W) {
+                *dst = v;
+            } else if constexpr (sizeof(R) == 4) {
+                atomicAdd(reinterpret_cast<float2 *>(dst), make_float2(v.x, v.y));
+            } else {
+                atomic_add_v(dst, v.x, v.y);
+            }
         }
     }
 }
@@ -867,6 +892,36 @@ void spectral_guard(const SpectralArgs &a, const SpectralPrepared &p, char *ws, 
     NCF_LAUNCH("spectral_guard_kernel", st,
                spectral_guard_kernel<<<(unsigned)((p.B + 127) / 128), 128, 0, st>>>(
                    a.x.d_stats, p.acf ? nullptr : a.y.d_stats, d_tc, p.B, max_span, 0.9 * p.L, status));
+}
+
+// FP64 forward transforms (+i sign, unnormalised) of B contiguous grids of
+// 2^lg complex values, by the same Stockham passes as the spectral path; the
+// result lands in `grid` or `scratch` (returned).  tw must hold
+// exp(+2 pi i q / 2^lg), q < 2^lg (fft_twiddles_f64).
+void fft_twiddles_f64(double2 *tw, int lg, cudaStream_t st) {
+    const int n = 1 << lg;
+    NCF_LAUNCH("twiddle_kernel", st, twiddle_kernel<double2><<<(n + 255) / 256, 256, 0, st>>>(tw, n));
+}
+
+double2 *fft_forward_f64(double2 *grid, double2 *scratch, const double2 *tw, int lg, int64_t B, cudaStream_t st) {
+    const RadixPlan rp = radix_plan(lg);
+    const int n = 1 << lg;
+    double2 *in = grid, *out = scratch;
+    int Ns = 1;
+    for (int q = 0; q < rp.n_pass; ++q) {
+        const int rad = rp.radix[q];
+        const int64_t items = B * (int64_t)(n / rad);
+        const unsigned blocks = (unsigned)((items + 255) / 256);
+        if (rad == 8)
+            NCF_LAUNCH("fft_pass_kernel", st, fft_pass_kernel<double2, 8><<<blocks, 256, 0, st>>>(in, out, lg, Ns, tw, B));
+        else if (rad == 4)
+            NCF_LAUNCH("fft_pass_kernel", st, fft_pass_kernel<double2, 4><<<blocks, 256, 0, st>>>(in, out, lg, Ns, tw, B));
+        else
+            NCF_LAUNCH("fft_pass_kernel", st, fft_pass_kernel<double2, 2><<<blocks, 256, 0, st>>>(in, out, lg, Ns, tw, B));
+        Ns *= rad;
+        std::swap(in, out);
+    }
+    return in;
 }
 
 }  // namespace ncf

@@ -64,4 +64,8 @@ bool contract_tc_supported(int64_t M2);
 void launch_contract_tc(const float *Anum, const float *Aden, const float *E, int64_t B, int64_t M2,
                         int64_t Kp, double *acc_num, double *acc_den, int *status, cudaStream_t st);
 
+// FP64 forward FFT passes shared with the regular-grid path (k_spectral.cu).
+void fft_twiddles_f64(double2 *tw, int lg, cudaStream_t st);
+double2 *fft_forward_f64(double2 *grid, double2 *scratch, const double2 *tw, int lg, int64_t B, cudaStream_t st);
+
 }  // namespace ncf
