@@ -50,6 +50,8 @@ struct ncf_ctx {
     size_t boot_cap = 0;
     uint64_t launches = 0;
     cudaEvent_t staged = nullptr;  // recorded after staging copies issued past the read-back sync
+    cudaStream_t copy_st = nullptr;  // host-buffer calls: uploads and read-backs beside the compute stream
+    std::vector<cudaEvent_t> copy_ev;
     NcfProfiler prof;
     ncf_plan_info plan{0.0, 0, 0, 0, 0, 0};
     std::string err;
@@ -773,7 +775,8 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
 // Plans: the analysis and tables of one evaluation, kept for repeated launches
 // ----------------------------------------------------------------------------
 struct ncf_plan {
-    ncf_ctx *ctx = nullptr;
+    ncf_ctx *ctx = nullptr;  // used by execute/status (the context must outlive those calls)
+    int device = 0;          // destroy needs no context
     ncf::Eval ev;
     char *pre = nullptr, *main = nullptr;
     size_t pre_cap = 0, main_cap = 0;
@@ -841,8 +844,10 @@ void ncf_destroy(ncf_ctx *ctx) {
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->staged) cudaEventDestroy(ctx->staged);
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
-    delete ctx;
+    if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
+    for (cudaEvent_t e : ctx->copy_ev) cudaEventDestroy(e);
     if (ctx->boot) cudaFree(ctx->boot);
+    delete ctx;  // last: nothing above may touch ctx after this
 }
 
 ncf_status ncf_last_plan(const ncf_ctx *ctx, ncf_plan_info *out) {
@@ -1030,23 +1035,81 @@ ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, const double
     double *dl = ar.take<double>(K);
     double *dc = ar.take<double>(B * K), *db = ar.take<double>(B * K);
     int64_t *dn = ar.take<int64_t>(B * K);
-    auto h2d = [&](void *d, const void *h, size_t n) {
-        return cudaMemcpyAsync(d, h, n, cudaMemcpyHostToDevice, st) == cudaSuccess;
-    };
-    if (!h2d(dt, t, nx * 8) || !h2d(dx, x, nx * 8) || !h2d(dl, lags, K * 8) ||
-        (!acf && (!h2d(ds, s, ny * 8) || !h2d(dy, y, ny * 8)))) {
-        ctx->err = std::string("host-to-device copy failed: ") + cudaGetErrorString(cudaGetLastError());
-        return NCF_ECUDA;
+    // Large batches run as up to four chunks of series with about equal points:
+    // the upload of chunk i+1 (copy stream) overlaps the evaluation of chunk i
+    // (the caller's stream), and each chunk's results come back while the next
+    // one runs.  Pinned host buffers are needed for the copies to overlap.
+    const int64_t pts = nx + ny;
+    const int C = (int)std::min<int64_t>(B, pts * 16 > (int64_t)(256 << 20) ? 4 : 1);
+    std::vector<int64_t> cut(C + 1, B);
+    cut[0] = 0;
+    for (int c = 1; c < C; ++c) {
+        const int64_t target = pts * c / C;
+        int64_t b = cut[c - 1];
+        while (b < B && offs_x[b] + (acf ? 0 : offs_y[b]) < target) ++b;
+        cut[c] = std::max(b, cut[c - 1]);
     }
-    rc = ncf::corr_batch_impl(ctx, offs_x, dt, dx, offs_y, ds, dy, B, dl, K, opt, dc, b_out ? db : nullptr,
-                              count_out ? dn : nullptr, st);
-    if (rc) return rc;
-    auto d2h = [&](void *h, const void *d, size_t n) {
-        return cudaMemcpyAsync(h, d, n, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    if (!ctx->copy_st && cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking) != cudaSuccess)
+        return ncf::fail(ctx, NCF_ECUDA, "ncf_corr_batch_host: copy stream creation failed");
+    while ((int)ctx->copy_ev.size() < 2 * C + 1) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return ncf::fail(ctx, NCF_ECUDA, "ncf_corr_batch_host: event creation failed");
+        ctx->copy_ev.push_back(e);
+    }
+    cudaStream_t cs = ctx->copy_st;
+    cudaEvent_t *ev_in = ctx->copy_ev.data(), *ev_out = ev_in + C, ev_start = ev_in[2 * C];
+    // the copy stream starts after the work already queued on the caller's stream
+    bool ok = cudaEventRecord(ev_start, st) == cudaSuccess && cudaStreamWaitEvent(cs, ev_start, 0) == cudaSuccess;
+    auto upload = [&](int c) {
+        const int64_t b0 = cut[c], b1 = cut[c + 1];
+        const int64_t x0 = offs_x[b0], x1 = offs_x[b1];
+        bool k = cudaMemcpyAsync(dt + x0, t + x0, (x1 - x0) * 8, cudaMemcpyHostToDevice, cs) == cudaSuccess &&
+                 cudaMemcpyAsync(dx + x0, x + x0, (x1 - x0) * 8, cudaMemcpyHostToDevice, cs) == cudaSuccess;
+        if (!acf) {
+            const int64_t y0 = offs_y[b0], y1 = offs_y[b1];
+            k = k && cudaMemcpyAsync(ds + y0, s + y0, (y1 - y0) * 8, cudaMemcpyHostToDevice, cs) == cudaSuccess &&
+                cudaMemcpyAsync(dy + y0, y + y0, (y1 - y0) * 8, cudaMemcpyHostToDevice, cs) == cudaSuccess;
+        }
+        return k && cudaEventRecord(ev_in[c], cs) == cudaSuccess;
     };
-    if (!d2h(c_out, dc, B * K * 8) || (b_out && !d2h(b_out, db, B * K * 8)) ||
-        (count_out && !d2h(count_out, dn, B * K * 8)) || cudaStreamSynchronize(st) != cudaSuccess) {
-        ctx->err = std::string("device-to-host copy failed: ") + cudaGetErrorString(cudaGetLastError());
+    ok = ok && cudaMemcpyAsync(dl, lags, K * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    for (int c = 0; c < std::min(C, 2); ++c) ok = ok && upload(c);
+    if (!ok) return ncf::fail(ctx, NCF_ECUDA, "host-to-device copy failed: %s", cudaGetErrorString(cudaGetLastError()));
+    std::vector<int64_t> ox, oy;
+    for (int c = 0; c < C; ++c) {
+        const int64_t b0 = cut[c], b1 = cut[c + 1], nb = b1 - b0;
+        if (nb > 0) {
+            const int64_t x0 = offs_x[b0], y0 = acf ? 0 : offs_y[b0];
+            ox.assign(offs_x + b0, offs_x + b1 + 1);
+            for (auto &v : ox) v -= x0;
+            if (!acf) {
+                oy.assign(offs_y + b0, offs_y + b1 + 1);
+                for (auto &v : oy) v -= y0;
+            }
+            if (cudaStreamWaitEvent(st, ev_in[c], 0) != cudaSuccess)
+                return ncf::fail(ctx, NCF_ECUDA, "ncf_corr_batch_host: stream wait failed");
+            rc = ncf::corr_batch_impl(ctx, ox.data(), dt + x0, dx + x0, acf ? nullptr : oy.data(),
+                                      acf ? nullptr : ds + y0, acf ? nullptr : dy + y0, nb, dl, K, opt, dc + b0 * K,
+                                      b_out ? db + b0 * K : nullptr, count_out ? dn + b0 * K : nullptr, st);
+            if (rc) {
+                cudaStreamSynchronize(cs);
+                return rc;
+            }
+        }
+        ok = cudaEventRecord(ev_out[c], st) == cudaSuccess;
+        if (c + 2 < C) ok = ok && upload(c + 2);
+        ok = ok && cudaStreamWaitEvent(cs, ev_out[c], 0) == cudaSuccess;
+        auto d2h = [&](void *h, const void *d) {
+            return cudaMemcpyAsync(h, d, nb * K * 8, cudaMemcpyDeviceToHost, cs) == cudaSuccess;
+        };
+        if (nb > 0)
+            ok = ok && d2h(c_out + b0 * K, dc + b0 * K) && (!b_out || d2h(b_out + b0 * K, db + b0 * K)) &&
+                 (!count_out || d2h(count_out + b0 * K, dn + b0 * K));
+        if (!ok) break;
+    }
+    if (!ok || cudaStreamSynchronize(cs) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+        ctx->err = std::string("copy failed: ") + cudaGetErrorString(cudaGetLastError());
         return NCF_ECUDA;
     }
     return NCF_OK;
@@ -1066,6 +1129,7 @@ ncf_status ncf_plan_create(ncf_ctx *ctx, const int64_t *offs_x, const double *t,
     if (ctx->staged) NCF_CUDA(cudaEventSynchronize(ctx->staged));
     ncf_plan *p = new ncf_plan();
     p->ctx = ctx;
+    p->device = ctx->device;
     Eval &ev = p->ev;
     auto bail = [&](ncf_status rc) {
         if (p->pre) cudaFree(p->pre);
@@ -1134,7 +1198,7 @@ size_t ncf_plan_device_bytes(const ncf_plan *plan) { return plan ? plan->pre_cap
 
 void ncf_plan_destroy(ncf_plan *plan) {
     if (!plan) return;
-    cudaSetDevice(plan->ctx->device);
+    cudaSetDevice(plan->device);
     cudaDeviceSynchronize();
     if (plan->pre) cudaFree(plan->pre);
     if (plan->main) cudaFree(plan->main);
