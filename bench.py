@@ -429,11 +429,24 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1)
-        c64 = out_g["c"]
+        c64 = out_g["c"].clone()
+
+        def gauss_ms(prec):
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for _ in range(3):
+                api.corr_batch(offs, t, x, lags, kernel="gaussian", h=H, path="spectral", precision=prec,
+                               ctx=ctx, stream=stream, out=out_g)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            return g0.elapsed_time(g1) / 3
+
+        g32, g64 = gauss_ms("fp32"), gauss_ms("fp64")
         fp64 = {"value": 2.0 * B * K * world / (ms64 / 1e3), "unit": "series*lags/s", "ms_per_step": ms64,
                 "path": "FP64 spectral (Gaussian) + exact scan (rectangle)",
                 "max_abs_diff_fp32_vs_fp64": float((c32 - c64).abs().max().item()),
-                "speedup_fp32_form": (ms64 / (total_ms / args.steps))}
+                "speedup_fp32_form": (ms64 / (total_ms / args.steps)),
+                "gaussian_only_ms": {"fp32_form": g32, "fp64": g64, "speedup": g64 / g32}}
 
     # ---- end to end through the host-buffer C call ----
     e2e = None
