@@ -215,6 +215,17 @@ NCF_API ncf_status ncf_corr_regular(ncf_ctx *ctx, const int64_t *m_x, const doub
                                     double *c_out, double *b_out, int64_t *count_out, void *stream);
 
 /*
+ * Self-test of failure detection (no counterpart in the paper): runs a kernel
+ * whose mbarrier wait -- the bounded wait the tensor-core contraction uses --
+ * is never satisfied, so it must give up after a short iteration limit, set
+ * the timeout bit of a device status word and return normally.  *flags
+ * receives that word (bit 1, the timeout bit of ncf_plan_status, expected).
+ * Returns NCF_OK when the timeout was reported; the context stays usable
+ * either way.
+ */
+NCF_API ncf_status ncf_selftest_bounded_wait(ncf_ctx *ctx, void *stream, int32_t *flags);
+
+/*
  * Bootstrap replicates of one ACF (s = y = NULL) or CCF, for per-lag sampling
  * uncertainties.  The paper recommends weighing an estimate against its
  * sampling variance by resampling or Monte-Carlo over realisations (Sec. 4,

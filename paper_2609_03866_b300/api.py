@@ -243,6 +243,21 @@ def corr(t, x, lags, kernel="gaussian", h=1.0, s=None, y=None, path="auto", prec
     return {"c": c, "b": b, "count": cnt}
 
 
+def selftest_bounded_wait(ctx: Context | None = None, stream=None) -> int:
+    """Runs the bounded-wait self-test (ncf_selftest_bounded_wait) and returns the
+    device status word it produced (bit 1: the wait gave up as designed)."""
+    import torch
+    L = lib()
+    L.ncf_selftest_bounded_wait.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
+    L.ncf_selftest_bounded_wait.restype = ctypes.c_int
+    ctx = ctx or default_context()
+    flags = ctypes.c_int32()
+    rc = L.ncf_selftest_bounded_wait(ctx.handle, _stream_handle(stream, torch.device("cuda", ctx.device)),
+                                     ctypes.byref(flags))
+    ctx.check(rc)
+    return flags.value
+
+
 def corr_regular(m, x, dt, lags, kernel="gaussian", h=1.0, m_y=None, y=None, norm="none",
                  ctx: Context | None = None, stream=None):
     """Classic-FFT estimator for regularly sampled data (ncf_corr_regular): times

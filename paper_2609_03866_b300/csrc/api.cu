@@ -925,6 +925,24 @@ ncf_status ncf_corr_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *t, 
                                 (cudaStream_t)stream);
 }
 
+ncf_status ncf_selftest_bounded_wait(ncf_ctx *ctx, void *stream, int32_t *flags) {
+    if (!ctx || !flags) return NCF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return NCF_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    ncf::LaunchScope scope(ctx);
+    ncf_status rc = ncf::grow(ctx, &ctx->ws, &ctx->ws_cap, 256, st);
+    if (rc) return rc;
+    int *dstat = reinterpret_cast<int *>(ctx->ws);
+    if (cudaMemsetAsync(dstat, 0, sizeof(int), st) != cudaSuccess) return NCF_ECUDA;
+    ncf::launch_bounded_wait_selftest(dstat, st);
+    int h = 0;
+    if (cudaMemcpyAsync(&h, dstat, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return ncf::fail(ctx, NCF_ECUDA, "bounded-wait self-test: %s", cudaGetErrorString(cudaGetLastError()));
+    *flags = h;
+    return (h & ncf::STATUS_TIMEOUT) ? NCF_OK : ncf::fail(ctx, NCF_ECUDA, "bounded wait did not report a timeout");
+}
+
 ncf_status ncf_corr_bootstrap(ncf_ctx *ctx, const double *t, const double *x, int64_t nx, const double *s,
                               const double *y, int64_t ny, const double *lags, int64_t K, const ncf_options *opt,
                               int64_t n_boot, uint64_t seed, double *c_out, double *b_out, int64_t *count_out,

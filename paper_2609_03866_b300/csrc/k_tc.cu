@@ -67,8 +67,8 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
         "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (long long it = 0; it < kSpinLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit = kSpinLimit) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -236,7 +236,21 @@ contract_tc_kernel(const float *__restrict__ Anum, const float *__restrict__ Ade
     }
 }
 
+// Self-test of the bounded wait: an mbarrier phase that nothing completes must
+// end in STATUS_TIMEOUT after `limit` polls, with the kernel returning normally.
+__global__ void bounded_wait_selftest_kernel(int *status, long long limit) {
+    __shared__ __align__(8) unsigned long long mb;
+    const uint32_t a = smem_u32(&mb);
+    if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(1));
+    __syncthreads();
+    if (!mbar_wait(a, 0u, limit) && threadIdx.x == 0) atomicOr(status, STATUS_TIMEOUT);
+}
+
 }  // namespace
+
+void launch_bounded_wait_selftest(int *status, cudaStream_t st) {
+    NCF_LAUNCH("bounded_wait_selftest_kernel", st, bounded_wait_selftest_kernel<<<1, 32, 0, st>>>(status, 4096));
+}
 
 size_t contract_tc_smem_bytes() { return 6 * (size_t)kTileBytes + 1024; }
 

@@ -68,4 +68,7 @@ void launch_contract_tc(const float *Anum, const float *Aden, const float *E, in
 void fft_twiddles_f64(double2 *tw, int lg, cudaStream_t st);
 double2 *fft_forward_f64(double2 *grid, double2 *scratch, const double2 *tw, int lg, int64_t B, cudaStream_t st);
 
+// Self-test: a bounded mbarrier wait that nothing completes sets STATUS_TIMEOUT (k_tc.cu).
+void launch_bounded_wait_selftest(int *status, cudaStream_t st);
+
 }  // namespace ncf

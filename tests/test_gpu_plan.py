@@ -92,3 +92,13 @@ def test_plan_device_guards():
     r = to_np(plan.execute(t, x))
     assert plan.status() == 0 and np.all(np.isfinite(r["c"]))
     assert plan.device_bytes > 0
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """A device wait that nothing satisfies ends in the timeout status bit after
+    its iteration limit (no hang, no fault); the same context then computes."""
+    from paper_2609_03866_b300 import api as _api
+    assert _api.selftest_bounded_wait() & 1
+    w = synth.ar1_acf(n=800, K=10)
+    r = _api.corr(w.t, w.x, w.lags, kernel="rectangle", h=1.0)
+    assert bool(torch.isfinite(r["c"]).all())
