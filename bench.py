@@ -230,7 +230,7 @@ def regular_run(api, device, n=256_000, K=366, h=1.0):
     return out
 
 
-def serve_pool(n_pool=32, n_lo=1_000, n_hi=2_000_000, seed=11):
+def serve_pool(n_pool=32, n_lo=1_000, n_hi=5_000_000, seed=11):
     """Request templates of the serving mix: half ACF light curves, half seasonal OU
     CCFs (n_B = 0.8 n_A); n log-uniform in [n_lo, n_hi]; K in {64, 256, 1024};
     Gaussian (FP32 form) or rectangle (exact scan), h = 0.5."""
@@ -331,7 +331,7 @@ def serve_run(api, device, n_req=160, slots=4, seed=11):
     return {"requests": n_req, "slots": slots, "saturation_requests_per_s": rate,
             "value": done_k / dt_closed, "unit": "series*lags/s", "loads": loads,
             "p50_ms": loads[1]["p50_ms"], "p99_ms": loads[1]["p99_ms"],
-            "mix": "50% ACF light curves / 50% OU CCF (n_B = 0.8 n_A), n log-uniform [1e3, 2e6], "
+            "mix": "50% ACF light curves / 50% OU CCF (n_B = 0.8 n_A), n log-uniform [1e3, 5e6], "
                    "K in {64, 256, 1024}, Gaussian FP32 form or rectangle exact scan, h = 0.5; "
                    "requests drawn from 32 seeded templates whose series are resident on the device"}
 

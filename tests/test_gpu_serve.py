@@ -118,3 +118,28 @@ def test_resident_series_give_the_same_results_and_hold_budget():
         tiny.put(w.t, w.x)
     assert e.value.name == "NCF_EBUSY"
     tiny.close()
+
+
+def test_serving_at_the_largest_request_sizes():
+    """Requests at the top of the serving mix (5e6-point ACF, 5e6 x 4e6 CCF,
+    K = 1024) through resident series: rectangle counts bit-exact and c within
+    1e-10 of the oracle on sampled lags; the Gaussian FP32 form within 1e-5 of
+    the FP64 spectral path (itself pinned to the oracle at smaller sizes) on
+    every lag."""
+    import oracle
+    srv = api.Server(slots=2, mem_budget_bytes=48 << 30)
+    w = synth.light_curves(B=1, K=1024, sizes=[5_000_000], seed=synth.BASE_SEED + 500)
+    c = synth.ou_ccf(nA=5_000_000, nB=4_000_000, K=1024, series=500)
+    hx, ha, hb = srv.put(w.t, w.x), srv.put(c.t, c.x), srv.put(c.s, c.y)
+    rng = np.random.default_rng(8)
+    for xs, ys, lags, t, x, s, y in [(hx, 0, w.lags, w.t, w.x, None, None), (ha, hb, c.lags, c.t, c.x, c.s, c.y)]:
+        r = srv.wait(srv.submit(None, None, lags, kernel="rectangle", h=0.5, x_series=xs, y_series=ys))
+        ks = np.sort(rng.choice(lags.size, 5, replace=False))
+        ref = oracle.corr(t, x, lags[ks], "rectangle", 0.5, s=s, y=y, method="windowed")
+        assert np.array_equal(r["count"][ks], ref["count"])
+        assert max_abs(r["c"][ks], ref["c"]) < 1e-10
+        g32 = srv.wait(srv.submit(None, None, lags, kernel="gaussian", h=0.5, path="spectral", precision="fp32",
+                                  x_series=xs, y_series=ys))
+        g64 = to_np(api.corr(t, x, lags, kernel="gaussian", h=0.5, s=s, y=y, path="spectral", precision="fp64"))
+        assert max_abs(g32["c"], g64["c"]) < 1e-5
+    srv.close()
