@@ -230,6 +230,33 @@ def regular_run(api, device, n=256_000, K=366, h=1.0):
     return out
 
 
+def hanning_run(api, device, h=0.5):
+    """Hanning kernel (FP64 windowed path) on the seasonal OU CCF at full size
+    (1e5 x 8e4 points, 200 lags), beside the exact rectangle scan on the same data."""
+    import torch
+    from paper_2609_03866_b300 import synth
+    w = synth.ou_ccf()
+    dev = torch.device("cuda", device)
+    t, x, s, y, lags = (torch.from_numpy(a).to(dev) for a in (w.t, w.x, w.s, w.y, w.lags))
+    ctx = api.Context(device)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for kernel in ("hanning", "rectangle"):
+        for _ in range(3):
+            api.corr(t, x, lags, kernel=kernel, h=h, s=s, y=y, ctx=ctx, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            api.corr(t, x, lags, kernel=kernel, h=h, s=s, y=y, ctx=ctx, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[kernel + "_ms"] = e0.elapsed_time(e1) / 5
+    ctx.close()
+    out.update({"workload": "seasonal OU CCF, 1e5 x 8e4 points, 200 lags on [-100, 100] d, h = 0.5 d"})
+    return out
+
+
 def serve_pool(n_pool=32, n_lo=1_000, n_hi=5_000_000, seed=11):
     """Request templates of the serving mix: half ACF light curves, half seasonal OU
     CCFs (n_B = 0.8 n_A); n log-uniform in [n_lo, n_hi]; K in {64, 256, 1024};
@@ -344,7 +371,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the serving, bootstrap, regular-grid and Hanning legs")
     ap.add_argument("--batch", type=int, default=B_SERIES, help="series per rank (profiling runs)")
     args = ap.parse_args()
 
@@ -482,6 +510,7 @@ def main():
         serve = serve_run(api, local)
     boot = None if args.no_serve else bootstrap_run(api, local)
     regular = None if args.no_serve else regular_run(api, local)
+    hanning = None if args.no_serve else hanning_run(api, local)
 
     if rank != 0:
         if world > 1:
@@ -557,9 +586,21 @@ def main():
         "roofline": roof,
         "e2e": e2e,
         "fp64_plain": fp64,
+        "paper_timings": {
+            "hardware": "MacBook Pro 2020, 2 GHz quad-core Intel Core i5, 16 GB LPDDR4X (the paper's benchmark machine)",
+            "note": "context only: other hardware, single series, K = 366; not the target",
+            "nufft_gaussian_s_per_point_per_lag": 1.13e-5 / 366, "nufft_rectangle_s_per_point_per_lag": 3.77e-6 / 366,
+            "realspace_gaussian_s_per_point_per_lag": 1.80e-5 / 366,
+            "realspace_rectangle_s_per_point_per_lag": 1.34e-6 / 366,
+            "regular_fft_n256000": {"gaussian_s": 0.07, "rectangle_s": 0.04},
+            "this_run_s_per_point_per_lag": {
+                "gaussian_fp32_form": (fp64["gaussian_only_ms"]["fp32_form"] / 1e3 / (n_pts * K)) if fp64 else None,
+                "rectangle_exact_scan": share.get("rect_scan_pt_kernel", share.get("rect_scan_kernel", 0.0))
+                * (total_ms / args.steps) / 1e3 / (n_pts * K)}},
         "serving": serve,
         "bootstrap": boot,
         "regular_fft": regular,
+        "hanning": hanning,
         "accuracy": acc,
         "cpu_baseline": cpu,
     }

@@ -80,7 +80,10 @@ typedef enum {
     NCF_EUNSUPPORTED = 9   /* option combination not provided (see ncf_last_error) */
 } ncf_status;
 
-typedef enum { NCF_GAUSSIAN = 0, NCF_RECTANGLE = 1 } ncf_kernel;
+/* NCF_HANNING: the Hann window b(d) = cos^2(pi d / (2 h)) / h for |d| <= h (unit
+ * mass), the kernel Sec. 2.3 names without defining; the rectangle's closed
+ * window with Hann weights, FP64 windowed path (and the regular-grid path) only. */
+typedef enum { NCF_GAUSSIAN = 0, NCF_RECTANGLE = 1, NCF_HANNING = 2 } ncf_kernel;
 typedef enum { NCF_PATH_AUTO = 0, NCF_PATH_SPECTRAL = 1, NCF_PATH_WINDOWED = 2 } ncf_path;
 typedef enum { NCF_FP64 = 0, NCF_FP32 = 1 } ncf_precision;
 typedef enum {

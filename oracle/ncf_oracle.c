@@ -64,13 +64,23 @@ void oracle_stats(const double *x, int64_t n, double *mean, double *std_) {
     *std_ = sqrt(nsum_get(&v) / (double)n);
 }
 
+#define ORACLE_PI 3.14159265358979323846264338327950288
+
 static inline double gauss_b(double d, double h) {
     return exp(-(d * d) / (2.0 * h * h)) / (ORACLE_SQRT_2PI * h);
 }
 
+/* Hann window of half-width h and unit mass, b(d) = cos^2(pi d / (2 h)) / h on
+ * |d| <= h (the Hanning kernel named in Sec. 2.3 and left undefined there). */
+static inline double hann_b(double d, double h) {
+    const double c = cos(ORACLE_PI * d / (2.0 * h));
+    return c * c / h;
+}
+
 /*
  * O1: direct double sum of Eq. kernel_estimator for each lag.
- *   kernel: 0 = Gaussian, 1 = rectangle.  eps: +1 ACF, -1 CCF.
+ *   kernel: 0 = Gaussian, 1 = rectangle, 2 = Hanning (the rectangle's closed
+ *   window with Hann weights).  eps: +1 ACF, -1 CCF.
  * Outputs per lag k: num[k] = sum x_i y_j b, den[k] = sum b, cnt[k] = number
  * of pairs with nonzero weight (rectangle: the exact integer pair count).
  */
@@ -91,6 +101,16 @@ void oracle_corr_direct(const double *t, const double *x, int64_t nx,
                 for (int64_t i = 0; i < nx; ++i) {
                     if (lo <= t[i] && t[i] <= hi) {
                         nsum_add(&N, x[i] * y[j]);
+                        C += 1;
+                    }
+                }
+            } else if (kernel == 2) {
+                const double lo = c - h, hi = c + h;
+                for (int64_t i = 0; i < nx; ++i) {
+                    if (lo <= t[i] && t[i] <= hi) {
+                        const double w = hann_b(t[i] - c, h);
+                        nsum_add(&N, w * x[i] * y[j]);
+                        nsum_add(&B, w);
                         C += 1;
                     }
                 }
@@ -141,6 +161,16 @@ void oracle_corr_windowed(const double *t, const double *x, int64_t nx,
                 while (hi < nx && t[hi] <= c + h) ++hi;
                 C += hi - lo;
                 N += y[j] * (cum[hi] - cum[lo]);
+            } else if (kernel == 2) {
+                while (lo < nx && t[lo] < c - h) ++lo;
+                if (hi < lo) hi = lo;
+                while (hi < nx && t[hi] <= c + h) ++hi;
+                for (int64_t i = lo; i < hi; ++i) {
+                    const double w = hann_b(t[i] - c, h);
+                    B += w;
+                    N += w * x[i] * y[j];
+                }
+                C += hi - lo;
             } else {
                 while (lo < nx && t[lo] < c - Rh) ++lo;
                 while (hi < nx && t[hi] < c + Rh) ++hi;

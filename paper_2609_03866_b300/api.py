@@ -25,7 +25,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libncf.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "ncf.h")
 
-KERNELS = {"gaussian": 0, "rectangle": 1}
+KERNELS = {"gaussian": 0, "rectangle": 1, "hanning": 2}
 PATHS = {"auto": 0, "spectral": 1, "windowed": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 NORMS = {"none": 0, "lag0": 1}

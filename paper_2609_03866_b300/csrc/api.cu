@@ -264,7 +264,7 @@ ncf_status check_args(ncf_ctx *ctx, const int64_t *offs_x, const double *t, cons
     if (!t || !x || !lags) return fail(ctx, NCF_EINVAL, "NULL t, x or lags");
     if (!(opt->h > 0.0) || !std::isfinite(opt->h))
         return fail(ctx, NCF_EINVAL, "h = %g (need finite h > 0)", opt->h);
-    if (opt->kernel != NCF_GAUSSIAN && opt->kernel != NCF_RECTANGLE)
+    if (opt->kernel != NCF_GAUSSIAN && opt->kernel != NCF_RECTANGLE && opt->kernel != NCF_HANNING)
         return fail(ctx, NCF_EINVAL, "unknown kernel %d", opt->kernel);
     if (opt->path < NCF_PATH_AUTO || opt->path > NCF_PATH_WINDOWED)
         return fail(ctx, NCF_EINVAL, "unknown path %d", opt->path);
@@ -286,8 +286,11 @@ ncf_status check_args(ncf_ctx *ctx, const int64_t *offs_x, const double *t, cons
                     "decays as 1/f, so a truncated spectrum cannot meet the tolerance)");
     if (opt->kernel == NCF_GAUSSIAN && path == NCF_PATH_WINDOWED && opt->precision == NCF_FP32)
         return fail(ctx, NCF_EUNSUPPORTED, "the windowed Gaussian path is FP64 only");
+    if (opt->kernel == NCF_HANNING && (path == NCF_PATH_SPECTRAL || opt->precision == NCF_FP32))
+        return fail(ctx, NCF_EUNSUPPORTED,
+                    "Hanning kernel: FP64 windowed path only (its transform decays as 1/f^3)");
     if (path == NCF_PATH_AUTO) {
-        if (opt->kernel == NCF_RECTANGLE) path = NCF_PATH_WINDOWED;
+        if (opt->kernel == NCF_RECTANGLE || opt->kernel == NCF_HANNING) path = NCF_PATH_WINDOWED;
         else if (opt->precision == NCF_FP32) path = NCF_PATH_SPECTRAL;
         // FP64 Gaussian: decided after the statistics pass (choose_path)
     }
@@ -600,24 +603,25 @@ ncf_status launch(ncf_ctx *ctx, Eval &ev, bool stats_fresh, bool guard, double *
         launch_finish_rect(ev.cnt, ev.num, B, K, inv_v2, ev.lag0 ? ev.scale : nullptr, ev.status, c_out, b_out,
                            count_out, st);
     } else if (ev.path == NCF_PATH_WINDOWED) {
-        const double R = ev.opt.trunc_R > 0.0 ? ev.opt.trunc_R : 8.0;
+        const int hann = ev.opt.kernel == NCF_HANNING;
+        const double R = hann ? 1.0 : (ev.opt.trunc_R > 0.0 ? ev.opt.trunc_R : 8.0);
         const double Rh = R * ev.opt.h;
         NCF_CUDA(cudaMemsetAsync(ev.gnum, 0, B * K * 8, st));
         NCF_CUDA(cudaMemsetAsync(ev.gden, 0, B * K * 8, st));
         NCF_CUDA(cudaMemsetAsync(ev.gcnt, 0, B * K * 8, st));
         const int eps = ev.acf ? +1 : -1;
         launch_gauss_window(X.t, X.v, X.d_offs, X.d_stats, O.t, O.v, O.d_stats, ev.g_tiles, ev.g_ntiles, ev.d_lags,
-                            K, eps, ev.opt.h, Rh, ev.gnum, ev.gden, ev.gcnt, st);
+                            K, eps, ev.opt.h, Rh, hann, ev.gnum, ev.gden, ev.gcnt, st);
         if (ev.lag0) {
             NCF_CUDA(cudaMemsetAsync(ev.zero_lag, 0, 8, st));
             NCF_CUDA(cudaMemsetAsync(ev.gn0, 0, 2 * B * 8, st));
             NCF_CUDA(cudaMemsetAsync(ev.gd0, 0, 2 * B * 8, st));
             NCF_CUDA(cudaMemsetAsync(ev.gc0, 0, 2 * B * 8, st));
             launch_gauss_window(X.t, X.v, X.d_offs, X.d_stats, X.t, X.v, X.d_stats, ev.g_xtiles, ev.g_nxtiles,
-                                ev.zero_lag, 1, +1, ev.opt.h, Rh, ev.gn0, ev.gd0, ev.gc0, st);
+                                ev.zero_lag, 1, +1, ev.opt.h, Rh, hann, ev.gn0, ev.gd0, ev.gc0, st);
             if (!ev.acf)
                 launch_gauss_window(ev.Y.t, ev.Y.v, ev.Y.d_offs, ev.Y.d_stats, ev.Y.t, ev.Y.v, ev.Y.d_stats,
-                                    ev.g_tiles, ev.g_ntiles, ev.zero_lag, 1, +1, ev.opt.h, Rh, ev.gn0 + B,
+                                    ev.g_tiles, ev.g_ntiles, ev.zero_lag, 1, +1, ev.opt.h, Rh, hann, ev.gn0 + B,
                                     ev.gd0 + B, ev.gc0 + B, st);
             launch_lag0_scale_gauss(ev.gn0, ev.gd0, ev.acf ? nullptr : ev.gn0 + B, ev.acf ? nullptr : ev.gd0 + B, B,
                                     ev.scale, st);
@@ -992,7 +996,7 @@ ncf_status ncf_corr_regular(ncf_ctx *ctx, const int64_t *m_x, const double *x, i
     const bool ccf = m_y != nullptr || y != nullptr;
     if (!m_x || !x || !lags || !c_out || !opt || nx < 2 || K < 1 || (ccf && (!m_y || !y || ny < 2)) ||
         !(dt > 0.0) || !std::isfinite(dt) || !(opt->h > 0.0) || !std::isfinite(opt->h) ||
-        (opt->kernel != NCF_GAUSSIAN && opt->kernel != NCF_RECTANGLE) ||
+        (opt->kernel != NCF_GAUSSIAN && opt->kernel != NCF_RECTANGLE && opt->kernel != NCF_HANNING) ||
         (opt->norm != NCF_NORM_NONE && opt->norm != NCF_NORM_LAG0)) {
         ctx->err = "ncf_corr_regular: NULL pointer, fewer than 2 points, no lags, dt or h not positive, or an "
                    "unknown kernel or normalisation";
@@ -1016,7 +1020,7 @@ ncf_status ncf_corr_regular(ncf_ctx *ctx, const int64_t *m_x, const double *x, i
         if (!std::isfinite(v)) return ncf::fail(ctx, NCF_EINVAL, "ncf_corr_regular: non-finite lag");
         max_tau = std::max(max_tau, std::fabs(v));
     }
-    const double reach = opt->kernel == NCF_RECTANGLE ? opt->h : 8.0 * opt->h;
+    const double reach = opt->kernel == NCF_GAUSSIAN ? 8.0 * opt->h : opt->h;
     const int lg = ncf::regular_lg(m1 - m0, max_tau, reach, dt);
     if (lg == 0) return ncf::fail(ctx, NCF_EUNSUPPORTED, "ncf_corr_regular: lattice span plus lag reach over 2^29");
     if ((rc = ncf::grow(ctx, &ctx->ws2, &ctx->ws2_cap, ncf::regular_workspace_bytes(lg, ccf, K), st))) return rc;

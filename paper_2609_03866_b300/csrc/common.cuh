@@ -125,11 +125,12 @@ size_t rect_staging_bytes(int64_t n_tiles, int64_t K);
 ncf_status rect_prepare(const RectArgs &a, char *ws, size_t ws_cap, char *pinned, size_t pinned_cap,
                         cudaStream_t st, RectPrepared *out, std::string *msg);
 ncf_status rect_launch(const RectArgs &a, const RectPrepared &r, cudaStream_t st, std::string *msg);
-// Gaussian windowed FP64 scan (Algorithms 5 and 7 with window R h).
+// Windowed FP64 scan (Algorithms 5 and 7): Gaussian over [c - Rh, c + Rh), or
+// (hann) the Hann window cos^2(pi d / 2h) / h over the closed [c - h, c + h].
 void launch_gauss_window(const double *tx, const double *x, const int64_t *offs_x,
                          const SeriesStats *stx, const double *sy, const double *y,
                          const SeriesStats *sty, const ScanTile *tiles, int64_t n_tiles,
-                         const double *lags, int64_t K, int eps, double h, double Rh,
+                         const double *lags, int64_t K, int eps, double h, double Rh, int hann,
                          double *num, double *den, unsigned long long *cnt, cudaStream_t st);
 // Bootstrap replicates (k_boot.cu): n_boot resamples with replacement of the n
 // points (t, x), each in time order, written to bt, bx [n_boot][n]; cnt is

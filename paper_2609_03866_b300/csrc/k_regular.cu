@@ -17,8 +17,8 @@
 //      W_m = conj(A_m) B_m + i conj(MA_m) MB_m, whose transform is
 //      2^lg (R(-d) + i C(-d)) with both parts real;
 //   4. one more forward FFT, then per lag the weighted sum over the lattice
-//      separations within the kernel's reach (h for the rectangle, 8 h for the
-//      Gaussian, whose tail beyond is 1.3e-14 of the peak).
+//      separations within the kernel's reach (h for the rectangle and the Hann
+//      window, 8 h for the Gaussian, whose tail beyond is 1.3e-14 of the peak).
 // Pair counts C(d) come out of FP64 FFTs within far less than 1/2 of an
 // integer and are rounded, so rectangle counts are exact.  A rectangle pair
 // counts when |fl(d dt - tau)| <= h in FP64 (the lattice separation itself,
@@ -138,8 +138,9 @@ __global__ void reg_spectrum_kernel(const double2 *__restrict__ Z1, const double
 
 // Per lag: N = sum_d R(d) b(d dt - tau), B = sum_d C(d) b(d dt - tau) over the
 // separations within the kernel's reach.  T = FFT(W) holds N_grid (R(-d) + i C(-d)).
+// kern: 0 Gaussian (reach 8 h), 1 rectangle, 2 Hann window (reach h, closed).
 __global__ void reg_lag_kernel(const double2 *__restrict__ T, int64_t N, const double *__restrict__ lags, int64_t K,
-                               double dt, int rect, double h, double reach, double *__restrict__ num,
+                               double dt, int kern, double h, double reach, double *__restrict__ num,
                                double *__restrict__ den, int64_t *__restrict__ cnt) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
@@ -152,9 +153,13 @@ __global__ void reg_lag_kernel(const double2 *__restrict__ T, int64_t N, const d
     for (int64_t d = d0; d <= d1; ++d) {
         const double u = __dsub_rn(__dmul_rn((double)d, dt), tau);
         double wgt;
-        if (rect) {
+        if (kern == 1) {
             if (!(fabs(u) <= h)) continue;
             wgt = 1.0;
+        } else if (kern == 2) {
+            if (!(fabs(u) <= h)) continue;
+            const double cw = cospi(0.5 * u / h);
+            wgt = cw * cw / h;
         } else {
             if (!(fabs(u) <= reach)) continue;
             wgt = gnorm * exp(-0.5 * (u / h) * (u / h));
@@ -168,7 +173,7 @@ __global__ void reg_lag_kernel(const double2 *__restrict__ T, int64_t N, const d
     }
     num[k] = sn;
     den[k] = sd;
-    if (cnt) cnt[k] = rect ? sc : 0;
+    if (cnt) cnt[k] = kern != 0 ? sc : 0;
 }
 
 __global__ void reg_finish_kernel(const double *__restrict__ num, const double *__restrict__ den, int64_t K,
@@ -257,8 +262,8 @@ ncf_status regular_launch(const int64_t *mx, const double *x, int64_t nx, const 
                           int64_t K, int kernel, double h, int lag0, char *ws, double *c_out, double *b_out,
                           int64_t *count_out, cudaStream_t st, std::string *msg) {
     const bool ccf = my != nullptr;
-    const bool rect = kernel == NCF_RECTANGLE;
-    const double reach = rect ? h : 8.0 * h;
+    const int kern = kernel == NCF_RECTANGLE ? 1 : (kernel == NCF_HANNING ? 2 : 0);
+    const double reach = kern == 0 ? 8.0 * h : h;
     const RegStats *dst = reinterpret_cast<const RegStats *>(stat_buf);
     const RegLayout Lo = reg_layout(lg, ccf, K);
     const int64_t N = (int64_t)1 << lg;
@@ -306,10 +311,10 @@ ncf_status regular_launch(const int64_t *mx, const double *x, int64_t nx, const 
         cudaMemsetAsync(misc, 0, 8, st);
         double2 *Tx = pipeline(mx, x, nx, dst, nullptr, nullptr, 0, nullptr);
         NCF_LAUNCH("reg_lag_kernel", st,
-                   reg_lag_kernel<<<1, 32, 0, st>>>(Tx, N, misc, 1, dt, rect, h, reach, num + K, den + K, nullptr));
+                   reg_lag_kernel<<<1, 32, 0, st>>>(Tx, N, misc, 1, dt, kern, h, reach, num + K, den + K, nullptr));
         if (ccf) {
             double2 *Ty = pipeline(my, y, ny, dst + 1, nullptr, nullptr, 0, nullptr);
-            NCF_LAUNCH("reg_lag_kernel", st, reg_lag_kernel<<<1, 32, 0, st>>>(Ty, N, misc, 1, dt, rect, h, reach,
+            NCF_LAUNCH("reg_lag_kernel", st, reg_lag_kernel<<<1, 32, 0, st>>>(Ty, N, misc, 1, dt, kern, h, reach,
                                                                               num + K + 1, den + K + 1, nullptr));
         }
         scale = misc + 1;
@@ -318,7 +323,7 @@ ncf_status regular_launch(const int64_t *mx, const double *x, int64_t nx, const 
     double2 *T = pipeline(mx, x, nx, dst, my, y, ny, ccf ? dst + 1 : nullptr);
     const unsigned kb = blocks(K);
     NCF_LAUNCH("reg_lag_kernel", st,
-               reg_lag_kernel<<<kb, 256, 0, st>>>(T, N, lags, K, dt, rect, h, reach, num, den, count_out));
+               reg_lag_kernel<<<kb, 256, 0, st>>>(T, N, lags, K, dt, kern, h, reach, num, den, count_out));
     NCF_LAUNCH("reg_finish_kernel", st, reg_finish_kernel<<<kb, 256, 0, st>>>(num, den, K, scale, c_out, b_out));
     if (cudaGetLastError() != cudaSuccess) {
         *msg = "regular path: kernel launch failed";

@@ -33,7 +33,7 @@ gauss_window_kernel(const double *__restrict__ tx, const double *__restrict__ x,
                     const int64_t *__restrict__ offs_x, const SeriesStats *__restrict__ stx,
                     const double *__restrict__ sy, const double *__restrict__ y,
                     const SeriesStats *__restrict__ sty, const ScanTile *__restrict__ tiles,
-                    const double *__restrict__ lags, int64_t K, int eps, double h, double Rh,
+                    const double *__restrict__ lags, int64_t K, int eps, double h, double Rh, int hann,
                     double *__restrict__ num, double *__restrict__ den,
                     unsigned long long *__restrict__ cnt) {
     const ScanTile tile = tiles[blockIdx.x];
@@ -45,7 +45,8 @@ gauss_window_kernel(const double *__restrict__ tx, const double *__restrict__ x,
     const double mx = stx[tile.b].mean, ix = stx[tile.b].inv_std;
     const double my = sty[tile.b].mean, iy = sty[tile.b].inv_std;
     const double inv2h2 = 1.0 / (2.0 * h * h);
-    const double norm = kInvSqrt2Pi / h;
+    const double inv2h = 0.5 / h;
+    const double norm = hann ? 1.0 / h : kInvSqrt2Pi / h;
     const int64_t j0 = tile.j0 + (int64_t)lane * kRunJ;
     const int64_t j1 = min(j0 + kRunJ, tile.j1);
     double N = 0.0, Bw = 0.0;
@@ -59,19 +60,37 @@ gauss_window_kernel(const double *__restrict__ tx, const double *__restrict__ x,
             }
             return lo;
         };
+        // first index with t > v
+        auto ub = [&](int64_t lo, int64_t hi, double v) {
+            while (lo < hi) {
+                int64_t mid = lo + ((hi - lo) >> 1);
+                if (tx[mid] <= v) lo = mid + 1; else hi = mid;
+            }
+            return lo;
+        };
+        // Gaussian: half-open [c - Rh, c + Rh); Hann: the rectangle's closed [c - h, c + h]
         const double c0 = centre(sy[j0], tau, eps);
         int64_t lo = lb(xa, xb, __dsub_rn(c0, Rh));
-        int64_t hi = lb(lo, xb, __dadd_rn(c0, Rh));
+        int64_t hi = hann ? ub(lo, xb, __dadd_rn(c0, Rh)) : lb(lo, xb, __dadd_rn(c0, Rh));
         for (int64_t j = j0; j < j1; ++j) {
             const double cj = centre(sy[j], tau, eps);
             const double wl = __dsub_rn(cj, Rh), wu = __dadd_rn(cj, Rh);
             while (lo < xb && tx[lo] < wl) ++lo;
-            while (hi < xb && tx[hi] < wu) ++hi;
+            if (hann)
+                while (hi < xb && tx[hi] <= wu) ++hi;
+            else
+                while (hi < xb && tx[hi] < wu) ++hi;
             const double yj = (y[j] - my) * iy;
             double nj = 0.0, bj = 0.0;
             for (int64_t i = lo; i < hi; ++i) {
                 const double d = tx[i] - cj;
-                const double w = exp(-d * d * inv2h2);
+                double w;
+                if (hann) {
+                    const double cw = cospi(d * inv2h);
+                    w = cw * cw;
+                } else {
+                    w = exp(-d * d * inv2h2);
+                }
                 bj += w;
                 nj = fma(w, (x[i] - mx) * ix, nj);
             }
@@ -182,12 +201,12 @@ void launch_lag0_scale_gauss(const double *num_x, const double *den_x, const dou
 void launch_gauss_window(const double *tx, const double *x, const int64_t *offs_x,
                          const SeriesStats *stx, const double *sy, const double *y,
                          const SeriesStats *sty, const ScanTile *tiles, int64_t n_tiles,
-                         const double *lags, int64_t K, int eps, double h, double Rh,
+                         const double *lags, int64_t K, int eps, double h, double Rh, int hann,
                          double *num, double *den, unsigned long long *cnt, cudaStream_t st) {
     dim3 grid((unsigned)n_tiles, (unsigned)((K + kWarps - 1) / kWarps));
     NCF_LAUNCH("gauss_window_kernel", st,
     gauss_window_kernel<<<grid, kWarps * 32, 0, st>>>(tx, x, offs_x, stx, sy, y, sty, tiles, lags, K,
-                                                      eps, h, Rh, num, den, cnt));
+                                                      eps, h, Rh, hann, num, den, cnt));
 }
 
 void launch_finish_rect(const unsigned long long *cnt, const unsigned long long *num128,

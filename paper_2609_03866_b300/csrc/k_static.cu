@@ -149,7 +149,7 @@ extern "C" ncf_status ncf_corr_window_static(const double *t, const double *x, i
     const double R = trunc_R > 0.0 ? trunc_R : 8.0;
     const int64_t n_tiles = (n_out + tileJ - 1) / tileJ;
     launch_gauss_window(t, x, offs, stats, acf ? t : s, acf ? x : y, acf ? stats : stats + 1, tiles,
-                        n_tiles, lags, K, acf ? +1 : -1, h, R * h, num, den, cnt, st);
+                        n_tiles, lags, K, acf ? +1 : -1, h, R * h, 0, num, den, cnt, st);
     launch_finish_gauss(num, den, cnt, 1, K, nullptr, nullptr, c_out, b_out, nullptr, st);
     if (cudaGetLastError() != cudaSuccess) return NCF_ECUDA;
     return NCF_OK;
