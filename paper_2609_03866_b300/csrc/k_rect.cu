@@ -320,11 +320,15 @@ constexpr int kPtWarps = 8;
 constexpr int kPtM = kRectTile / (kPtWarps * 32);  // outer points per lane
 constexpr int kPtBatch = 4;                         // points of a lane handled together (load ILP)
 constexpr int kPtCap = 4000;                        // staged entries per sub-group
+constexpr int kPtSamples = 1024;                    // planning samples of a lag group's key range
+constexpr int kPtExact = 16;                        // sample stride up to which the bounds stay coarse
+constexpr int kPtStage = 3;                         // staged entries a thread loads per round
 constexpr int kPtBinsLog = 13;
 constexpr int kPtBins = 1 << kPtBinsLog;            // rank-table bins
 static_assert(kPtBins % (kPtWarps * 32) == 0, "bins split evenly over the threads");
 static_assert(16 * (kPtCap + 1) <= 65535, "rank-table entries are 16-bit byte offsets");
 static_assert(kPtM % kPtBatch == 0, "whole batches");
+static_assert(8 * kPtSamples <= 16 * (kPtCap + 1), "planning samples fit the staging area");
 
 struct PtSub {
     int ka, kb, global, pad;
@@ -336,6 +340,7 @@ struct __align__(16) PtSmem {
     uint16_t sT[kPtBins];               // byte offset into sE of the bin's first entry
     int4 lc[kLagGroup];                 // lag offsets relative to vmin: dlc, dlc2, duc, duc2
     int64_t klo[kLagGroup], khi[kLagGroup];
+    int64_t kdl[kLagGroup], kdu[kLagGroup];
     PtSub sub[kLagGroup];
     int2 seg[16];                       // stack of outer-point segments [pa, pb) still to do
     int n_sub, n_seg;
@@ -350,6 +355,22 @@ __device__ __forceinline__ int4 pt_ent(const unsigned char *S, unsigned off) {
 }
 __device__ __forceinline__ unsigned pt_bin(const unsigned char *S, int32_t v, int bsh) {
     return *reinterpret_cast<const uint16_t *>(S + kOffT + 2u * (unsigned)(v >> bsh));
+}
+
+// Bounds of lower_bound(Tx, ia, ib, v) from the planning samples samp[m] =
+// Tx[ia + m stride], m < ns: lo <= answer <= hi with hi - lo < stride.  Past
+// kPtExact the bracket is closed by a binary search on the global keys.
+__device__ __forceinline__ void pt_bracket(const int64_t *samp, int ns, int64_t stride,
+                                           const int64_t *__restrict__ Tx, int64_t ia, int64_t ib,
+                                           int64_t v, int64_t &lo, int64_t &hi) {
+    int a = 0, b = ns;
+    while (a < b) {
+        const int mid = (a + b) >> 1;
+        if (samp[mid] < v) a = mid + 1; else b = mid;
+    }
+    lo = a == 0 ? ia : ia + (int64_t)(a - 1) * stride + 1;
+    hi = min(ia + (int64_t)a * stride, ib);
+    if (stride > kPtExact) lo = hi = lower_bound64(Tx, lo, hi, v);
 }
 
 // Window edges inside the coarse band: full keys, then the FP64 predicate of
@@ -561,8 +582,23 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
         __syncthreads();  // every thread has read the segment before warp 0 edits the stack
         // plan the segment: lag sub-groups whose key unions fit the staging area,
         // or a split of the segment when one lag's union does not fit
+        const bool whole = pa == 0 && pb == tn && ib - ia + 1 <= kPtCap;
+        // planning samples of the group's keys [ia, ib), one round of independent
+        // loads by the whole CTA into the (idle) staging area; the searches below
+        // run on them in shared memory
+        const int64_t *samp = reinterpret_cast<const int64_t *>(sm.sE);
+        int64_t stride = 1;
+        int ns = 0;
+        if (!whole) {
+            const int64_t nr = ib - ia;
+            stride = max((int64_t)1, (nr + kPtSamples - 1) / kPtSamples);
+            ns = (int)((nr + stride - 1) / stride);
+            int64_t *w = reinterpret_cast<int64_t *>(sm.sE);
+            for (int m = tid; m < ns; m += blockDim.x) w[m] = Tx[ia + (int64_t)m * stride];
+            __syncthreads();
+        }
         if (warp == 0) {
-            if (pa == 0 && pb == tn && ib - ia + 1 <= kPtCap) {
+            if (whole) {
                 if (lane == 0) {
                     sm.sub[0] = PtSub{0, nk, 0, 0, ia, ib, gmin[g], gmax[g]};
                     sm.n_sub = 1;
@@ -572,15 +608,24 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                 const int64_t Sa = Sy[tile.j0 + pa], Sb = Sy[tile.j0 + pb - 1];
                 int big = 0, wide = 0;
                 if (lane < nk) {
+                    // bracketed ranks: the lower end of the first query, the upper
+                    // end of the last; the staged range may grow by < 2 stride keys
                     const int64_t dl = dls[k0 + lane], du = dus[k0 + lane];
-                    const int64_t lo = lower_bound64(Tx, ia, ib, Sa + dl - eta);
-                    const int64_t hi = lower_bound64(Tx, lo, ib, Sb + du + eta);
+                    int64_t lo, hi, x0, x1;
+                    pt_bracket(samp, ns, stride, Tx, ia, ib, Sa + dl - eta, lo, x1);
+                    pt_bracket(samp, ns, stride, Tx, ia, ib, Sb + du + eta, x0, hi);
+                    hi = max(hi, lo);
                     sm.klo[lane] = lo;
                     sm.khi[lane] = hi;
+                    sm.kdl[lane] = dl;
+                    sm.kdu[lane] = du;
                     big = hi - lo + 1 > kPtCap;
                     // a single outer point's window already fills half the area:
                     // splitting would not help, the lag runs on the global keys
-                    if (big) wide = lower_bound64(Tx, lo, ib, Sa + du + eta) - lo + 1 > kPtCap / 2;
+                    if (big) {
+                        pt_bracket(samp, ns, stride, Tx, ia, ib, Sa + du + eta, x0, x1);
+                        wide = x1 - lo + 1 > kPtCap / 2;
+                    }
                 }
                 const bool split = __any_sync(0xffffffffu, big && !wide) && pb - pa > 32;
                 __syncwarp();
@@ -595,7 +640,7 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                         int n = 0, a = 0;
                         while (a < nk) {
                             int64_t lo = sm.klo[a], hi = sm.khi[a];
-                            int64_t dmn = dls[k0 + a], dmx = dus[k0 + a];
+                            int64_t dmn = sm.kdl[a], dmx = sm.kdu[a];
                             int b = a + 1;
                             const int gl = (hi - lo + 1 > kPtCap) ? 1 : 0;
                             while (!gl && b < nk) {
@@ -603,8 +648,8 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                                 if (nhi - nlo + 1 > kPtCap) break;
                                 lo = nlo;
                                 hi = nhi;
-                                dmn = min(dmn, dls[k0 + b]);
-                                dmx = max(dmx, dus[k0 + b]);
+                                dmn = min(dmn, sm.kdl[b]);
+                                dmx = max(dmx, sm.kdu[b]);
                                 ++b;
                             }
                             sm.sub[n++] = PtSub{a, b, gl, 0, lo, hi, dmn, dmx};
@@ -635,16 +680,28 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                 const int32_t vmax = scb + (int32_t)((S0 + sb.dmax + eta - base) >> sh) + 2;
                 const int vbits = 32 - __clz(max(vmax - vmin, 1));
                 const int bsh = max(0, vbits - kPtBinsLog);
-                // entries 0 .. nK: keys (nK: the sentinel) and the limbs of P[ia + i]
-                for (int i = tid; i <= max(nK, 0); i += blockDim.x) {
-                    int32_t key = kSentinel;
-                    if (i < nK) {
-                        const int64_t v = ((Tx[sb.ia + i] - base) >> sh) - vmin;
-                        key = (int32_t)max(min(v, (int64_t)(1 << 30)), (int64_t)-1);
+                // entries 0 .. nK: keys (nK: the sentinel) and the limbs of P[ia + i];
+                // each thread issues the loads of kPtStage entries before any store
+                for (int i0 = tid; i0 <= max(nK, 0); i0 += kPtStage * blockDim.x) {
+                    int64_t tv[kPtStage], pv[kPtStage];
+#pragma unroll
+                    for (int u = 0; u < kPtStage; ++u) {
+                        const int i = i0 + u * blockDim.x;
+                        tv[u] = i < nK ? Tx[sb.ia + i] : 0;
+                        pv[u] = i <= nK ? P[sb.ia + i] : 0;
                     }
-                    const int64_t pv = P[sb.ia + i];
-                    sm.sE[i] = make_int4(key, (int32_t)(pv & 0x1fffff), (int32_t)((pv >> 21) & 0x1fffff),
-                                         (int32_t)(pv >> 42));
+#pragma unroll
+                    for (int u = 0; u < kPtStage; ++u) {
+                        const int i = i0 + u * blockDim.x;
+                        if (i > nK) break;
+                        int32_t key = kSentinel;
+                        if (i < nK) {
+                            const int64_t v = ((tv[u] - base) >> sh) - vmin;
+                            key = (int32_t)max(min(v, (int64_t)(1 << 30)), (int64_t)-1);
+                        }
+                        sm.sE[i] = make_int4(key, (int32_t)(pv[u] & 0x1fffff),
+                                             (int32_t)((pv[u] >> 21) & 0x1fffff), (int32_t)(pv[u] >> 42));
+                    }
                 }
                 if (tid < sb.kb - sb.ka) {
                     const int k = (int)k0 + sb.ka + tid;
