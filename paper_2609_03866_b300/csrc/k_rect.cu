@@ -337,7 +337,7 @@ struct PtSub {
 
 struct __align__(16) PtSmem {
     int4 sE[kPtCap + 1];                // {key, p0, p1, p2}; entry nK carries the sentinel key
-    uint16_t sT[kPtBins];               // byte offset into sE of the bin's first entry
+    uint16_t sT[kPtBins];               // byte offset into sE of the bin's first entry (16-byte aligned)
     int4 lc[kLagGroup];                 // lag offsets relative to vmin: dlc, dlc2, duc, duc2
     int64_t klo[kLagGroup], khi[kLagGroup];
     int64_t kdl[kLagGroup], kdu[kLagGroup];
@@ -349,6 +349,7 @@ struct __align__(16) PtSmem {
 };
 constexpr unsigned kOffE = offsetof(PtSmem, sE);
 constexpr unsigned kOffT = offsetof(PtSmem, sT);
+static_assert(kOffT % 16 == 0, "the rank table is written with 16-byte stores");
 
 __device__ __forceinline__ int4 pt_ent(const unsigned char *S, unsigned off) {
     return *reinterpret_cast<const int4 *>(S + kOffE + off);
@@ -713,9 +714,11 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                 }
                 __syncthreads();
                 // rank table: sT[b] = 16 x (first index with key >= b << bsh); each
-                // thread merges 32 consecutive bins against the keys
+                // thread merges 32 consecutive bins against the keys (the current
+                // key kept in a register) and writes them as four 16-byte stores
                 {
                     constexpr int kPer = kPtBins / (kPtWarps * 32);
+                    static_assert(kPer % 8 == 0, "bins are written eight at a time");
                     const int b0 = tid * kPer;
                     const int32_t v0 = b0 << bsh;
                     int lo = 0, hi = max(nK, 0);
@@ -724,11 +727,23 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                         if (sm.sE[mid].x < v0) lo = mid + 1; else hi = mid;
                     }
                     int p = lo;
-#pragma unroll 4
-                    for (int b = b0; b < b0 + kPer; ++b) {
-                        const int32_t v = b << bsh;
-                        while (sm.sE[p].x < v) ++p;
-                        sm.sT[b] = (uint16_t)(16 * p);
+                    int32_t kp = sm.sE[p].x;  // entry nK holds the sentinel: every walk ends there
+                    uint4 *dst = reinterpret_cast<uint4 *>(sm.sT + b0);
+#pragma unroll
+                    for (int q = 0; q < kPer / 8; ++q) {
+                        unsigned w[4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            unsigned pair = 0;
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                const int32_t v = (b0 + 8 * q + 2 * r + e) << bsh;
+                                while (kp < v) kp = sm.sE[++p].x;
+                                pair |= (unsigned)(16 * p) << (16 * e);
+                            }
+                            w[r] = pair;
+                        }
+                        dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
                     }
                 }
                 __syncthreads();
