@@ -189,6 +189,44 @@ NCF_API ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, cons
 
 
 /*
+ * The paper's own NUFFT estimators, smoothing step included (Appendix
+ * "NUFFT-based ACF/CCF algorithms", Algorithms 1-4), for users who need the
+ * published package's numbers rather than Eq. kernel_estimator itself:
+ *   Algorithm 1  L = span + 2 max|tau| (lag 0 included), t_c = t_min + span/2,
+ *                N1 = round(32 n_max L / span) (Eq. N1_default; N1 > 0 overrides);
+ *   Algorithm 2  CCF: type-1 transforms of the standardised x and y on the map
+ *                t -> pi + 2 pi (t - t_c) / L (N1 modes k = -floor(N1/2) ..
+ *                ceil(N1/2) - 1, exp(+i k t~)), cross spectrum conj(F1) F2, its
+ *                type-2 transform (exp(-i k tau~)) at the sorted lags with lag 0
+ *                prepended, the smoothing S_h along that sorted array, division
+ *                by the pair count, unsorting, division by sqrt(ACF_x(0) ACF_y(0));
+ *   Algorithm 3  ACF(0) of each series for that scale, smoothed at the centre of
+ *                the array -n_h .. n_h, n_h = max(ceil(4h) + 2, 5);
+ *   Algorithm 4  ACF: the same with |F|^2, normalised by the prepended lag 0.
+ * S_h (the paper names it without fixing edges or truncation; this library
+ * reads it as scipy.ndimage's defaults): Gaussian weights exp(-j^2 / 2h^2),
+ * |j| <= int(4h + 0.5), unit sum; rectangle: the mean of round(2h) entries
+ * j = -size/2 .. size - 1 - size/2 (round half to even, size >= 1); both with
+ * half-sample reflection at the array ends.  PairCount (Algorithms 5, 6): the
+ * Gaussian summed over [c - 6h, c + 6h), the rectangle counted in [c - h, c + h].
+ * The smoothing acts on array positions, so the result matches Eq.
+ * kernel_estimator only for integer times with unit lag spacing; the
+ * transforms are evaluated to about 1e-13 relative (no FINUFFT tolerance).
+ *
+ * DEVICE pointers as ncf_corr: t, x [nx], s, y [ny] (both NULL for an ACF),
+ * lags [K] (any order), c_out [K], b_out [K] or NULL (PairCount clamped below
+ * at 1e-16).  kernel: NCF_GAUSSIAN or NCF_RECTANGLE (NCF_EUNSUPPORTED
+ * otherwise).  The data must span a positive interval (NCF_EDEGENERATE) and
+ * N1 must fit a grid of 2^27 cells, N1 <= about 6.7e7 (NCF_EUNSUPPORTED).
+ * Other errors as ncf_corr.  Several host synchronisations (statistics, lags,
+ * and the pair counts, which run through ncf_corr's windowed paths).
+ */
+NCF_API ncf_status ncf_corr_paper(ncf_ctx *ctx, const double *t, const double *x, int64_t nx,
+                                  const double *s, const double *y, int64_t ny, const double *lags, int64_t K,
+                                  ncf_kernel kernel, double h, int64_t N1, double *c_out, double *b_out,
+                                  void *stream);
+
+/*
  * Classic-FFT estimator for data on a regular grid (the paper's dedicated FFT
  * path for regularly sampled series, Table 1 and Sec. 5.2): every time is a
  * whole multiple of one step, t_i = m_x[i] dt and s_j = m_y[j] dt, so a pair's

@@ -243,6 +243,36 @@ def corr(t, x, lags, kernel="gaussian", h=1.0, s=None, y=None, path="auto", prec
     return {"c": c, "b": b, "count": cnt}
 
 
+def corr_paper(t, x, lags, kernel="gaussian", h=1.0, s=None, y=None, N1=0, ctx: Context | None = None,
+               stream=None):
+    """The paper's own NUFFT estimator with the smoothing step (ncf_corr_paper,
+    Algorithms 1-4): ACF (s, y omitted) or CCF.  N1 = 0 takes the default grid
+    size round(32 n_max L / span).  Returns dict(c, b) of device tensors in the
+    order of `lags` (b: the pair counts, clamped below at 1e-16)."""
+    import torch
+    L = lib()
+    if not getattr(L, "_paper_types", False):
+        vp = ctypes.c_void_p
+        L.ncf_corr_paper.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, ctypes.c_int64,
+                                     ctypes.c_int, ctypes.c_double, ctypes.c_int64, vp, vp, vp]
+        L.ncf_corr_paper.restype = ctypes.c_int
+        L._paper_types = True
+    ctx = ctx or default_context()
+    dev = torch.device("cuda", ctx.device)
+    t, x, lags = _dev(t, dev), _dev(x, dev), _dev(lags, dev)
+    acf = s is None
+    if not acf:
+        s, y = _dev(s, dev), _dev(y, dev)
+    K = lags.numel()
+    c = torch.empty(K, dtype=torch.float64, device=dev)
+    b = torch.empty(K, dtype=torch.float64, device=dev)
+    rc = L.ncf_corr_paper(ctx.handle, _ptr(t), _ptr(x), t.numel(), _ptr(None if acf else s),
+                          _ptr(None if acf else y), 0 if acf else s.numel(), _ptr(lags), K, KERNELS[kernel],
+                          float(h), int(N1), _ptr(c), _ptr(b), _stream_handle(stream, dev))
+    ctx.check(rc)
+    return {"c": c, "b": b}
+
+
 def selftest_bounded_wait(ctx: Context | None = None, stream=None) -> int:
     """Runs the bounded-wait self-test (ncf_selftest_bounded_wait) and returns the
     device status word it produced (bit 1: the wait gave up as designed)."""

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -48,6 +49,8 @@ struct ncf_ctx {
     size_t hbuf_cap = 0;
     char *boot = nullptr;        // bootstrap replicates and their multiplicities
     size_t boot_cap = 0;
+    char *paper = nullptr;       // the paper's NUFFT variant (ncf_corr_paper)
+    size_t paper_cap = 0;
     uint64_t launches = 0;
     cudaEvent_t staged = nullptr;  // recorded after staging copies issued past the read-back sync
     cudaStream_t copy_st = nullptr;  // host-buffer calls: uploads and read-backs beside the compute stream
@@ -773,6 +776,183 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
     return launch(ctx, ev, /*stats_fresh=*/true, /*guard=*/false, c_out, b_out, count_out, st);
 }
 
+// frac(tau / L) 2^64 to about one unit: q = fl(tau / L), the exact remainder
+// e = tau - q L from one FMA, then the fraction of q plus e / L.
+static unsigned long long lag_phase(double tau, double L) {
+    const double q = tau / L;
+    const double e = std::fma(-q, L, tau);
+    const double fq = q - std::floor(q);                                  // exact, in [0, 1)
+    const unsigned long long hi = (unsigned long long)std::ldexp(fq, 64);  // exact above 2^-11
+    const long long lo = std::llround(std::ldexp(e / L, 64));
+    return hi + (unsigned long long)lo;
+}
+
+static ncf_status corr_paper_impl(ncf_ctx *ctx, const double *t, const double *x, int64_t nx, const double *s,
+                                  const double *y, int64_t ny, const double *lags, int64_t K, ncf_kernel kernel,
+                                  double h, int64_t N1, double *c_out, double *b_out, cudaStream_t st) {
+    LaunchScope scope(ctx);
+    ctx->err.clear();
+    if (ctx->staged) NCF_CUDA(cudaEventSynchronize(ctx->staged));
+    if (kernel != NCF_GAUSSIAN && kernel != NCF_RECTANGLE)
+        return fail(ctx, NCF_EUNSUPPORTED, "the paper's NUFFT estimators smooth with a Gaussian or a box only");
+    if (!(h > 0.0) || !std::isfinite(h)) return fail(ctx, NCF_EINVAL, "h = %g (need finite h > 0)", h);
+    const int box = kernel == NCF_RECTANGLE ? (int)std::nearbyint(2.0 * h) : 0;
+    if (kernel == NCF_RECTANGLE && box < 1)
+        return fail(ctx, NCF_EINVAL, "box filter size round(2h) = %d for h = %g (need >= 1)", box, h);
+    if (N1 < 0) return fail(ctx, NCF_EINVAL, "N1 = %lld (need >= 0; 0 = the default rule)", (long long)N1);
+    if (!c_out) return fail(ctx, NCF_EINVAL, "c_out is NULL");
+    ncf_options opt;
+    ncf_options_default(&opt);
+    opt.kernel = kernel;
+    opt.h = h;
+    opt.path = NCF_PATH_WINDOWED;
+    opt.precision = NCF_FP64;
+    opt.norm = NCF_NORM_NONE;
+    opt.trunc_R = kernel == NCF_GAUSSIAN ? 6.0 : 0.0;  // PairCount's window [c - 6h, c + 6h)
+    const int64_t ox[2] = {0, nx}, oy[2] = {0, ny};
+    const bool acf = (s == nullptr && y == nullptr);
+    Eval ev;
+    ncf_status rc = check_args(ctx, ox, t, x, acf ? nullptr : oy, s, y, 1, lags, K, &opt, ev);
+    if (rc) return rc;
+    ev.X.t = t; ev.X.v = x;
+    if (!acf) { ev.Y.t = s; ev.Y.v = y; }
+    if ((rc = grow(ctx, &ctx->ws, &ctx->ws_cap, pre_bytes(ev), st))) return rc;
+    carve_pre(ev, ctx->ws);
+    if ((rc = analyze(ctx, ev, lags, st))) return rc;
+
+    // Algorithms 2 and 4, first steps: lag 0 prepended, stable sort
+    const int64_t K1 = K + 1;
+    std::vector<double> tau_eval(K1);
+    tau_eval[0] = 0.0;
+    for (int64_t k = 0; k < K; ++k) tau_eval[k + 1] = ev.lagv[k];
+    std::vector<int64_t> perm(K1);
+    std::iota(perm.begin(), perm.end(), 0);
+    std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) { return tau_eval[a] < tau_eval[b]; });
+    std::vector<double> tau_srt(K1);
+    int64_t pos0 = 0;
+    for (int64_t i = 0; i < K1; ++i) {
+        tau_srt[i] = tau_eval[perm[i]];
+        if (perm[i] == 0) pos0 = i;
+    }
+    // Algorithm 1 on the union of both series' extents
+    double t_min = ev.X.stats[0].t_first, t_max = ev.X.stats[0].t_last;
+    int64_t n_max = nx;
+    if (!acf) {
+        t_min = std::min(t_min, ev.Y.stats[0].t_first);
+        t_max = std::max(t_max, ev.Y.stats[0].t_last);
+        n_max = std::max(nx, ny);
+    }
+    const double span = t_max - t_min;
+    if (!(span > 0.0)) return fail(ctx, NCF_EDEGENERATE, "the times span no interval (span = %g)", span);
+    double max_tau = 0.0;
+    for (double v : tau_srt) max_tau = std::max(max_tau, std::fabs(v));
+    const double L = span + 2.0 * max_tau;
+    const double tc = t_min + span / 2.0;
+    const double n1f = N1 > 0 ? (double)N1 : std::nearbyint(32.0 * (double)n_max * L / span);
+    if (!(n1f >= 1.0) || n1f > 1e12) return fail(ctx, NCF_EUNSUPPORTED, "N1 = %g out of range", n1f);
+    PaperModes pm;
+    std::string msg;
+    if ((rc = paper_modes_plan(L, tc, (int64_t)n1f, &pm, &msg))) return fail(ctx, rc, "%s", msg.c_str());
+    // Algorithm 3's symmetric array, the smoothing weights and the lag phases
+    const int n_h = std::max((int)std::ceil(4.0 * h) + 2, 5);
+    const int64_t nsym = 2 * n_h + 1;
+    std::vector<double> w;
+    int o0 = 0;
+    if (kernel == NCF_GAUSSIAN) {
+        const int r = (int)(4.0 * h + 0.5);
+        double sum = 0.0;
+        for (int j = -r; j <= r; ++j) {
+            w.push_back(std::exp(-0.5 / (h * h) * (double)j * (double)j));
+            sum += w.back();
+        }
+        for (double &v : w) v /= sum;
+        o0 = -r;
+    } else {
+        w.assign(box, 1.0 / box);
+        o0 = -(box / 2);
+    }
+    std::vector<unsigned long long> phi(K1 + nsym);
+    for (int64_t i = 0; i < K1; ++i) phi[i] = lag_phase(tau_srt[i], L);
+    for (int64_t j = 0; j < nsym; ++j) phi[K1 + j] = lag_phase((double)(j - n_h), L);
+    const double zero = 0.0;
+
+    // device memory of the variant (ctx->paper; the nested pair-count calls use ws, ws2, pinned)
+    const int64_t Mh = pm.Mh;
+    const size_t modes_b = paper_modes_bytes(pm, !acf);
+    const size_t need = modes_b + al((Mh + 1) * 16) * (acf ? 1 : 3) + al((K1 + nsym) * 8) +
+                        al(K1 * 8) * 5 + al(nsym * 8) * 2 + al(8) * 3 + al(K1 * 8) + al(w.size() * 8) + 4096;
+    if ((rc = grow(ctx, &ctx->paper, &ctx->paper_cap, need, st))) return rc;
+    Arena ar{ctx->paper, ctx->paper_cap, 0};
+    char *modes_ws = ar.take<char>(modes_b);
+    double2 *A = ar.take<double2>(Mh + 1);
+    double2 *Ax = acf ? nullptr : ar.take<double2>(Mh + 1);
+    double2 *Ay = acf ? nullptr : ar.take<double2>(Mh + 1);
+    auto *d_phi = ar.take<unsigned long long>(K1 + nsym);
+    double *craw = ar.take<double>(K1), *bsrt = ar.take<double>(K1), *ctmp = ar.take<double>(K1);
+    double *d_tau = ar.take<double>(K1), *tmp = ar.take<double>(K1);
+    double *craw_x = ar.take<double>(nsym), *craw_y = ar.take<double>(nsym);
+    double *bx0 = ar.take<double>(1), *by0 = ar.take<double>(1), *d_zero = ar.take<double>(1);
+    auto *d_perm = ar.take<int64_t>(K1);
+    double *d_w = ar.take<double>(w.size());
+    if (!modes_ws || !A || (!acf && (!Ax || !Ay)) || !d_phi || !craw || !bsrt || !ctmp || !d_tau || !tmp ||
+        !craw_x || !craw_y || !bx0 || !by0 || !d_zero || !d_perm || !d_w)
+        return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
+    const size_t pin_need = al((K1 + nsym) * 8) + al(K1 * 8) * 2 + al(8) + al(w.size() * 8) +
+                            paper_modes_pinned_bytes(pm) + 1024;
+    if ((rc = grow_pinned(ctx, pin_need, st))) return rc;
+    size_t off = 0;
+    auto up = [&](void *dst, const void *src, size_t bytes) -> ncf_status {
+        std::memcpy(ctx->pinned + off, src, bytes);
+        NCF_CUDA(cudaMemcpyAsync(dst, ctx->pinned + off, bytes, cudaMemcpyHostToDevice, st));
+        off += al(bytes);
+        return NCF_OK;
+    };
+    if ((rc = up(d_phi, phi.data(), (K1 + nsym) * 8))) return rc;
+    if ((rc = up(d_tau, tau_srt.data(), K1 * 8))) return rc;
+    if ((rc = up(d_perm, perm.data(), K1 * 8))) return rc;
+    if ((rc = up(d_zero, &zero, 8))) return rc;
+    if ((rc = up(d_w, w.data(), w.size() * 8))) return rc;
+
+    // type-1 coefficients, spectra and the raw correlation (Algorithms 2-4)
+    const SpecSide sx{ev.X.t, ev.X.v, ev.X.d_offs, ev.X.d_stats, ev.X.offs.data(), ev.X.stats.data(),
+                      ev.X.n_total, ev.X.n_max, ev.X.d_chunk_base, ev.X.n_chunks, ev.X.d_cs};
+    SpecSide sy{};
+    if (!acf)
+        sy = SpecSide{ev.Y.t, ev.Y.v, ev.Y.d_offs, ev.Y.d_stats, ev.Y.offs.data(), ev.Y.stats.data(),
+                      ev.Y.n_total, ev.Y.n_max, ev.Y.d_chunk_base, ev.Y.n_chunks, ev.Y.d_cs};
+    double2 *Fx = nullptr, *Fy = nullptr;
+    paper_modes_run(pm, sx, acf ? nullptr : &sy, modes_ws, ctx->pinned + off, &Fx, &Fy, st);
+    NCF_CUDA(cudaEventRecord(ctx->staged, st));
+    NCF_CUDA(cudaMemsetAsync(craw, 0, K1 * 8, st));
+    if (acf) {
+        paper_spectrum(Fx, Fx, Mh, pm.N1, A, st);
+    } else {
+        paper_spectrum(Fx, Fy, Mh, pm.N1, A, st);
+        paper_spectrum(Fx, Fx, Mh, pm.N1, Ax, st);
+        paper_spectrum(Fy, Fy, Mh, pm.N1, Ay, st);
+        NCF_CUDA(cudaMemsetAsync(craw_x, 0, nsym * 8, st));
+        NCF_CUDA(cudaMemsetAsync(craw_y, 0, nsym * 8, st));
+        paper_eval(Ax, Mh, d_phi + K1, nsym, craw_x, st);
+        paper_eval(Ay, Mh, d_phi + K1, nsym, craw_y, st);
+    }
+    paper_eval(A, Mh, d_phi, K1, craw, st);
+    // PairCount (Algorithms 5 and 6) through the windowed paths: the sorted lags
+    // and, for the CCF scales, lag 0 of each series' ACF
+    if ((rc = corr_batch_impl(ctx, ox, t, x, acf ? nullptr : oy, s, y, 1, d_tau, K1, &opt, ctmp, bsrt, nullptr, st)))
+        return rc;
+    if (!acf) {
+        if ((rc = corr_batch_impl(ctx, ox, t, x, nullptr, nullptr, nullptr, 1, d_zero, 1, &opt, ctmp, bx0, nullptr, st)))
+            return rc;
+        if ((rc = corr_batch_impl(ctx, oy, s, y, nullptr, nullptr, nullptr, 1, d_zero, 1, &opt, ctmp, by0, nullptr, st)))
+            return rc;
+    }
+    paper_finish(craw, bsrt, K1, d_perm, pos0, d_w, (int)w.size(), o0, acf, craw_x, craw_y, nsym, bx0, by0, tmp,
+                 c_out, b_out, st);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, NCF_ECUDA, "paper NUFFT launch failed: %s", cudaGetErrorString(e));
+    return NCF_OK;
+}
+
 }  // namespace ncf
 
 // ----------------------------------------------------------------------------
@@ -851,6 +1031,7 @@ void ncf_destroy(ncf_ctx *ctx) {
     if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
     for (cudaEvent_t e : ctx->copy_ev) cudaEventDestroy(e);
     if (ctx->boot) cudaFree(ctx->boot);
+    if (ctx->paper) cudaFree(ctx->paper);
     delete ctx;  // last: nothing above may touch ctx after this
 }
 
@@ -917,6 +1098,15 @@ ncf_status ncf_corr(ncf_ctx *ctx, const double *t, const double *x, int64_t nx, 
     const bool acf = (s == nullptr && y == nullptr);
     return ncf::corr_batch_impl(ctx, ox, t, x, acf ? nullptr : oy, s, y, 1, lags, K, opt, c_out, b_out,
                                 count_out, (cudaStream_t)stream);
+}
+
+ncf_status ncf_corr_paper(ncf_ctx *ctx, const double *t, const double *x, int64_t nx, const double *s,
+                          const double *y, int64_t ny, const double *lags, int64_t K, ncf_kernel kernel, double h,
+                          int64_t N1, double *c_out, double *b_out, void *stream) {
+    if (!ctx) return NCF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return NCF_ECUDA;
+    return ncf::corr_paper_impl(ctx, t, x, nx, s, y, ny, lags, K, kernel, h, N1, c_out, b_out,
+                                (cudaStream_t)stream);
 }
 
 ncf_status ncf_corr_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,

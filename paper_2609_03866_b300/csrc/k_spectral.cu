@@ -830,7 +830,157 @@ __global__ void spectral_guard_kernel(const SeriesStats *__restrict__ sx, const 
         atomicOr(status, STATUS_DOMAIN);
 }
 
+// ---------------------------------------------------------------------------
+// The paper's own NUFFT estimators (Algorithms 2-4, smoothing step included):
+// deconvolved type-1 coefficients on the padded period of Algorithm 1.
+// ---------------------------------------------------------------------------
+constexpr int kCoefRun = 32;  // consecutive modes per thread of the deconvolution
+
+// F_m = X_m / phihat_m for m = 0 .. Mh, X_m from the Hermitian unpack of the
+// grid transform.  phihat_m = (W/2) int_{-1}^{1} phi(z) cos(pi m W z / n_f) dz by
+// Gauss-Legendre quadrature; the integrand is even, so only the nq/2 positive
+// nodes are summed (twice).  Along a thread's run of modes the cosines follow
+// the rotation cos(pi (m+1) a) = Re[exp(i pi m a) exp(i pi a)], restarted from
+// sincospi at every run.
+__global__ void paper_coef_kernel(const double2 *__restrict__ Gx, const double2 *__restrict__ Gy, int nf,
+                                  int64_t Mh, int W, const double *__restrict__ gx,
+                                  const double *__restrict__ gphi, int nq_half, double2 *__restrict__ Fx,
+                                  double2 *__restrict__ Fy) {
+    const int64_t m0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kCoefRun;
+    if (m0 > Mh) return;
+    double acc[kCoefRun];
+#pragma unroll
+    for (int j = 0; j < kCoefRun; ++j) acc[j] = 0.0;
+    for (int q = 0; q < nq_half; ++q) {
+        const double a = (double)W / nf * gx[q];
+        const double w = gphi[q];
+        double c, sn, rc, rs;
+        sincospi((double)m0 * a, &sn, &c);
+        sincospi(a, &rs, &rc);
+#pragma unroll
+        for (int j = 0; j < kCoefRun; ++j) {
+            acc[j] = fma(w, c, acc[j]);
+            const double c2 = fma(c, rc, -sn * rs);
+            sn = fma(sn, rc, c * rs);
+            c = c2;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kCoefRun; ++j) {
+        const int64_t m = m0 + j;
+        if (m > Mh) break;
+        const double inv = 1.0 / (W * acc[j]);  // (W/2) x 2 x (sum over the positive nodes)
+        double2 X, Wt;
+        unpack(Gx, nf, m, X, Wt);
+        Fx[m] = make_double2(X.x * inv, X.y * inv);
+        if (Gy) {
+            unpack(Gy, nf, m, X, Wt);
+            Fy[m] = make_double2(X.x * inv, X.y * inv);
+        }
+    }
+}
+
+struct PaperBufs {
+    double2 *grid_x, *grid_y, *scratch, *tw, *Fx, *Fy;
+    double *d_tc, *d_gx, *d_gphi;
+    size_t used;
+};
+
+PaperBufs carve_paper(const PaperModes &pm, bool ccf, char *ws) {
+    PaperBufs b{};
+    size_t used = 0;
+    b.grid_x = take<double2>(ws, used, pm.nf);
+    b.grid_y = ccf ? take<double2>(ws, used, pm.nf) : nullptr;
+    b.scratch = take<double2>(ws, used, pm.nf);
+    b.tw = take<double2>(ws, used, pm.nf);
+    b.Fx = take<double2>(ws, used, pm.Mh + 1);
+    b.Fy = ccf ? take<double2>(ws, used, pm.Mh + 1) : nullptr;
+    b.d_tc = take<double>(ws, used, 1);
+    b.d_gx = take<double>(ws, used, pm.nq / 2);
+    b.d_gphi = take<double>(ws, used, pm.nq / 2);
+    b.used = used + 256;
+    return b;
+}
+
 }  // namespace
+
+ncf_status paper_modes_plan(double L, double tc, int64_t N1, PaperModes *pm, std::string *msg) {
+    PaperModes p;
+    p.L = L;
+    p.tc = tc;
+    p.N1 = N1;
+    p.Mh = N1 / 2;
+    p.W = 16;
+    p.beta = 2.30 * p.W;
+    p.nq = 128;
+    const int64_t need = 4 * (p.Mh + 1) + p.W;  // oversampling >= 2, as the Gaussian path
+    p.lg = 1;
+    while ((int64_t(1) << p.lg) < need) ++p.lg;
+    if (p.lg > 27) {
+        *msg = "N1 = " + std::to_string(N1) + " needs a grid above 2^27 cells";
+        return NCF_EUNSUPPORTED;
+    }
+    p.nf = 1 << p.lg;
+    std::vector<double> gw;
+    gauss_legendre(p.nq, p.gx, gw);  // nodes in decreasing order: the first nq/2 are positive
+    p.gphi.resize(p.nq);
+    for (int q = 0; q < p.nq; ++q)
+        p.gphi[q] = gw[q] * std::exp(p.beta * (std::sqrt(std::max(0.0, 1.0 - p.gx[q] * p.gx[q])) - 1.0));
+    p.poly = es_poly(p.W, p.beta, PolyDeg<16>::D);
+    *pm = std::move(p);
+    return NCF_OK;
+}
+
+size_t paper_modes_bytes(const PaperModes &pm, bool ccf) { return carve_paper(pm, ccf, nullptr).used; }
+
+size_t paper_modes_pinned_bytes(const PaperModes &pm) { return al(8) + 2 * al(pm.nq / 2 * 8); }
+
+void paper_modes_run(const PaperModes &pm, const SpecSide &x, const SpecSide *y, char *ws, char *pinned,
+                     double2 **Fx, double2 **Fy, cudaStream_t st) {
+    const bool ccf = y != nullptr;
+    PaperBufs bf = carve_paper(pm, ccf, ws);
+    size_t off = 0;
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        std::memcpy(pinned + off, src, bytes);
+        cudaMemcpyAsync(dst, pinned + off, bytes, cudaMemcpyHostToDevice, st);
+        off += al(bytes);
+    };
+    up(bf.d_tc, &pm.tc, 8);
+    up(bf.d_gx, pm.gx.data(), pm.nq / 2 * 8);
+    up(bf.d_gphi, pm.gphi.data(), pm.nq / 2 * 8);
+    constexpr size_t smem = spread_smem_bytes<double>();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(spread_kernel<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    EsPoly<double, 16, PolyDeg<16>::D> poly{};
+    for (size_t i = 0; i < pm.poly.size(); ++i) poly.c[i] = pm.poly[i];
+    const double a_scale = (double)pm.nf / pm.L;
+    auto spread = [&](const SpecSide &sd, double2 *grid) {
+        cudaMemsetAsync(grid, 0, (size_t)pm.nf * sizeof(double2), st);
+        NCF_LAUNCH("spread_kernel", st,
+                   spread_kernel<double, 16><<<(unsigned)sd.n_chunks, kSpreadThreads, smem, st>>>(
+                       sd.t, sd.v, sd.d_offs, sd.d_chunk_base, sd.d_cs, sd.d_stats, bf.d_tc, a_scale, pm.nf,
+                       poly, grid));
+    };
+    spread(x, bf.grid_x);
+    if (ccf) spread(*y, bf.grid_y);
+    NCF_LAUNCH("twiddle_kernel", st,
+               twiddle_kernel<double2><<<(pm.nf + 255) / 256, 256, 0, st>>>(bf.tw, pm.nf));
+    double2 *Gx = fft_forward_f64(bf.grid_x, bf.scratch, bf.tw, pm.lg, 1, st);
+    if (Gx == bf.scratch && ccf) {
+        cudaMemcpyAsync(bf.grid_x, bf.scratch, (size_t)pm.nf * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+        Gx = bf.grid_x;
+    }
+    double2 *Gy = ccf ? fft_forward_f64(bf.grid_y, bf.scratch, bf.tw, pm.lg, 1, st) : nullptr;
+    const int64_t threads = (pm.Mh + kCoefRun) / kCoefRun;
+    NCF_LAUNCH("paper_coef_kernel", st,
+               paper_coef_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(
+                   Gx, Gy, pm.nf, pm.Mh, pm.W, bf.d_gx, bf.d_gphi, pm.nq / 2, bf.Fx, bf.Fy));
+    *Fx = bf.Fx;
+    *Fy = bf.Fy;
+}
 
 ncf_status spectral_plan(const SpectralArgs &a, SpectralPrepared *sp, size_t *ws_bytes,
                          size_t *pinned_bytes, std::string *msg) {

@@ -68,6 +68,35 @@ void launch_contract_tc(const float *Anum, const float *Aden, const float *E, in
 void fft_twiddles_f64(double2 *tw, int lg, cudaStream_t st);
 double2 *fft_forward_f64(double2 *grid, double2 *scratch, const double2 *tw, int lg, int64_t B, cudaStream_t st);
 
+// The paper's own NUFFT estimators (Algorithms 2-4 with the smoothing step):
+// geometry of the type-1 transforms on the padded period L of Algorithm 1.
+struct PaperModes {
+    double L = 0.0, tc = 0.0;
+    int64_t N1 = 0, Mh = 0;  // coefficients m = 0 .. Mh = floor(N1 / 2)
+    int lg = 0, nf = 0, W = 16, nq = 128;
+    double beta = 0.0;
+    std::vector<double> gx, gphi, poly;
+};
+ncf_status paper_modes_plan(double L, double tc, int64_t N1, PaperModes *pm, std::string *msg);
+size_t paper_modes_bytes(const PaperModes &pm, bool ccf);
+size_t paper_modes_pinned_bytes(const PaperModes &pm);
+// F_m = sum_j x_std,j exp(+2 pi i m (t_j - t_c) / L), m = 0 .. Mh, of side x
+// (and y), by ES spreading, FFT and deconvolution; *Fx, *Fy point into ws.
+void paper_modes_run(const PaperModes &pm, const SpecSide &x, const SpecSide *y, char *ws, char *pinned,
+                     double2 **Fx, double2 **Fy, cudaStream_t st);
+
+// k_paper.cu: A_m = fac_m conj(Fa_m) Fb_m (fac 1 at m = 0 and, N1 even, at
+// m = N1/2; 2 otherwise); c[k] += sum_m Re(A_m exp(-2 pi i m tau_k / L)) with
+// phi[k] = frac(tau_k / L) 2^64 (c zeroed by the caller); the smoothing,
+// pair-count division, normalisation and unsorting of Algorithms 2-4.
+void paper_spectrum(const double2 *Fa, const double2 *Fb, int64_t Mh, int64_t N1, double2 *A, cudaStream_t st);
+void paper_eval(const double2 *A, int64_t Mh, const unsigned long long *phi, int64_t K, double *c,
+                cudaStream_t st);
+void paper_finish(const double *craw, const double *bsrt, int64_t K1, const int64_t *perm, int64_t pos0,
+                  const double *w, int nw, int o0, bool acf, const double *craw_x, const double *craw_y,
+                  int64_t nsym, const double *bx0, const double *by0, double *tmp, double *c_out,
+                  double *b_out, cudaStream_t st);
+
 // Self-test: a bounded mbarrier wait that nothing completes sets STATUS_TIMEOUT (k_tc.cu).
 void launch_bounded_wait_selftest(int *status, cudaStream_t st);
 
