@@ -257,6 +257,63 @@ def hanning_run(api, device, h=0.5):
     return out
 
 
+def paper_run(api, device, h=0.5):
+    """The paper's own NUFFT estimators (Algorithms 1-4 with the smoothing step, default N1)
+    on the seasonal OU CCF at full size (1e5 x 8e4 points, 200 lags), both kernels, beside
+    the b-hat spectral FP64 path on the same data.  Each call synchronises with the host
+    (statistics, lags, pair counts), so the events around it measure the whole call.  The
+    type-2 evaluation kernel's time comes from the context's kernel profiler; its FP64 work
+    is 6 operations per (mode, lag): a rotation (2 FMA + 2 MUL) and 2 FMA of accumulation."""
+    import math
+    import torch
+    from paper_2609_03866_b300 import synth
+    w = synth.ou_ccf()
+    dev = torch.device("cuda", device)
+    t, x, s, y, lags = (torch.from_numpy(a).to(dev) for a in (w.t, w.x, w.s, w.y, w.lags))
+    ctx = api.Context(device)
+    stream = torch.cuda.current_stream(dev)
+    span = max(w.t.max(), w.s.max()) - min(w.t.min(), w.s.min())
+    L = span + 2.0 * np.abs(np.concatenate([[0.0], w.lags])).max()
+    N1 = int(round(32.0 * max(w.t.size, w.s.size) * L / span))
+    Mh = N1 // 2
+    K1 = w.lags.size + 1
+    out = {"workload": "seasonal OU CCF, 1e5 x 8e4 points, 200 lags on [-100, 100] d", "N1": N1,
+           "unit": "ms per CCF (one call)"}
+
+    def timed(fn, reps=3):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for kernel, hh in (("gaussian", h), ("rectangle", 1.0)):
+        call = lambda: api.corr_paper(t, x, lags, kernel=kernel, h=hh, s=s, y=y, ctx=ctx, stream=stream)
+        ms = timed(call)
+        ctx.profile_reset()
+        ctx.profile(True)
+        call()
+        rep = ctx.profile_report()
+        ctx.profile(False)
+        ctx.profile_reset()
+        n_h = max(math.ceil(4 * hh) + 2, 5)
+        flops = 6.0 * (Mh + 1) * (K1 + 2 * (2 * n_h + 1))
+        ev_ms = rep.get("paper_eval_kernel", (0, float("nan")))[1]
+        out[kernel] = {"h": hh, "ms": ms, "eval_kernel_ms": ev_ms,
+                       "eval_fp64_tflops": flops / (ev_ms * 1e-3) / 1e12,
+                       "kernels_ms": {k: round(v[1], 3) for k, v in rep.items()}}
+    out["bhat_spectral_fp64_gaussian_ms"] = timed(lambda: api.corr(t, x, lags, kernel="gaussian", h=h, s=s, y=y,
+                                                                  path="spectral", precision="fp64",
+                                                                  norm="lag0", ctx=ctx, stream=stream))
+    ctx.close()
+    return out
+
+
 def serve_pool(n_pool=32, n_lo=1_000, n_hi=5_000_000, seed=11):
     """Request templates of the serving mix: half ACF light curves, half seasonal OU
     CCFs (n_B = 0.8 n_A); n log-uniform in [n_lo, n_hi]; K in {64, 256, 1024};
@@ -372,8 +429,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-serve", action="store_true",
-                    help="skip the serving, bootstrap, regular-grid and Hanning legs")
+                    help="skip the serving, bootstrap, regular-grid, Hanning and paper-NUFFT legs")
     ap.add_argument("--batch", type=int, default=B_SERIES, help="series per rank (profiling runs)")
+    ap.add_argument("--only", choices=["paper"], default=None,
+                    help="run one side leg alone and print its JSON (profiling runs)")
     args = ap.parse_args()
 
     from paper_2609_03866_b300 import shard
@@ -387,6 +446,9 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.only == "paper":
+        print(json.dumps({"paper_nufft": paper_run(api, local)}))
+        return
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
@@ -511,6 +573,7 @@ def main():
     boot = None if args.no_serve else bootstrap_run(api, local)
     regular = None if args.no_serve else regular_run(api, local)
     hanning = None if args.no_serve else hanning_run(api, local)
+    paper = None if args.no_serve else paper_run(api, local)
 
     if rank != 0:
         if world > 1:
@@ -601,6 +664,7 @@ def main():
         "bootstrap": boot,
         "regular_fft": regular,
         "hanning": hanning,
+        "paper_nufft": paper,
         "accuracy": acc,
         "cpu_baseline": cpu,
     }
