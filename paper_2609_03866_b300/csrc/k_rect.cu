@@ -337,7 +337,7 @@ struct PtSub {
 
 struct __align__(16) PtSmem {
     int4 sE[kPtCap + 1];                // {key, p0, p1, p2}; entry nK carries the sentinel key
-    uint16_t sT[kPtBins];               // byte offset into sE of the bin's first entry (16-byte aligned)
+    uint16_t sT[kPtBins];               // byte offset into sE of the bin's first entry
     int4 lc[kLagGroup];                 // lag offsets relative to vmin: dlc, dlc2, duc, duc2
     int64_t klo[kLagGroup], khi[kLagGroup];
     int64_t kdl[kLagGroup], kdu[kLagGroup];
@@ -349,7 +349,6 @@ struct __align__(16) PtSmem {
 };
 constexpr unsigned kOffE = offsetof(PtSmem, sE);
 constexpr unsigned kOffT = offsetof(PtSmem, sT);
-static_assert(kOffT % 16 == 0, "the rank table is written with 16-byte stores");
 
 __device__ __forceinline__ int4 pt_ent(const unsigned char *S, unsigned off) {
     return *reinterpret_cast<const int4 *>(S + kOffE + off);
@@ -713,37 +712,32 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                                                    (int32_t)((S0 + du + eta - base) >> sh) + 2 - vmin);
                 }
                 __syncthreads();
-                // rank table: sT[b] = 16 x (first index with key >= b << bsh); each
-                // thread merges 32 consecutive bins against the keys (the current
-                // key kept in a register) and writes them as four 16-byte stores
+                // rank table: sT[b] = 16 x (first index with key >= b << bsh), as a
+                // merge of the bins (values b << bsh) with the keys, bin b before key
+                // e iff key_e >= b << bsh.  Each thread takes an equal share of the
+                // merged sequence (merge path), so a dense stretch of keys and a
+                // long gap cost the same; entry nK is the sentinel, after every bin.
                 {
-                    constexpr int kPer = kPtBins / (kPtWarps * 32);
-                    static_assert(kPer % 8 == 0, "bins are written eight at a time");
-                    const int b0 = tid * kPer;
-                    const int32_t v0 = b0 << bsh;
-                    int lo = 0, hi = max(nK, 0);
+                    constexpr int kThreads = kPtWarps * 32;
+                    const int nE = max(nK, 0) + 1;
+                    const int total = kPtBins + nE;
+                    const int d0 = (int)(((long long)tid * total) / kThreads);
+                    const int d1 = (int)(((long long)(tid + 1) * total) / kThreads);
+                    int lo = max(0, d0 - nE), hi = min(d0, kPtBins);  // bins among the first d0
                     while (lo < hi) {
                         const int mid = (lo + hi) >> 1;
-                        if (sm.sE[mid].x < v0) lo = mid + 1; else hi = mid;
+                        if (sm.sE[d0 - 1 - mid].x >= (mid << bsh)) lo = mid + 1; else hi = mid;
                     }
-                    int p = lo;
-                    int32_t kp = sm.sE[p].x;  // entry nK holds the sentinel: every walk ends there
-                    uint4 *dst = reinterpret_cast<uint4 *>(sm.sT + b0);
-#pragma unroll
-                    for (int q = 0; q < kPer / 8; ++q) {
-                        unsigned w[4];
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            unsigned pair = 0;
-#pragma unroll
-                            for (int e = 0; e < 2; ++e) {
-                                const int32_t v = (b0 + 8 * q + 2 * r + e) << bsh;
-                                while (kp < v) kp = sm.sE[++p].x;
-                                pair |= (unsigned)(16 * p) << (16 * e);
-                            }
-                            w[r] = pair;
+                    int a = lo, e = d0 - lo;
+                    int32_t ke = sm.sE[min(e, nE - 1)].x;
+                    for (int d = d0; d < d1 && a < kPtBins; ++d) {
+                        if (ke >= (a << bsh)) {
+                            sm.sT[a] = (uint16_t)(16 * e);
+                            ++a;
+                        } else {
+                            ++e;
+                            ke = sm.sE[min(e, nE - 1)].x;
                         }
-                        dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
                     }
                 }
                 __syncthreads();
