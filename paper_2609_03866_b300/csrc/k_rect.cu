@@ -477,6 +477,12 @@ __device__ __forceinline__ void pt_lag(const unsigned char *S, const int32_t (&s
             ok[i] = kFull || (pt >= g.pa && pt < g.pb);
             s[i] = ok[i] ? sc[q0 + i] : sca;  // a point outside the segment queries in range, counts nothing
         }
+        if (!kFull) {  // a warp with no point of the segment in this batch skips it
+            bool any = false;
+#pragma unroll
+            for (int i = 0; i < kPtBatch; ++i) any |= ok[i];
+            if (!__any_sync(0xffffffffu, any)) continue;
+        }
         unsigned ol[kPtBatch], oh[kPtBatch];
         int4 el[kPtBatch], eh[kPtBatch];
 #pragma unroll
@@ -627,13 +633,41 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                         wide = x1 - lo + 1 > kPtCap / 2;
                     }
                 }
-                const bool split = __any_sync(0xffffffffu, big && !wide) && pb - pa > 32;
+                // Split point: at the widest time gap between consecutive outer points
+                // when it spans a quarter of the segment or more (a tile across a
+                // seasonal gap, whose windows at some lags cover a whole observing
+                // season), else in the middle.  Gap splits stop at 8 pending segments
+                // and middle splits at 15, so the stack of 16 never overflows.
+                const bool need = __any_sync(0xffffffffu, big && !wide);
+                int cut = -1;
+                if (need && pb - pa > 1 && n_seg < 8) {
+                    int64_t best = -1;
+                    int at = -1;
+                    for (int p = pa + lane; p + 1 < pb; p += 32) {
+                        const int64_t gp = Sy[tile.j0 + p + 1] - Sy[tile.j0 + p];
+                        if (gp > best) {
+                            best = gp;
+                            at = p;
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const int64_t b2 = __shfl_xor_sync(0xffffffffu, best, o);
+                        const int a2 = __shfl_xor_sync(0xffffffffu, at, o);
+                        if (b2 > best || (b2 == best && a2 >= 0 && (at < 0 || a2 < at))) {
+                            best = b2;
+                            at = a2;
+                        }
+                    }
+                    if (at >= 0 && 4 * best >= Sb - Sa) cut = at + 1;
+                }
+                if (cut < 0 && need && pb - pa > 32 && n_seg < 15) cut = pa + ((((pb - pa) >> 1) + 31) & ~31);
+                const bool split = cut > pa && cut < pb;
                 __syncwarp();
                 if (lane == 0) {
                     if (split) {
-                        const int mid = pa + ((((pb - pa) >> 1) + 31) & ~31);
-                        sm.seg[n_seg - 1] = make_int2(mid, pb);
-                        sm.seg[n_seg] = make_int2(pa, mid);
+                        sm.seg[n_seg - 1] = make_int2(cut, pb);
+                        sm.seg[n_seg] = make_int2(pa, cut);
                         sm.n_seg = n_seg + 1;
                         sm.n_sub = 0;
                     } else {
