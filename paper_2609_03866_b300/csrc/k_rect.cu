@@ -319,14 +319,14 @@ rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
 constexpr int kPtWarps = 8;
 constexpr int kPtM = kRectTile / (kPtWarps * 32);  // outer points per lane
 constexpr int kPtBatch = 4;                         // points of a lane handled together (load ILP)
-constexpr int kPtCap = 4000;                        // staged entries per sub-group
+constexpr int kPtCap = 5300;                        // staged entries per sub-group
 constexpr int kPtSamples = 1024;                    // planning samples of a lag group's key range
 constexpr int kPtExact = 16;                        // sample stride up to which the bounds stay coarse
 constexpr int kPtStage = 3;                         // staged entries a thread loads per round
 constexpr int kPtBinsLog = 13;
 constexpr int kPtBins = 1 << kPtBinsLog;            // rank-table bins
 static_assert(kPtBins % (kPtWarps * 32) == 0, "bins split evenly over the threads");
-static_assert(16 * (kPtCap + 1) <= 65535, "rank-table entries are 16-bit byte offsets");
+static_assert(kPtCap + 1 <= 65535, "rank-table entries are 16-bit entry indices");
 static_assert(kPtM % kPtBatch == 0, "whole batches");
 static_assert(8 * kPtSamples <= 16 * (kPtCap + 1), "planning samples fit the staging area");
 
@@ -337,7 +337,7 @@ struct PtSub {
 
 struct __align__(16) PtSmem {
     int4 sE[kPtCap + 1];                // {key, p0, p1, p2}; entry nK carries the sentinel key
-    uint16_t sT[kPtBins];               // byte offset into sE of the bin's first entry
+    uint16_t sT[kPtBins];               // index in sE of the bin's first entry
     int4 lc[kLagGroup];                 // lag offsets relative to vmin: dlc, dlc2, duc, duc2
     int64_t klo[kLagGroup], khi[kLagGroup];
     int64_t kdl[kLagGroup], kdu[kLagGroup];
@@ -349,12 +349,14 @@ struct __align__(16) PtSmem {
 };
 constexpr unsigned kOffE = offsetof(PtSmem, sE);
 constexpr unsigned kOffT = offsetof(PtSmem, sT);
+// two CTAs per SM: 228 KB of shared memory, 1 KB of it reserved per CTA
+static_assert(2 * (sizeof(PtSmem) + 1024) <= 228 * 1024, "two CTAs per SM");
 
 __device__ __forceinline__ int4 pt_ent(const unsigned char *S, unsigned off) {
     return *reinterpret_cast<const int4 *>(S + kOffE + off);
 }
 __device__ __forceinline__ unsigned pt_bin(const unsigned char *S, int32_t v, int bsh) {
-    return *reinterpret_cast<const uint16_t *>(S + kOffT + 2u * (unsigned)(v >> bsh));
+    return (unsigned)*reinterpret_cast<const uint16_t *>(S + kOffT + 2u * (unsigned)(v >> bsh)) << 4;
 }
 
 // Bounds of lower_bound(Tx, ia, ib, v) from the planning samples samp[m] =
@@ -746,7 +748,7 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                                                    (int32_t)((S0 + du + eta - base) >> sh) + 2 - vmin);
                 }
                 __syncthreads();
-                // rank table: sT[b] = 16 x (first index with key >= b << bsh), as a
+                // rank table: sT[b] = the first index with key >= b << bsh, as a
                 // merge of the bins (values b << bsh) with the keys, bin b before key
                 // e iff key_e >= b << bsh.  Each thread takes an equal share of the
                 // merged sequence (merge path), so a dense stretch of keys and a
@@ -766,7 +768,7 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                     int32_t ke = sm.sE[min(e, nE - 1)].x;
                     for (int d = d0; d < d1 && a < kPtBins; ++d) {
                         if (ke >= (a << bsh)) {
-                            sm.sT[a] = (uint16_t)(16 * e);
+                            sm.sT[a] = (uint16_t)e;
                             ++a;
                         } else {
                             ++e;
