@@ -3,9 +3,11 @@ pair counts and numerators, equal to the FP64 oracle (Algorithms 6 and 8).
 
 Variants 0-2 put lags on lanes (runs of 16 / 32 / 64 outer points); variant 3
 puts outer points on lanes with a rank table, splits a lag group into
-sub-groups when its key union does not fit shared memory, and runs a lag
-whose union alone does not fit on the global keys.  The cases below reach
-each of those branches.
+sub-groups when its key union does not fit shared memory, splits the outer
+points of a tile (at its widest time gap, else in the middle) when one lag's
+union does not fit, and runs a lag on the global keys when a single outer
+point's window fills half the staging area.  The cases below reach each of
+those branches.
 """
 import os
 
@@ -53,9 +55,10 @@ def test_dense_light_curves_lag_subgroups():
         assert max_abs(got["c"][b, ks], ref["c"]) < 1e-10
 
 
-def test_sparse_outer_dense_inner_ccf_global_path():
+def test_sparse_outer_dense_inner_ccf_middle_splits():
     """CCF whose outer series is sparse over a long span and inner series dense:
-    a single lag's union exceeds the staging area (global-key branch)."""
+    a single lag's union exceeds the staging area and the tile, with no
+    dominant gap, is split in the middle down to small segments."""
     rng = np.random.default_rng(2)
     t = np.sort(rng.uniform(0, 3000, 150_000))
     x = rng.normal(size=t.size)
@@ -64,6 +67,37 @@ def test_sparse_outer_dense_inner_ccf_global_path():
     lags = np.linspace(-40, 40, 37)
     got = all_variants(lambda: api.corr(t, x, lags, kernel="rectangle", h=0.75, s=s, y=y))
     ref = oracle.corr(t, x, lags, "rectangle", 0.75, s=s, y=y, method="windowed")
+    assert np.array_equal(got["count"], ref["count"])
+    assert max_abs(got["c"], ref["c"]) < 1e-10
+
+
+def test_dense_seasons_across_a_gap_split_at_the_gap():
+    """Two dense observing seasons 120 days apart: the tile holding the season
+    boundary spans the gap, and at lags that carry its windows into the other
+    season one lag's union far exceeds the staging area; the split falls at the
+    gap.  Counts are exact and equal the oracle's at every lag."""
+    rng = np.random.default_rng(21)
+    nights = np.concatenate([np.arange(0, 60), np.arange(180, 240)]).astype(np.float64)
+    t = np.sort((nights[:, None] + rng.uniform(0.0, 0.3, (nights.size, 200))).ravel())
+    x = np.sin(t / 7.0) + rng.normal(size=t.size)
+    lags = np.linspace(0.0, 200.0, 64)
+    got = all_variants(lambda: api.corr(t, x, lags, kernel="rectangle", h=0.5))
+    ref = oracle.corr(t, x, lags, "rectangle", 0.5, method="windowed")
+    assert np.array_equal(got["count"], ref["count"])
+    assert max_abs(got["c"], ref["c"]) < 1e-10
+
+
+def test_wide_windows_global_path():
+    """A window of 2h = 40 days over 100 points a day holds 4000 keys, more than
+    half the staging area: such lags run on the global keys."""
+    rng = np.random.default_rng(22)
+    t = np.sort(rng.uniform(0.0, 400.0, 40_000))
+    x = rng.normal(size=t.size)
+    s = np.sort(rng.uniform(0.0, 400.0, 3000))
+    y = rng.normal(size=s.size)
+    lags = np.linspace(-50.0, 50.0, 21)
+    got = all_variants(lambda: api.corr(t, x, lags, kernel="rectangle", h=20.0, s=s, y=y))
+    ref = oracle.corr(t, x, lags, "rectangle", 20.0, s=s, y=y, method="windowed")
     assert np.array_equal(got["count"], ref["count"])
     assert max_abs(got["c"], ref["c"]) < 1e-10
 
