@@ -8,7 +8,8 @@
 // the window pointers only advance (the window centre s_j + e*tau grows with
 // j).  Each warp reduces its lane sums and adds them to the per-(series, lag)
 // accumulators with FP64 atomics.  This is the plain FP64 path for the
-// Gaussian kernel: one FP64 exp per pair inside the window [c - R h, c + R h).
+// Gaussian kernel: one FP64 exponential per pair inside the window
+// [c - R h, c + R h), by a table-driven method for non-positive arguments.
 #include <cmath>
 #include <cstdint>
 
@@ -28,6 +29,29 @@ __device__ __forceinline__ double centre(double s, double tau, int eps) {
 
 constexpr double kInvSqrt2Pi = 0.398942280401432677939946059934381868;
 
+// exp(z) for z <= 0 by Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2),
+// 1989): z = (64 m + j) ln2/64 + r with |r| <= ln2/128, so exp(z) = 2^m 2^(j/64) e^r.
+// ln2/64 = L1 + L2, L1 with 32 significant bits (N L1 exact for |N| < 2^21);
+// e^r - 1 by its Taylor polynomial of degree 5 (remainder below 4e-17); the
+// table 2^(j/64) is filled per CTA from exp2.  About 10 FP64 operations against
+// the two dozen of a general exp; the Gaussian weights need only z <= 0.
+constexpr double kExpInvL = 92.33248261689366;         // 64 / ln 2
+constexpr double kExpL1 = 0x1.62e42fee00000p-7;        // ln2/64, upper 32 bits
+constexpr double kExpL2 = 0x1.a39ef35793c76p-39;       // ln2/64 - L1
+__device__ __forceinline__ double exp_neg(double z, const double *__restrict__ T) {
+    if (z < -708.0) return 0.0;  // below the normal range: weight 0
+    const double nd = fma(z, kExpInvL, 0x1.8p52);       // N in the low bits
+    const int n = (int)__double2loint(nd);
+    const double N = nd - 0x1.8p52;
+    double r = fma(-N, kExpL1, z);
+    r = fma(-N, kExpL2, r);
+    const double p = r * fma(r, fma(r, fma(r, fma(r, 0x1.1111111111111p-7, 0x1.5555555555555p-5),
+                                            0x1.5555555555555p-3), 0.5), 1.0);
+    const double t = T[n & 63];
+    const double v = fma(t, p, t);
+    return v * __longlong_as_double((long long)((n >> 6) + 1023) << 52);
+}
+
 __global__ void __launch_bounds__(kWarps * 32)
 gauss_window_kernel(const double *__restrict__ tx, const double *__restrict__ x,
                     const int64_t *__restrict__ offs_x, const SeriesStats *__restrict__ stx,
@@ -36,6 +60,9 @@ gauss_window_kernel(const double *__restrict__ tx, const double *__restrict__ x,
                     const double *__restrict__ lags, int64_t K, int eps, double h, double Rh, int hann,
                     double *__restrict__ num, double *__restrict__ den,
                     unsigned long long *__restrict__ cnt) {
+    __shared__ double T2[64];  // 2^(j/64) for exp_neg
+    if (threadIdx.x < 64) T2[threadIdx.x] = exp2((double)threadIdx.x / 64.0);
+    __syncthreads();
     const ScanTile tile = tiles[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t k = (int64_t)blockIdx.y * kWarps + warp;
@@ -89,7 +116,7 @@ gauss_window_kernel(const double *__restrict__ tx, const double *__restrict__ x,
                     const double cw = cospi(d * inv2h);
                     w = cw * cw;
                 } else {
-                    w = exp(-d * d * inv2h2);
+                    w = exp_neg(-d * d * inv2h2, T2);
                 }
                 bj += w;
                 nj = fma(w, (x[i] - mx) * ix, nj);
