@@ -232,7 +232,9 @@ def regular_run(api, device, n=256_000, K=366, h=1.0):
 
 def hanning_run(api, device, h=0.5):
     """Hanning kernel (FP64 windowed path) on the seasonal OU CCF at full size
-    (1e5 x 8e4 points, 200 lags), beside the exact rectangle scan on the same data."""
+    (1e5 x 8e4 points, 200 lags), beside the exact rectangle scan on the same data,
+    and the spectral-sinc rectangle (FP64 spectral path, tol 1e-2) with its error
+    against that exact scan."""
     import torch
     from paper_2609_03866_b300 import synth
     w = synth.ou_ccf()
@@ -252,6 +254,24 @@ def hanning_run(api, device, h=0.5):
         e1.record(stream)
         torch.cuda.synchronize()
         out[kernel + "_ms"] = e0.elapsed_time(e1) / 5
+    # the spectral-sinc rectangle on the same data, against the exact scan's result
+    exact = api.corr(t, x, lags, kernel="rectangle", h=h, s=s, y=y, ctx=ctx, stream=stream)["c"]
+    sinc_tol = 1e-2
+    sinc = lambda: api.corr(t, x, lags, kernel="rectangle", h=h, s=s, y=y, path="spectral", tol=sinc_tol,
+                            ctx=ctx, stream=stream)
+    approx = sinc()["c"]
+    torch.cuda.synchronize()
+    for _ in range(2):
+        sinc()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        sinc()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["spectral_sinc"] = {"tol": sinc_tol, "ms": e0.elapsed_time(e1) / 3,
+                            "max_abs_err_vs_exact_scan": float((approx - exact).abs().max())}
     ctx.close()
     out.update({"workload": "seasonal OU CCF, 1e5 x 8e4 points, 200 lags on [-100, 100] d, h = 0.5 d"})
     return out
@@ -431,7 +451,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the serving, bootstrap, regular-grid, Hanning and paper-NUFFT legs")
     ap.add_argument("--batch", type=int, default=B_SERIES, help="series per rank (profiling runs)")
-    ap.add_argument("--only", choices=["paper"], default=None,
+    ap.add_argument("--only", choices=["paper", "hanning"], default=None,
                     help="run one side leg alone and print its JSON (profiling runs)")
     args = ap.parse_args()
 
@@ -448,6 +468,9 @@ def main():
     dev = torch.device("cuda", local)
     if args.only == "paper":
         print(json.dumps({"paper_nufft": paper_run(api, local)}))
+        return
+    if args.only == "hanning":
+        print(json.dumps({"hanning": hanning_run(api, local)}))
         return
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)

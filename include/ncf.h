@@ -25,9 +25,14 @@
  *   NCF_PATH_SPECTRAL  Wiener-Khinchin (Sec. 2.6): type-1 NUFFT of the values
  *                      and of unit weights onto a uniform grid, FFT, cross-
  *                      spectrum times the kernel's Fourier transform, sum of
- *                      the modes at the K lags.  Gaussian kernel only (the
- *                      rectangle's transform decays too slowly for a tight
- *                      tolerance, so the rectangle always uses the exact scan).
+ *                      the modes at the K lags.  For the rectangle this is the
+ *                      spectral-sinc variant, taken only when asked for: its
+ *                      transform sin(2 pi f h)/(pi f) decays as 1/f, so the sum
+ *                      over |m| <= L/(h tol) modes (tol default 1e-3) carries
+ *                      an error of order tol of a pair's weight near the window
+ *                      edges (reported by the tests, not gated); count_out is 0.
+ *                      It keeps a mode-by-lag table, so it suits single series
+ *                      and moderate L/(h tol) (NCF_ENOMEM otherwise).
  *   NCF_PATH_WINDOWED  the two-pointer real-space scan (Algorithms 5-8).
  *   NCF_PATH_AUTO      spectral for the Gaussian, windowed for the rectangle.
  *
@@ -100,7 +105,9 @@ typedef struct {
     double trunc_R;     /* Gaussian windowed path: window [c - R h, c + R h) as in
                            Algorithm 5 with 6 replaced by R; 0 selects 8 */
     double tol;         /* spectral path tolerance on the kernel transform and the
-                           spreading; 0 selects 1e-14 (FP64) or 1e-7 (FP32) */
+                           spreading; 0 selects 1e-14 (FP64) or 1e-7 (FP32), and
+                           1e-3 for the spectral-sinc rectangle (its mode count
+                           L / (h tol)) */
 } ncf_options;
 
 /* Fills *o with: Gaussian, AUTO path, FP64, NORM_NONE, h = 1, trunc_R = 0, tol = 0. */

@@ -283,10 +283,6 @@ ncf_status check_args(ncf_ctx *ctx, const int64_t *offs_x, const double *t, cons
     if (rc) return rc;
     if (!acf && (rc = check_offsets(ctx, offs_y, B, "offs_y"))) return rc;
     int path = opt->path;
-    if (opt->kernel == NCF_RECTANGLE && path == NCF_PATH_SPECTRAL)
-        return fail(ctx, NCF_EUNSUPPORTED,
-                    "rectangle kernel: only the exact windowed scan is provided (its transform "
-                    "decays as 1/f, so a truncated spectrum cannot meet the tolerance)");
     if (opt->kernel == NCF_GAUSSIAN && path == NCF_PATH_WINDOWED && opt->precision == NCF_FP32)
         return fail(ctx, NCF_EUNSUPPORTED, "the windowed Gaussian path is FP64 only");
     if (opt->kernel == NCF_HANNING && (path == NCF_PATH_SPECTRAL || opt->precision == NCF_FP32))
@@ -307,6 +303,9 @@ ncf_status check_args(ncf_ctx *ctx, const int64_t *offs_x, const double *t, cons
     if (!acf) plan_side(ev.Y, offs_y, B);
     return NCF_OK;
 }
+
+// The rectangle runs on the exact scan unless the spectral-sinc variant was asked for.
+bool rect_scan(const Eval &ev) { return ev.opt.kernel == NCF_RECTANGLE && ev.path != NCF_PATH_SPECTRAL; }
 
 size_t pre_bytes(const Eval &ev) {
     auto side = [&](const Side &sd) {
@@ -404,7 +403,11 @@ SpectralArgs spectral_args(const Eval &ev, double *c_out, double *b_out, int64_t
     sa.K = ev.K;
     sa.h = ev.opt.h;
     sa.fp32 = ev.opt.precision == NCF_FP32;
-    sa.tol = ev.opt.tol > 0.0 ? ev.opt.tol : (sa.fp32 ? 1e-7 : 1e-14);
+    sa.kernel = ev.opt.kernel == NCF_RECTANGLE ? 1 : 0;
+    if (sa.kernel == 1)
+        sa.tol = ev.opt.tol > 0.0 ? ev.opt.tol : 1e-3;  // the spectral-sinc truncation
+    else
+        sa.tol = ev.opt.tol > 0.0 ? ev.opt.tol : (sa.fp32 ? 1e-7 : 1e-14);
     sa.max_tau = ev.max_tau;
     sa.lag0 = ev.lag0;
     sa.h_lags = ev.lagv.data();
@@ -427,7 +430,7 @@ size_t key_bytes(const Side &sd) {
 // Sizes of the path-specific device memory and of its host staging.
 ncf_status main_bytes(ncf_ctx *ctx, Eval &ev, size_t *dev, size_t *pin) {
     const int64_t B = ev.B, K = ev.K;
-    if (ev.opt.kernel == NCF_RECTANGLE) {
+    if (rect_scan(ev)) {
         const Side &O = ev.outer();
         const size_t rw = rect_workspace_bytes(rect_tiles_of(O.offs, B), K);
         const size_t rwx = ev.lag0 ? rect_workspace_bytes(rect_tiles_of(ev.X.offs, B), 1) : 0;
@@ -469,7 +472,7 @@ ncf_status prepare(ncf_ctx *ctx, Eval &ev, char *mem, size_t cap, char *pinned, 
     if (!d_lags) return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
     NCF_CUDA(cudaMemcpyAsync(d_lags, lags, K * 8, cudaMemcpyDeviceToDevice, st));
     ev.d_lags = d_lags;
-    if (ev.opt.kernel == NCF_RECTANGLE) {
+    if (rect_scan(ev)) {
         Side &X = ev.X, &O = ev.outer();
         ev.fs = choose_scales(ev.t_abs + ev.max_tau + ev.opt.h + 1.0, std::max(X.n_max, O.n_max));
         auto keys = [&](const Side &sd, int64_t *&T, int64_t *&Xq, int64_t *&P, int64_t *&C) {
@@ -573,7 +576,7 @@ ncf_status launch(ncf_ctx *ctx, Eval &ev, bool stats_fresh, bool guard, double *
     if (!stats_fresh) run_stats(ev, st);
     if (guard) launch_stats_guard(ev.X.d_stats, ev.acf ? nullptr : ev.Y.d_stats, B, ev.status, st);
     Side &X = ev.X, &O = ev.outer();
-    if (ev.opt.kernel == NCF_RECTANGLE) {
+    if (rect_scan(ev)) {
         launch_keys_prefix(X.t, X.v, X.d_offs, X.d_chunk_base, X.d_cs, X.n_chunks, kPrepChunk, X.d_stats, ev.fs,
                            ev.kxT, ev.kxX, ev.kxP, ev.kxC, X.n_total, st);
         if (!ev.acf)
@@ -772,7 +775,7 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
     if ((rc = grow_pinned(ctx, pin, st))) return rc;
     if ((rc = prepare(ctx, ev, ctx->ws2, ctx->ws2_cap, ctx->pinned, ctx->pinned_cap, lags, st))) return rc;
     NCF_CUDA(cudaEventRecord(ctx->staged, st));
-    if (ev.opt.kernel == NCF_RECTANGLE && (rc = tune_rect(ctx, ev, st))) return rc;
+    if (rect_scan(ev) && (rc = tune_rect(ctx, ev, st))) return rc;
     return launch(ctx, ev, /*stats_fresh=*/true, /*guard=*/false, c_out, b_out, count_out, st);
 }
 
@@ -1370,7 +1373,7 @@ ncf_status ncf_plan_create(ncf_ctx *ctx, const int64_t *offs_x, const double *t,
     }
     if ((rc = grow_pinned(ctx, pin, st))) return bail(rc);
     if ((rc = prepare(ctx, ev, p->main, dev, ctx->pinned, ctx->pinned_cap, lags, st))) return bail(rc);
-    if (ev.opt.kernel == NCF_RECTANGLE && (rc = tune_rect(ctx, ev, st))) return bail(rc);
+    if (rect_scan(ev) && (rc = tune_rect(ctx, ev, st))) return bail(rc);
     if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(ctx, NCF_ECUDA, "plan set-up failed"));
     *out = p;
     return NCF_OK;

@@ -126,11 +126,14 @@ template <> struct PolyDeg<16> { static constexpr int D = 14; };
 // ---------------------------------------------------------------------------
 
 // Per-mode weight of the spectra, folding the deconvolution (1 / phihat_m^2),
-// the Gaussian transform bhat(m/L), the 1/L of the Fourier series and the
+// the kernel's transform bhat(m/L), the 1/L of the Fourier series and the
 // factor 2 of the +-m pair:  wgt_m = fac_m bhat(m/L) / (L phihat_m^2).
+// Gaussian (unit mass): bhat(f) = exp(-2 pi^2 h^2 f^2).  Rectangle (a pair
+// counts 1 inside |d| <= h): bhat(f) = sin(2 pi f h) / (pi f), 2h at f = 0; its
+// 1/f tail makes the truncated sum an approximation (the spectral-sinc variant).
 // phihat_m = (w/2) int_{-1}^{1} phi(z) cos(pi m w z / n_f) dz by quadrature.
 __global__ void mode_weight_kernel(const double *__restrict__ gx, const double *__restrict__ gphi,
-                                   int nq, int64_t M, int64_t Mp, int W, int nf, double L, double h,
+                                   int nq, int64_t M, int64_t Mp, int W, int nf, double L, double h, int rect,
                                    double *__restrict__ wgt64, float *__restrict__ wgt32) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= Mp) return;
@@ -141,7 +144,8 @@ __global__ void mode_weight_kernel(const double *__restrict__ gx, const double *
         for (int q = 0; q < nq; ++q) s += gphi[q] * cospi(a * gx[q]);
         const double ph = 0.5 * W * s;
         const double f = (double)m / L;
-        const double bhat = exp(-2.0 * kPi * kPi * h * h * f * f);
+        const double bhat = rect ? (m == 0 ? 2.0 * h : sinpi(2.0 * f * h) / (kPi * f))
+                                 : exp(-2.0 * kPi * kPi * h * h * f * f);
         out = (m == 0 ? 1.0 : 2.0) * bhat / (L * ph * ph);
     }
     if (wgt64) wgt64[m] = out;
@@ -613,11 +617,20 @@ T *take(char *base, size_t &used, size_t count) {
 
 void make_plan(const SpectralArgs &a, double max_span, SpectralPrepared &p) {
     const double tol = a.tol;
-    p.R_alias = std::sqrt(2.0 * std::log(1.0 / (tol * 1e-2)));
-    p.L = max_span + a.max_tau + p.R_alias * a.h;
-    const double delta = tol * 1e-3;
-    const double mscale = std::sqrt(std::log(1.0 / delta) / (2.0 * kPi * kPi));
-    p.M = (int64_t)std::ceil(p.L * mscale / a.h) + 1;
+    if (a.kernel == 1) {
+        // spectral-sinc rectangle: compact support (alias margin 2h); the sum
+        // keeps |m| <= L / (h tol), so the truncated kernel's error near a
+        // window edge is of order L / (M h) = tol of a pair's weight
+        p.R_alias = 2.0;
+        p.L = max_span + a.max_tau + p.R_alias * a.h;
+        p.M = (int64_t)std::ceil(p.L / (a.h * tol)) + 1;
+    } else {
+        p.R_alias = std::sqrt(2.0 * std::log(1.0 / (tol * 1e-2)));
+        p.L = max_span + a.max_tau + p.R_alias * a.h;
+        const double delta = tol * 1e-3;
+        const double mscale = std::sqrt(std::log(1.0 / delta) / (2.0 * kPi * kPi));
+        p.M = (int64_t)std::ceil(p.L * mscale / a.h) + 1;
+    }
     p.Mp = (p.M + 31) / 32 * 32;
     p.W = a.fp32 ? 8 : 16;
     p.beta = 2.30 * p.W;
@@ -630,6 +643,7 @@ void make_plan(const SpectralArgs &a, double max_span, SpectralPrepared &p) {
     p.Kp = (p.K1 + 3) / 4 * 4;
     p.M2 = a.acf ? p.Mp : 2 * p.Mp;
     p.fp32 = a.fp32;
+    p.kernel = a.kernel;
     p.acf = a.acf;
     p.lag0 = a.lag0;
     p.B = a.B;
@@ -697,7 +711,7 @@ void prepare_typed(const SpectralPrepared &p, char *ws, const double *h_tc,
     up(bf.d_gphi, gphi.data(), p.nq * 8);
     NCF_LAUNCH("mode_weight_kernel", st,
                mode_weight_kernel<<<(unsigned)((p.Mp + 255) / 256), 256, 0, st>>>(
-                   bf.d_gx, bf.d_gphi, p.nq, p.M, p.Mp, p.W, p.nf, p.L, p.h, bf.wgt64,
+                   bf.d_gx, bf.d_gphi, p.nq, p.M, p.Mp, p.W, p.nf, p.L, p.h, p.kernel == 1, bf.wgt64,
                    std::is_same<R, float>::value ? reinterpret_cast<float *>(bf.wgt) : nullptr));
     if (std::is_same<R, double>::value)
         cudaMemcpyAsync(bf.wgt, bf.wgt64, p.Mp * 8, cudaMemcpyDeviceToDevice, st);

@@ -75,7 +75,8 @@ size_t estimate_bytes(const ncf_request &r, const Resident *rx, const Resident *
     const double copied = (double)(rx ? 0 : nx) + (double)(ry ? 0 : ny);
     const double K = (double)r.K;
     double bytes = 16.0 * copied + 32.0 * K + 64.0 * n + 4096.0;  // inputs, outputs, statistics, keys, tables
-    const bool spectral = r.opt.kernel == NCF_GAUSSIAN && r.opt.path != NCF_PATH_WINDOWED;
+    const bool sinc = r.opt.kernel == NCF_RECTANGLE && r.opt.path == NCF_PATH_SPECTRAL;
+    const bool spectral = (r.opt.kernel == NCF_GAUSSIAN && r.opt.path != NCF_PATH_WINDOWED) || sinc;
     if (spectral) {
         double lo = rx ? rx->t_first : r.t[0], hi = rx ? rx->t_last : r.t[nx - 1];
         if (!acf) {
@@ -87,7 +88,9 @@ size_t estimate_bytes(const ncf_request &r, const Resident *rx, const Resident *
         const bool fp32 = r.opt.precision == NCF_FP32;
         const double h = r.opt.h > 0.0 ? r.opt.h : 1.0;
         const double L = (hi - lo) + max_tau + 9.0 * h;
-        const double M = L * (fp32 ? 1.09 : 1.41) / h + 32.0;
+        // the spectral-sinc rectangle keeps L / (h tol) modes
+        const double M = sinc ? L / (h * (r.opt.tol > 0.0 ? r.opt.tol : 1e-3)) + 32.0
+                              : L * (fp32 ? 1.09 : 1.41) / h + 32.0;
         double nf = 16.0;
         while (nf < 4.0 * M + 16.0) nf *= 2.0;
         const double cell = fp32 ? 8.0 : 16.0, real = fp32 ? 4.0 : 8.0;

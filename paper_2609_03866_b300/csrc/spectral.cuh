@@ -22,6 +22,7 @@ struct SpecSide {
 
 struct SpectralArgs {
     bool acf = true, fp32 = false, lag0 = false;
+    int kernel = 0;  // NCF_GAUSSIAN (b-hat Gaussian) or NCF_RECTANGLE (the spectral-sinc variant)
     int64_t B = 0, K = 0;
     double h = 1.0, tol = 1e-14, max_tau = 0.0;
     const double *lags = nullptr;    // device [K]
@@ -39,6 +40,7 @@ struct SpectralPrepared {
     int64_t M = 0, Mp = 0, K1 = 0, Kp = 0, M2 = 0, B = 0, K = 0;
     int nf = 0, lg = 0, W = 8, nq = 64;
     bool fp32 = false, acf = true, lag0 = false;
+    int kernel = 0;
     std::vector<double> tc, gx, gphi, poly;
     std::vector<unsigned long long> phi;
 };

@@ -144,7 +144,7 @@ def test_invalid_inputs_are_rejected_before_any_launch():
         api.corr(t, x, lags, h=0.0)
     assert e.value.name == "NCF_EINVAL"
     with pytest.raises(api.NcfError) as e:
-        api.corr(t, x, lags, kernel="rectangle", path="spectral")
+        api.corr(t, x, lags, kernel="hanning", path="spectral")
     assert e.value.name == "NCF_EUNSUPPORTED"
     # a valid call still works afterwards
     r = gpu(t, x, lags, kernel="rectangle", h=0.5)
