@@ -291,7 +291,7 @@ rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
 
 // ---------------------------------------------------------------------------
 // Points-on-lanes scan.  Lane l of warp w owns the outer points
-// w*256 + l + 32 q (q < 8) of the tile, so at every step the 32 lanes of a warp
+// (q 8 + w) 32 + l (q < 8) of the tile, so at every step the 32 lanes of a warp
 // hold 32 consecutive outer points: their window edges sit at neighbouring
 // positions of the staged keys (conflict-free shared-memory access) and the
 // loop over the lags of the group is warp-uniform.  A window edge is found in
@@ -318,6 +318,10 @@ rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
 // ---------------------------------------------------------------------------
 constexpr int kPtWarps = 8;
 constexpr int kPtM = kRectTile / (kPtWarps * 32);  // outer points per lane
+// Lane l of warp w owns points (q kPtWarps + w) 32 + l, q < kPtM: each warp's
+// groups of 32 consecutive points are spread over the whole tile, so dense and
+// sparse stretches of a tile fall evenly on the warps.
+constexpr int kPtStride = kPtWarps * 32;
 constexpr int kPtBatch = 4;                         // points of a lane handled together (load ILP)
 constexpr int kPtCap = 5300;                        // staged entries per sub-group
 constexpr int kPtSamples = 1024;                    // planning samples of a lag group's key range
@@ -475,7 +479,7 @@ __device__ __forceinline__ void pt_lag(const unsigned char *S, const int32_t (&s
         bool ok[kPtBatch];
 #pragma unroll
         for (int i = 0; i < kPtBatch; ++i) {
-            const int pt = pbase + 32 * (q0 + i);
+            const int pt = pbase + kPtStride * (q0 + i);
             ok[i] = kFull || (pt >= g.pa && pt < g.pb);
             s[i] = ok[i] ? sc[q0 + i] : sca;  // a point outside the segment queries in range, counts nothing
         }
@@ -511,7 +515,7 @@ __device__ __forceinline__ void pt_lag(const unsigned char *S, const int32_t (&s
                 const bool fl = el[i].x < s[i] + L.y, fh = eh[i].x < s[i] + L.w;
                 if (ok[i] && (fl || fh)) {
                     const int2 r = pt_band(g.Tx, g.tx, g.Sy, g.sy, g.dls, g.dus, g.slags,
-                                           g.j0 + pbase + 32 * (q0 + i), g.k, g.eps, g.h, g.eta, g.ia_s, g.lim,
+                                           g.j0 + pbase + kPtStride * (q0 + i), g.k, g.eps, g.h, g.eta, g.ia_s, g.lim,
                                            (int)(ol[i] >> 4), (int)(oh[i] >> 4), fl, fh);
                     ol[i] = 16u * (unsigned)r.x;
                     oh[i] = 16u * (unsigned)r.y;
@@ -566,10 +570,10 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
     }
     // this lane's outer points: coarse offsets and the two limbs of Y
     int32_t sc[kPtM], y0[kPtM], y1[kPtM];
-    const int pbase = warp * 32 * kPtM + lane;
+    const int pbase = warp * 32 + lane;
 #pragma unroll
     for (int q = 0; q < kPtM; ++q) {
-        const int pt = pbase + 32 * q;
+        const int pt = pbase + kPtStride * q;
         const int64_t Y = pt < tn ? Yq[tile.j0 + pt] : 0;
         sc[q] = pt < tn ? (int32_t)((Sy[tile.j0 + pt] - S0) >> sh) : 0;
         y0[q] = (int32_t)(Y & 0x7fffffffll);
@@ -805,7 +809,7 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                     unsigned int c = 0;
                     U128 acc{0ull, 0ull};
                     for (int q = 0; q < kPtM; ++q) {
-                        const int pt = pbase + 32 * q;
+                        const int pt = pbase + kPtStride * q;
                         if (pt < pa || pt >= pb) continue;
                         const int64_t j = tile.j0 + pt;
                         const int64_t Lf = Sy[j] + dl, Uf = Sy[j] + du;
