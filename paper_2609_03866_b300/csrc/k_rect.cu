@@ -326,7 +326,6 @@ constexpr int kPtBatch = 4;                         // points of a lane handled 
 constexpr int kPtCap = 5300;                        // staged entries per sub-group
 constexpr int kPtSamples = 1024;                    // planning samples of a lag group's key range
 constexpr int kPtExact = 16;                        // sample stride up to which the bounds stay coarse
-constexpr int kPtStage = 3;                         // staged entries a thread loads per round
 constexpr int kPtBinsLog = 13;
 constexpr int kPtBins = 1 << kPtBinsLog;            // rank-table bins
 static_assert(kPtBins % (kPtWarps * 32) == 0, "bins split evenly over the threads");
@@ -720,28 +719,29 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                 const int32_t vmax = scb + (int32_t)((S0 + sb.dmax + eta - base) >> sh) + 2;
                 const int vbits = 32 - __clz(max(vmax - vmin, 1));
                 const int bsh = max(0, vbits - kPtBinsLog);
-                // entries 0 .. nK: keys (nK: the sentinel) and the limbs of P[ia + i];
-                // each thread issues the loads of kPtStage entries before any store
-                for (int i0 = tid; i0 <= max(nK, 0); i0 += kPtStage * blockDim.x) {
-                    int64_t tv[kPtStage], pv[kPtStage];
-#pragma unroll
-                    for (int u = 0; u < kPtStage; ++u) {
-                        const int i = i0 + u * blockDim.x;
-                        tv[u] = i < nK ? Tx[sb.ia + i] : 0;
-                        pv[u] = i <= nK ? P[sb.ia + i] : 0;
+                // entries 0 .. nK: keys (nK: the sentinel) and the limbs of P[ia + i].
+                // Tx and P of entry i are copied asynchronously into its own 16-byte
+                // slot (all copies in flight at once), then each thread rewrites its
+                // own slots in place as {key, p0, p1, p2}.
+                for (int i = tid; i <= max(nK, 0); i += blockDim.x) {
+                    const unsigned slot = (unsigned)__cvta_generic_to_shared(&sm.sE[i]);
+                    if (i < nK)
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(slot), "l"(Tx + sb.ia + i)
+                                     : "memory");
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(slot + 8u), "l"(P + sb.ia + i)
+                                 : "memory");
+                }
+                asm volatile("cp.async.wait_all;" ::: "memory");
+                for (int i = tid; i <= max(nK, 0); i += blockDim.x) {
+                    const longlong2 raw = *reinterpret_cast<const longlong2 *>(&sm.sE[i]);
+                    int32_t key = kSentinel;
+                    if (i < nK) {
+                        const int64_t v = ((raw.x - base) >> sh) - vmin;
+                        key = (int32_t)max(min(v, (int64_t)(1 << 30)), (int64_t)-1);
                     }
-#pragma unroll
-                    for (int u = 0; u < kPtStage; ++u) {
-                        const int i = i0 + u * blockDim.x;
-                        if (i > nK) break;
-                        int32_t key = kSentinel;
-                        if (i < nK) {
-                            const int64_t v = ((tv[u] - base) >> sh) - vmin;
-                            key = (int32_t)max(min(v, (int64_t)(1 << 30)), (int64_t)-1);
-                        }
-                        sm.sE[i] = make_int4(key, (int32_t)(pv[u] & 0x1fffff),
-                                             (int32_t)((pv[u] >> 21) & 0x1fffff), (int32_t)(pv[u] >> 42));
-                    }
+                    const int64_t pv = raw.y;
+                    sm.sE[i] = make_int4(key, (int32_t)(pv & 0x1fffff), (int32_t)((pv >> 21) & 0x1fffff),
+                                         (int32_t)(pv >> 42));
                 }
                 if (tid < sb.kb - sb.ka) {
                     const int k = (int)k0 + sb.ka + tid;
