@@ -58,12 +58,14 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms, logged to
+    $NCF_CLOCKS_DIR/clocks_gpu<index>.csv (default: the system temporary directory)."""
 
     def __init__(self, index: int):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+        self.path = os.path.join(os.environ.get("NCF_CLOCKS_DIR", tempfile.gettempdir()), f"clocks_gpu{index}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
