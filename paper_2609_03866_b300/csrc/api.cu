@@ -790,6 +790,8 @@ static unsigned long long lag_phase(double tau, double L) {
     return hi + (unsigned long long)lo;
 }
 
+constexpr int64_t kPaperType2Lags = 48;
+
 static ncf_status corr_paper_impl(ncf_ctx *ctx, const double *t, const double *x, int64_t nx, const double *s,
                                   const double *y, int64_t ny, const double *lags, int64_t K, ncf_kernel kernel,
                                   double h, int64_t N1, double *c_out, double *b_out, cudaStream_t st) {
@@ -938,7 +940,12 @@ static ncf_status corr_paper_impl(ncf_ctx *ctx, const double *t, const double *x
         paper_eval(Ax, Mh, d_phi + K1, nsym, craw_x, st);
         paper_eval(Ay, Mh, d_phi + K1, nsym, craw_y, st);
     }
-    paper_eval(A, Mh, d_phi, K1, craw, st);
+    // the sorted lags: a direct mode sum for short arrays, a type-2 transform (one FFT
+    // and 16 taps per lag) from kPaperType2Lags on
+    if (K1 >= kPaperType2Lags)
+        paper_type2(pm, !acf, modes_ws, A, d_phi, K1, craw, st);
+    else
+        paper_eval(A, Mh, d_phi, K1, craw, st);
     // PairCount (Algorithms 5 and 6) through the windowed paths: the sorted lags
     // and, for the CCF scales, lag 0 of each series' ACF
     if ((rc = corr_batch_impl(ctx, ox, t, x, acf ? nullptr : oy, s, y, 1, d_tau, K1, &opt, ctmp, bsrt, nullptr, st)))

@@ -859,7 +859,7 @@ constexpr int kCoefRun = 32;  // consecutive modes per thread of the deconvoluti
 __global__ void paper_coef_kernel(const double2 *__restrict__ Gx, const double2 *__restrict__ Gy, int nf,
                                   int64_t Mh, int W, const double *__restrict__ gx,
                                   const double *__restrict__ gphi, int nq_half, double2 *__restrict__ Fx,
-                                  double2 *__restrict__ Fy) {
+                                  double2 *__restrict__ Fy, double *__restrict__ invph) {
     const int64_t m0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kCoefRun;
     if (m0 > Mh) return;
     double acc[kCoefRun];
@@ -884,6 +884,7 @@ __global__ void paper_coef_kernel(const double2 *__restrict__ Gx, const double2 
         const int64_t m = m0 + j;
         if (m > Mh) break;
         const double inv = 1.0 / (W * acc[j]);  // (W/2) x 2 x (sum over the positive nodes)
+        invph[m] = inv;
         double2 X, Wt;
         unpack(Gx, nf, m, X, Wt);
         Fx[m] = make_double2(X.x * inv, X.y * inv);
@@ -896,7 +897,7 @@ __global__ void paper_coef_kernel(const double2 *__restrict__ Gx, const double2 
 
 struct PaperBufs {
     double2 *grid_x, *grid_y, *scratch, *tw, *Fx, *Fy;
-    double *d_tc, *d_gx, *d_gphi;
+    double *d_tc, *d_gx, *d_gphi, *invph;
     size_t used;
 };
 
@@ -912,8 +913,51 @@ PaperBufs carve_paper(const PaperModes &pm, bool ccf, char *ws) {
     b.d_tc = take<double>(ws, used, 1);
     b.d_gx = take<double>(ws, used, pm.nq / 2);
     b.d_gphi = take<double>(ws, used, pm.nq / 2);
+    b.invph = take<double>(ws, used, pm.Mh + 1);
     b.used = used + 256;
     return b;
+}
+
+// Type-2 evaluation (modes -> lags) of S(tau) = sum_{m=0}^{Mh} A_m exp(-2 pi i m tau / L)
+// by the ES kernel: b_m = A_m / phihat_m on the n_f grid, one FFT, and at each lag a
+// W-tap interpolation at grid coordinate u = frac(tau / L) n_f, taken from the lag's
+// 64-bit phase.  The +i FFT of conj(b) is the conjugate of the -i transform, so its
+// real part is Re S directly.  Cost: one FFT plus W taps per lag, whatever K.
+__global__ void paper_place_kernel(const double2 *__restrict__ A, const double *__restrict__ invph, int64_t Mh,
+                                   int nf, double2 *__restrict__ grid) {
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nf) return;
+    double2 v = make_double2(0.0, 0.0);
+    if (l <= Mh) {
+        const double s = invph[l];
+        const double2 a = A[l];
+        v = make_double2(a.x * s, -a.y * s);
+    }
+    grid[l] = v;
+}
+
+template <int W, int D>
+__global__ void paper_interp_kernel(const double2 *__restrict__ G, int lg, const unsigned long long *__restrict__ phi,
+                                    int64_t K, const EsPoly<double, W, D> poly, double *__restrict__ c) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const long long mask = (1ll << lg) - 1;
+    const unsigned long long ph = phi[k];
+    const long long ui = (long long)(ph >> (64 - lg));                  // integer part of u
+    const double uf = (double)((ph << lg) >> 11) * 0x1.0p-53;           // fraction of u
+    const int up = uf > 0.0;
+    const long long l0 = ui - W / 2 + up;                               // ceil(u - W/2)
+    const double v = 2.0 * (up ? 1.0 - uf : 0.0) - 1.0;                 // 2 f0 - 1
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+        const double *cf = poly.c + t * (D + 1);
+        double w = cf[D];
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) w = fma(w, v, cf[d]);
+        acc = fma(G[(l0 + t) & mask].x, w, acc);
+    }
+    c[k] = acc;
 }
 
 }  // namespace
@@ -991,9 +1035,23 @@ void paper_modes_run(const PaperModes &pm, const SpecSide &x, const SpecSide *y,
     const int64_t threads = (pm.Mh + kCoefRun) / kCoefRun;
     NCF_LAUNCH("paper_coef_kernel", st,
                paper_coef_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(
-                   Gx, Gy, pm.nf, pm.Mh, pm.W, bf.d_gx, bf.d_gphi, pm.nq / 2, bf.Fx, bf.Fy));
+                   Gx, Gy, pm.nf, pm.Mh, pm.W, bf.d_gx, bf.d_gphi, pm.nq / 2, bf.Fx, bf.Fy, bf.invph));
     *Fx = bf.Fx;
     *Fy = bf.Fy;
+}
+
+void paper_type2(const PaperModes &pm, bool ccf, char *ws, const double2 *A, const unsigned long long *phi,
+                 int64_t K, double *c, cudaStream_t st) {
+    PaperBufs bf = carve_paper(pm, ccf, ws);
+    NCF_LAUNCH("paper_place_kernel", st,
+               paper_place_kernel<<<(unsigned)((pm.nf + 255) / 256), 256, 0, st>>>(A, bf.invph, pm.Mh, pm.nf,
+                                                                                 bf.grid_x));
+    const double2 *G = fft_forward_f64(bf.grid_x, bf.scratch, bf.tw, pm.lg, 1, st);
+    EsPoly<double, 16, PolyDeg<16>::D> poly{};
+    for (size_t i = 0; i < pm.poly.size(); ++i) poly.c[i] = pm.poly[i];
+    NCF_LAUNCH("paper_interp_kernel", st,
+               (paper_interp_kernel<16, PolyDeg<16>::D><<<(unsigned)((K + 127) / 128), 128, 0, st>>>(
+                   G, pm.lg, phi, K, poly, c)));
 }
 
 ncf_status spectral_plan(const SpectralArgs &a, SpectralPrepared *sp, size_t *ws_bytes,

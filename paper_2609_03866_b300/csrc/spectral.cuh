@@ -86,6 +86,11 @@ size_t paper_modes_pinned_bytes(const PaperModes &pm);
 // (and y), by ES spreading, FFT and deconvolution; *Fx, *Fy point into ws.
 void paper_modes_run(const PaperModes &pm, const SpecSide &x, const SpecSide *y, char *ws, char *pinned,
                      double2 **Fx, double2 **Fy, cudaStream_t st);
+// c[k] = Re sum_{m=0}^{Mh} A_m exp(-2 pi i m tau_k / L) by a type-2 transform on the
+// grid of paper_modes_run (after it): deconvolution, one FFT, W-tap interpolation at
+// each lag from its phase phi[k] = frac(tau_k / L) 2^64.  Overwrites the grids.
+void paper_type2(const PaperModes &pm, bool ccf, char *ws, const double2 *A, const unsigned long long *phi,
+                 int64_t K, double *c, cudaStream_t st);
 
 // k_paper.cu: A_m = fac_m conj(Fa_m) Fb_m (fac 1 at m = 0 and, N1 even, at
 // m = N1/2; 2 otherwise); c[k] += sum_m Re(A_m exp(-2 pi i m tau_k / L)) with

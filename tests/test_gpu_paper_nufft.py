@@ -65,6 +65,23 @@ def test_ccf_matches_oracle(kernel, h):
     np.testing.assert_allclose(b, ref["b"], rtol=B_RTOL)
 
 
+@pytest.mark.parametrize("kernel,h", [("gaussian", 0.7), ("rectangle", 1.5)])
+def test_long_lag_arrays_through_the_type2_transform(kernel, h):
+    # from 48 evaluation lags on, the raw correlation comes from a type-2 transform
+    # (deconvolution, one FFT, 16-tap interpolation) instead of the direct mode sum
+    t, x = _irregular(280, 140.0, 12)
+    s, y = _irregular(230, 130.0, 13, phase=6.0)
+    lags = _lags(120, -35.0, 35.0, 14)
+    c, b = _run(t, x, lags, kernel, h, s=s, y=y)
+    ref = pn.ccf(t, x, s, y, lags, kernel, h)
+    print("type2 ccf", kernel, h, ref["N1"], np.abs(c - ref["c"]).max())
+    np.testing.assert_allclose(c, ref["c"], rtol=0, atol=C_TOL)
+    np.testing.assert_allclose(b, ref["b"], rtol=B_RTOL)
+    c, b = _run(t, x, lags, kernel, h)
+    ref = pn.acf(t, x, lags, kernel, h)
+    np.testing.assert_allclose(c, ref["c"], rtol=0, atol=C_TOL)
+
+
 @pytest.mark.parametrize("N1", [4096, 4097])
 def test_explicit_grid_sizes(N1):
     # even N1 carries the unpaired mode -N1/2 with weight 1
