@@ -297,8 +297,11 @@ rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
 // loop over the lags of the group is warp-uniform.  A window edge is found in
 // O(1): a rank table over uniform bins of the coarse key range gives the first
 // key of the edge's bin, and a short walk inside the bin finishes.  The group's
-// lags are split into sub-groups whose key union fits the staging area; a
-// single lag whose union does not fit runs on the global keys.
+// lags are split into sub-groups whose key union fits the staging area.  When a
+// single lag's union does not fit, the tile's outer points are split into
+// segments (at the widest time gap, else in the middle) and each segment is
+// planned again; a lag whose single-point window fills half the staging area
+// runs on the global keys.
 //
 // Staged entries.  Entry i of a sub-group holds the coarse key of window point
 // ia + i (relative to the segment's smallest query) and the prefix sum
