@@ -937,8 +937,7 @@ static ncf_status corr_paper_impl(ncf_ctx *ctx, const double *t, const double *x
         paper_spectrum(Fy, Fy, Mh, pm.N1, Ay, st);
         NCF_CUDA(cudaMemsetAsync(craw_x, 0, nsym * 8, st));
         NCF_CUDA(cudaMemsetAsync(craw_y, 0, nsym * 8, st));
-        paper_eval(Ax, Mh, d_phi + K1, nsym, craw_x, st);
-        paper_eval(Ay, Mh, d_phi + K1, nsym, craw_y, st);
+        paper_eval(Ax, Mh, d_phi + K1, nsym, craw_x, st, Ay, craw_y);
     }
     // the sorted lags: a direct mode sum for short arrays, a type-2 transform (one FFT
     // and 16 taps per lag) from kPaperType2Lags on

@@ -39,21 +39,30 @@ __global__ void paper_spectrum_kernel(const double2 *__restrict__ Fa, const doub
 // exact in integer arithmetic, so each warp starts its run of modes from an
 // exactly reduced angle and steps with the rotation exp(-2 pi i tau_k / L).
 __global__ void __launch_bounds__(kEvalWarps * 32)
-paper_eval_kernel(const double2 *__restrict__ A, int64_t Mh, const unsigned long long *__restrict__ phi,
-                  int64_t K, double *__restrict__ c) {
+paper_eval_kernel(const double2 *__restrict__ A0, const double2 *__restrict__ A1, int64_t Mh,
+                  const unsigned long long *__restrict__ phi, int64_t K, double *__restrict__ c0,
+                  double *__restrict__ c1) {
+    // blockIdx.z selects one of two spectra evaluated at the same lags
+    const double2 *__restrict__ A = blockIdx.z ? A1 : A0;
+    double *__restrict__ c = blockIdx.z ? c1 : c0;
     __shared__ double part[kEvalWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t k = (int64_t)blockIdx.y * 32 + lane;
+    // With 16 lags or fewer (one lag tile), S = 32 / K lanes share a lag and take
+    // every S-th mode of the warp's run, so that no lane idles; else S = 1.
+    const int S = (K <= 16) ? (int)(32 / K) : 1;
+    const int64_t k = (int64_t)blockIdx.y * 32 + lane / S;
+    const int sub = lane % S;
     const int64_t m0 = ((int64_t)blockIdx.x * kEvalWarps + warp) * kEvalModes;
     double acc = 0.0;
-    if (k < K && m0 <= Mh) {
+    if (k < K && lane / S < 32 / S && m0 + sub <= Mh) {
         const unsigned long long ph = phi[k];
-        const unsigned long long p0 = (unsigned long long)m0 * ph;
+        const unsigned long long p0 = (unsigned long long)(m0 + sub) * ph;
+        const unsigned long long pstep = (unsigned long long)S * ph;
         double zs, zc, rs, rc;
         sincospi(2.0 * ((double)(p0 >> 11) * 0x1.0p-53), &zs, &zc);
-        sincospi(2.0 * ((double)(ph >> 11) * 0x1.0p-53), &rs, &rc);
+        sincospi(2.0 * ((double)(pstep >> 11) * 0x1.0p-53), &rs, &rc);
         const int64_t m1 = min(m0 + kEvalModes, Mh + 1);
-        for (int64_t m = m0; m < m1; ++m) {
+        for (int64_t m = m0 + sub; m < m1; m += S) {
             const double2 a = A[m];
             acc = fma(a.x, zc, fma(a.y, zs, acc));  // Re[(a.x + i a.y)(cos - i sin)]
             const double c2 = fma(zc, rc, -zs * rs);
@@ -63,11 +72,14 @@ paper_eval_kernel(const double2 *__restrict__ A, int64_t Mh, const unsigned long
     }
     part[warp][lane] = acc;
     __syncthreads();
-    if (warp == 0 && k < K) {
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < kEvalWarps; ++w) s += part[w][lane];
-        atomicAdd(c + k, s);
+    if (warp == 0 && lane < 32 / S) {
+        const int64_t kk = (int64_t)blockIdx.y * 32 + lane;
+        if (kk < K) {
+            double s = 0.0;
+            for (int w = 0; w < kEvalWarps; ++w)
+                for (int j = 0; j < S; ++j) s += part[w][lane * S + j];
+            atomicAdd(c + kk, s);
+        }
     }
 }
 
@@ -128,11 +140,11 @@ void paper_spectrum(const double2 *Fa, const double2 *Fb, int64_t Mh, int64_t N1
 }
 
 void paper_eval(const double2 *A, int64_t Mh, const unsigned long long *phi, int64_t K, double *c,
-                cudaStream_t st) {
+                cudaStream_t st, const double2 *A1, double *c1) {
     const int64_t per_cta = (int64_t)kEvalWarps * kEvalModes;
-    dim3 grid((unsigned)((Mh + per_cta) / per_cta), (unsigned)((K + 31) / 32));
+    dim3 grid((unsigned)((Mh + per_cta) / per_cta), (unsigned)((K + 31) / 32), A1 ? 2u : 1u);
     NCF_LAUNCH("paper_eval_kernel", st,
-               paper_eval_kernel<<<grid, kEvalWarps * 32, 0, st>>>(A, Mh, phi, K, c));
+               paper_eval_kernel<<<grid, kEvalWarps * 32, 0, st>>>(A, A1, Mh, phi, K, c, c1));
 }
 
 void paper_finish(const double *craw, const double *bsrt, int64_t K1, const int64_t *perm, int64_t pos0,

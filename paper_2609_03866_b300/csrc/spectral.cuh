@@ -97,8 +97,9 @@ void paper_type2(const PaperModes &pm, bool ccf, char *ws, const double2 *A, con
 // phi[k] = frac(tau_k / L) 2^64 (c zeroed by the caller); the smoothing,
 // pair-count division, normalisation and unsorting of Algorithms 2-4.
 void paper_spectrum(const double2 *Fa, const double2 *Fb, int64_t Mh, int64_t N1, double2 *A, cudaStream_t st);
+// (with A1, c1: a second spectrum at the same lags in the same launch)
 void paper_eval(const double2 *A, int64_t Mh, const unsigned long long *phi, int64_t K, double *c,
-                cudaStream_t st);
+                cudaStream_t st, const double2 *A1 = nullptr, double *c1 = nullptr);
 void paper_finish(const double *craw, const double *bsrt, int64_t K1, const int64_t *perm, int64_t pos0,
                   const double *w, int nw, int o0, bool acf, const double *craw_x, const double *craw_y,
                   int64_t nsym, const double *bx0, const double *by0, double *tmp, double *c_out,
