@@ -30,11 +30,13 @@ __device__ __forceinline__ double centre(double s, double tau, int eps) {
 constexpr double kInvSqrt2Pi = 0.398942280401432677939946059934381868;
 
 // exp(z) for z <= 0 by Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2),
-// 1989): z = (64 m + j) ln2/64 + r with |r| <= ln2/128, so exp(z) = 2^m 2^(j/64) e^r.
-// ln2/64 = L1 + L2, L1 with 32 significant bits (N L1 exact for |N| < 2^21);
-// e^r - 1 by its Taylor polynomial of degree 5 (remainder below 4e-17); the
-// table 2^(j/64) is filled per CTA from exp2.  About 10 FP64 operations against
-// the two dozen of a general exp; the Gaussian weights need only z <= 0.
+// 1989): z = (256 m + j) ln2/256 + r with |r| <= ln2/512, so exp(z) = 2^m 2^(j/256) e^r.
+// ln2/256 = L1 + L2, L1 with 33 significant bits (N L1 exact for |N| < 2^20);
+// e^r - 1 by its Taylor polynomial of degree 4 (remainder below 4e-17); the
+// table 2^(j/256) is filled per CTA from exp2, and 2^m is added to the exponent
+// field as an integer.  About 9 FP64 operations against the two dozen of a
+// general exp, within 1.3 ulp for a correctly rounded table; the Gaussian weights
+// need only z <= 0.
 // cos(pi v) for |v| <= 1/2 (the Hann window's range) by its Taylor series in
 // (pi v)^2 up to degree 22: the remainder is below 2e-17 and the evaluation within
 // 4e-16 of the exact value.
@@ -55,21 +57,24 @@ __device__ __forceinline__ double cos_pi_half(double v) {
     return fma(a, w, 1.0);
 }
 
-constexpr double kExpInvL = 92.33248261689366;         // 64 / ln 2
-constexpr double kExpL1 = 0x1.62e42fee00000p-7;        // ln2/64, upper 32 bits
-constexpr double kExpL2 = 0x1.a39ef35793c76p-39;       // ln2/64 - L1
+constexpr double kExpInvL = 369.3299304675746;         // 256 / ln 2
+constexpr double kExpL1 = 0x1.62e42fee00000p-9;        // ln2/256, upper 33 bits
+constexpr double kExpL2 = 0x1.a39ef35793c76p-41;       // ln2/256 - L1
+constexpr int kExpTable = 256;
+// below N = -1021 * 256 (z < -707.7) the weight is returned as 0: above it the
+// result and every intermediate stay normal numbers
 __device__ __forceinline__ double exp_neg(double z, const double *__restrict__ T) {
-    if (z < -708.0) return 0.0;  // below the normal range: weight 0
     const double nd = fma(z, kExpInvL, 0x1.8p52);       // N in the low bits
     const int n = (int)__double2loint(nd);
+    if (n < -1021 * kExpTable) return 0.0;
     const double N = nd - 0x1.8p52;
     double r = fma(-N, kExpL1, z);
     r = fma(-N, kExpL2, r);
-    const double p = r * fma(r, fma(r, fma(r, fma(r, 0x1.1111111111111p-7, 0x1.5555555555555p-5),
-                                            0x1.5555555555555p-3), 0.5), 1.0);
-    const double t = T[n & 63];
-    const double v = fma(t, p, t);
-    return v * __longlong_as_double((long long)((n >> 6) + 1023) << 52);
+    const double p = r * fma(r, fma(r, fma(r, 1.0 / 24.0, 1.0 / 6.0), 0.5), 1.0);
+    const double t = T[n & (kExpTable - 1)];
+    const double v = fma(t, p, t);                      // in [0.99, 2): a normal number
+    return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(v) +
+                                            ((unsigned long long)(long long)(n >> 8) << 52)));
 }
 
 __global__ void __launch_bounds__(kWarps * 32)
@@ -80,8 +85,8 @@ gauss_window_kernel(const double *__restrict__ tx, const double *__restrict__ x,
                     const double *__restrict__ lags, int64_t K, int eps, double h, double Rh, int hann,
                     double *__restrict__ num, double *__restrict__ den,
                     unsigned long long *__restrict__ cnt) {
-    __shared__ double T2[64];  // 2^(j/64) for exp_neg
-    if (threadIdx.x < 64) T2[threadIdx.x] = exp2((double)threadIdx.x / 64.0);
+    __shared__ double T2[kExpTable];  // 2^(j/256) for exp_neg
+    for (int i = threadIdx.x; i < kExpTable; i += blockDim.x) T2[i] = exp2((double)i / kExpTable);
     __syncthreads();
     const ScanTile tile = tiles[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -128,6 +133,7 @@ gauss_window_kernel(const double *__restrict__ tx, const double *__restrict__ x,
             else
                 while (hi < xb && tx[hi] < wu) ++hi;
             const double yj = (y[j] - my) * iy;
+            // sum_i w_i (x_i - m_x); the factor 1 / sigma_x is applied once per outer point
             double nj = 0.0, bj = 0.0;
             for (int64_t i = lo; i < hi; ++i) {
                 const double d = tx[i] - cj;
@@ -139,10 +145,10 @@ gauss_window_kernel(const double *__restrict__ tx, const double *__restrict__ x,
                     w = exp_neg(-d * d * inv2h2, T2);
                 }
                 bj += w;
-                nj = fma(w, (x[i] - mx) * ix, nj);
+                nj = fma(w, x[i] - mx, nj);
             }
             Bw += bj;
-            N = fma(nj, yj, N);
+            N = fma(nj * ix, yj, N);
             c += (unsigned long long)(hi > lo ? hi - lo : 0);
         }
     }
