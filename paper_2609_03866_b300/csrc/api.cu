@@ -235,6 +235,7 @@ struct Eval {
     int64_t B = 0, K = 0;
     ncf_options opt{};
     int path = NCF_PATH_AUTO;
+    bool den_only = false;  // windowed path: the pair sums alone (PairCount), no numerator
     Side X, Y;
     std::vector<double> lagv;
     double max_tau = 0.0, t_abs = 0.0;
@@ -616,8 +617,8 @@ ncf_status launch(ncf_ctx *ctx, Eval &ev, bool stats_fresh, bool guard, double *
         NCF_CUDA(cudaMemsetAsync(ev.gden, 0, B * K * 8, st));
         NCF_CUDA(cudaMemsetAsync(ev.gcnt, 0, B * K * 8, st));
         const int eps = ev.acf ? +1 : -1;
-        launch_gauss_window(X.t, X.v, X.d_offs, X.d_stats, O.t, O.v, O.d_stats, ev.g_tiles, ev.g_ntiles, ev.d_lags,
-                            K, eps, ev.opt.h, Rh, hann, ev.gnum, ev.gden, ev.gcnt, st);
+        launch_gauss_window(X.t, ev.den_only ? nullptr : X.v, X.d_offs, X.d_stats, O.t, O.v, O.d_stats, ev.g_tiles,
+                            ev.g_ntiles, ev.d_lags, K, eps, ev.opt.h, Rh, hann, ev.gnum, ev.gden, ev.gcnt, st);
         if (ev.lag0) {
             NCF_CUDA(cudaMemsetAsync(ev.zero_lag, 0, 8, st));
             NCF_CUDA(cudaMemsetAsync(ev.gn0, 0, 2 * B * 8, st));
@@ -754,7 +755,7 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
                                   const double *x, const int64_t *offs_y, const double *s,
                                   const double *y, int64_t B, const double *lags, int64_t K,
                                   const ncf_options *opt, double *c_out, double *b_out,
-                                  int64_t *count_out, cudaStream_t st) {
+                                  int64_t *count_out, cudaStream_t st, bool den_only = false) {
     LaunchScope scope(ctx);
     ctx->err.clear();
     // the pinned staging buffer may still feed a copy queued by the previous call
@@ -762,6 +763,7 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
     Eval ev;
     ncf_status rc = check_args(ctx, offs_x, t, x, offs_y, s, y, B, lags, K, opt, ev);
     if (rc) return rc;
+    ev.den_only = den_only;
     if (!c_out) return fail(ctx, NCF_EINVAL, "c_out is NULL");
     ev.X.t = t; ev.X.v = x;
     if (!ev.acf) { ev.Y.t = s; ev.Y.v = y; }
@@ -945,14 +947,17 @@ static ncf_status corr_paper_impl(ncf_ctx *ctx, const double *t, const double *x
         paper_type2(pm, !acf, modes_ws, A, d_phi, K1, craw, st);
     else
         paper_eval(A, Mh, d_phi, K1, craw, st);
-    // PairCount (Algorithms 5 and 6) through the windowed paths: the sorted lags
-    // and, for the CCF scales, lag 0 of each series' ACF
-    if ((rc = corr_batch_impl(ctx, ox, t, x, acf ? nullptr : oy, s, y, 1, d_tau, K1, &opt, ctmp, bsrt, nullptr, st)))
+    // PairCount (Algorithms 5 and 6) through the windowed paths, pair sums alone:
+    // the sorted lags and, for the CCF scales, lag 0 of each series' ACF
+    if ((rc = corr_batch_impl(ctx, ox, t, x, acf ? nullptr : oy, s, y, 1, d_tau, K1, &opt, ctmp, bsrt, nullptr, st,
+                              true)))
         return rc;
     if (!acf) {
-        if ((rc = corr_batch_impl(ctx, ox, t, x, nullptr, nullptr, nullptr, 1, d_zero, 1, &opt, ctmp, bx0, nullptr, st)))
+        if ((rc = corr_batch_impl(ctx, ox, t, x, nullptr, nullptr, nullptr, 1, d_zero, 1, &opt, ctmp, bx0, nullptr, st,
+                                  true)))
             return rc;
-        if ((rc = corr_batch_impl(ctx, oy, s, y, nullptr, nullptr, nullptr, 1, d_zero, 1, &opt, ctmp, by0, nullptr, st)))
+        if ((rc = corr_batch_impl(ctx, oy, s, y, nullptr, nullptr, nullptr, 1, d_zero, 1, &opt, ctmp, by0, nullptr, st,
+                                  true)))
             return rc;
     }
     paper_finish(craw, bsrt, K1, d_perm, pos0, d_w, (int)w.size(), o0, acf, craw_x, craw_y, nsym, bx0, by0, tmp,

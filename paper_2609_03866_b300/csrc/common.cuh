@@ -127,6 +127,7 @@ ncf_status rect_prepare(const RectArgs &a, char *ws, size_t ws_cap, char *pinned
 ncf_status rect_launch(const RectArgs &a, const RectPrepared &r, cudaStream_t st, std::string *msg);
 // Windowed FP64 scan (Algorithms 5 and 7): Gaussian over [c - Rh, c + Rh), or
 // (hann) the Hann window cos^2(pi d / 2h) / h over the closed [c - h, c + h].
+// x == nullptr: the pair sums (den, cnt) alone, PairCount of Algorithm 5; num untouched.
 void launch_gauss_window(const double *tx, const double *x, const int64_t *offs_x,
                          const SeriesStats *stx, const double *sy, const double *y,
                          const SeriesStats *sty, const ScanTile *tiles, int64_t n_tiles,

@@ -29,14 +29,6 @@ __device__ __forceinline__ double centre(double s, double tau, int eps) {
 
 constexpr double kInvSqrt2Pi = 0.398942280401432677939946059934381868;
 
-// exp(z) for z <= 0 by Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2),
-// 1989): z = (256 m + j) ln2/256 + r with |r| <= ln2/512, so exp(z) = 2^m 2^(j/256) e^r.
-// ln2/256 = L1 + L2, L1 with 33 significant bits (N L1 exact for |N| < 2^20);
-// e^r - 1 by its Taylor polynomial of degree 4 (remainder below 4e-17); the
-// table 2^(j/256) is filled per CTA from exp2, and 2^m is added to the exponent
-// field as an integer.  About 9 FP64 operations against the two dozen of a
-// general exp, within 1.3 ulp for a correctly rounded table; the Gaussian weights
-// need only z <= 0.
 // cos(pi v) for |v| <= 1/2 (the Hann window's range) by its Taylor series in
 // (pi v)^2 up to degree 22: the remainder is below 2e-17 and the evaluation within
 // 4e-16 of the exact value.
@@ -57,9 +49,18 @@ __device__ __forceinline__ double cos_pi_half(double v) {
     return fma(a, w, 1.0);
 }
 
+// exp(z) for z <= 0 by Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2),
+// 1989): z = (256 m + j) ln2/256 + r with |r| <= ln2/512, so exp(z) = 2^m 2^(j/256) e^r.
+// r = z - N C in one FMA with C = fl(ln2/256), 9.1e-20 below ln2/256: with
+// |N| <= |z| 256/ln2 + 1/2 this shifts r by at most 3.4e-17 |z|, an error of
+// e^z |z| 3.4e-17 <= 1.3e-17 in absolute terms, whatever z (the weights only
+// enter sums, whose scale is the peak weight 1).  e^r - 1 by its Taylor
+// polynomial of degree 4 (remainder below 4e-17); the table 2^(j/256) is filled
+// per CTA from exp2, and 2^m is added to the exponent field as an integer.
+// 8 FP64 operations; within 1.3 ulp for -1 < z <= 0 and 1.3e-16 absolute for all
+// z <= 0 (for a correctly rounded table).
 constexpr double kExpInvL = 369.3299304675746;         // 256 / ln 2
-constexpr double kExpL1 = 0x1.62e42fee00000p-9;        // ln2/256, upper 33 bits
-constexpr double kExpL2 = 0x1.a39ef35793c76p-41;       // ln2/256 - L1
+constexpr double kExpC = 0x1.62e42fefa39efp-9;        // fl(ln2 / 256)
 constexpr int kExpTable = 256;
 // below N = -1021 * 256 (z < -707.7) the weight is returned as 0: above it the
 // result and every intermediate stay normal numbers
@@ -68,8 +69,7 @@ __device__ __forceinline__ double exp_neg(double z, const double *__restrict__ T
     const int n = (int)__double2loint(nd);
     if (n < -1021 * kExpTable) return 0.0;
     const double N = nd - 0x1.8p52;
-    double r = fma(-N, kExpL1, z);
-    r = fma(-N, kExpL2, r);
+    const double r = fma(-N, kExpC, z);
     const double p = r * fma(r, fma(r, fma(r, 1.0 / 24.0, 1.0 / 6.0), 0.5), 1.0);
     const double t = T[n & (kExpTable - 1)];
     const double v = fma(t, p, t);                      // in [0.99, 2): a normal number
@@ -77,6 +77,8 @@ __device__ __forceinline__ double exp_neg(double z, const double *__restrict__ T
                                             ((unsigned long long)(long long)(n >> 8) << 52)));
 }
 
+// kNum = false: the pair sums B alone (PairCount); x, y and num are not read
+template <bool kNum>
 __global__ void __launch_bounds__(kWarps * 32)
 gauss_window_kernel(const double *__restrict__ tx, const double *__restrict__ x,
                     const int64_t *__restrict__ offs_x, const SeriesStats *__restrict__ stx,
@@ -132,7 +134,6 @@ gauss_window_kernel(const double *__restrict__ tx, const double *__restrict__ x,
                 while (hi < xb && tx[hi] <= wu) ++hi;
             else
                 while (hi < xb && tx[hi] < wu) ++hi;
-            const double yj = (y[j] - my) * iy;
             // sum_i w_i (x_i - m_x); the factor 1 / sigma_x is applied once per outer point
             double nj = 0.0, bj = 0.0;
             for (int64_t i = lo; i < hi; ++i) {
@@ -145,10 +146,10 @@ gauss_window_kernel(const double *__restrict__ tx, const double *__restrict__ x,
                     w = exp_neg(-d * d * inv2h2, T2);
                 }
                 bj += w;
-                nj = fma(w, x[i] - mx, nj);
+                if constexpr (kNum) nj = fma(w, x[i] - mx, nj);
             }
             Bw += bj;
-            N = fma(nj * ix, yj, N);
+            if constexpr (kNum) N = fma(nj * ix, (y[j] - my) * iy, N);
             c += (unsigned long long)(hi > lo ? hi - lo : 0);
         }
     }
@@ -159,7 +160,7 @@ gauss_window_kernel(const double *__restrict__ tx, const double *__restrict__ x,
     }
     if (lane == 0) {
         const int64_t slot = (int64_t)tile.b * K + k;
-        atomicAdd(num + slot, N * norm);
+        if constexpr (kNum) atomicAdd(num + slot, N * norm);
         atomicAdd(den + slot, Bw * norm);
         atomicAdd(cnt + slot, c);
     }
@@ -257,9 +258,14 @@ void launch_gauss_window(const double *tx, const double *x, const int64_t *offs_
                          const double *lags, int64_t K, int eps, double h, double Rh, int hann,
                          double *num, double *den, unsigned long long *cnt, cudaStream_t st) {
     dim3 grid((unsigned)n_tiles, (unsigned)((K + kWarps - 1) / kWarps));
-    NCF_LAUNCH("gauss_window_kernel", st,
-    gauss_window_kernel<<<grid, kWarps * 32, 0, st>>>(tx, x, offs_x, stx, sy, y, sty, tiles, lags, K,
-                                                      eps, h, Rh, hann, num, den, cnt));
+    if (x)
+        NCF_LAUNCH("gauss_window_kernel", st,
+        gauss_window_kernel<true><<<grid, kWarps * 32, 0, st>>>(tx, x, offs_x, stx, sy, y, sty, tiles, lags, K,
+                                                                eps, h, Rh, hann, num, den, cnt));
+    else
+        NCF_LAUNCH("gauss_window_kernel", st,
+        gauss_window_kernel<false><<<grid, kWarps * 32, 0, st>>>(tx, x, offs_x, stx, sy, y, sty, tiles, lags, K,
+                                                                 eps, h, Rh, hann, num, den, cnt));
 }
 
 void launch_finish_rect(const unsigned long long *cnt, const unsigned long long *num128,
