@@ -85,6 +85,19 @@ def test_gaussian_windowed_matches_untruncated_definition():
     assert np.max(np.abs(got["b"] - ref["b"]) / ref["b"]) < 1e-12
 
 
+def test_gaussian_windowed_very_wide_window_underflows_to_zero_weights():
+    # R = 45: weights down to exp(-1012), past the exponential's cut at z = -707.7
+    # (weight 0, where the oracle's exp gives at most a few subnormals)
+    w = synth.ar1_acf()
+    ref = oracle.corr(w.t, w.x, w.lags, "gaussian", 1.0, trunc_R=45, method="windowed")
+    got = gpu(w.t, w.x, w.lags, kernel="gaussian", h=1.0, path="windowed", trunc_R=45)
+    assert np.array_equal(got["count"], ref["count"])
+    assert max_abs(got["c"], ref["c"]) < TOL
+    assert np.max(np.abs(got["b"] - ref["b"]) / ref["b"]) < 1e-12
+    full = oracle.corr(w.t, w.x, w.lags, "gaussian", 1.0)
+    assert max_abs(got["c"], full["c"]) < TOL
+
+
 def test_gaussian_windowed_paper_window_counts_exact():
     w = synth.ou_ccf(nA=4000, nB=3000, K=41)
     ref = oracle.corr(w.t, w.x, w.lags, "gaussian", 0.5, s=w.s, y=w.y, trunc_R=6, method="windowed")
