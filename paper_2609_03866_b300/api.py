@@ -220,6 +220,33 @@ def _stream_handle(stream, device):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+_OUT_DTYPES = (("c", "float64"), ("b", "float64"), ("count", "int64"))
+
+
+def _check_out(out, shape, device):
+    """Caller-supplied result buffers: out["c"] required, "b" and "count" optional;
+    each contiguous, of its dtype, on `device` and of `shape`."""
+    import torch
+    if out.get("c") is None:
+        raise ValueError('out["c"] is required')
+    for key, dt in _OUT_DTYPES:
+        v = out.get(key)
+        if v is None:
+            continue
+        if not isinstance(v, torch.Tensor) or v.dtype != getattr(torch, dt) or v.device != torch.device(device) \
+                or tuple(v.shape) != tuple(shape) or not v.is_contiguous():
+            raise ValueError(f'out["{key}"] must be a contiguous {dt} tensor of shape {tuple(shape)} on {device}')
+
+
+def _check_device_input(name, a, n, device):
+    """Plan inputs are used as they are: contiguous float64 tensors on the plan's
+    device with the element count the plan was built for."""
+    import torch
+    if not isinstance(a, torch.Tensor) or a.dtype != torch.float64 or a.device != torch.device(device) \
+            or not a.is_contiguous() or a.numel() != n:
+        raise ValueError(f"{name} must be a contiguous float64 tensor of {n} elements on {device}")
+
+
 def corr(t, x, lags, kernel="gaussian", h=1.0, s=None, y=None, path="auto", precision="fp64",
          norm="none", trunc_R=0.0, tol=0.0, ctx: Context | None = None, stream=None):
     """One ACF (s, y omitted) or CCF on the GPU.  Returns dict(c, b, count)
@@ -303,11 +330,13 @@ def corr_regular(m, x, dt, lags, kernel="gaussian", h=1.0, m_y=None, y=None, nor
         L._reg_types = True
     ctx = ctx or default_context()
     dev = torch.device("cuda", ctx.device)
-    mi = torch.as_tensor(np.ascontiguousarray(m, dtype=np.int64) if not hasattr(m, "device") else m).to(dev)
+    mi = torch.as_tensor(np.ascontiguousarray(m, dtype=np.int64) if not hasattr(m, "device") else m)
+    mi = mi.to(device=dev, dtype=torch.int64).contiguous()
     x, lags = _dev(x, dev), _dev(lags, dev)
     ccf = y is not None
     if ccf:
-        my = torch.as_tensor(np.ascontiguousarray(m_y, dtype=np.int64) if not hasattr(m_y, "device") else m_y).to(dev)
+        my = torch.as_tensor(np.ascontiguousarray(m_y, dtype=np.int64) if not hasattr(m_y, "device") else m_y)
+        my = my.to(device=dev, dtype=torch.int64).contiguous()
         y = _dev(y, dev)
     K = lags.numel()
     out = {"c": torch.empty(K, dtype=torch.float64, device=dev), "b": torch.empty(K, dtype=torch.float64, device=dev),
@@ -379,6 +408,8 @@ def corr_batch(offs, t, x, lags, kernel="gaussian", h=1.0, offs_y=None, s=None, 
         out = {"c": torch.empty(B, K, dtype=torch.float64, device=dev),
                "b": torch.empty(B, K, dtype=torch.float64, device=dev),
                "count": torch.empty(B, K, dtype=torch.int64, device=dev)}
+    else:
+        _check_out(out, (B, K), dev)
     o = make_options(kernel, h, path, precision, norm, trunc_R, tol)
     rc = lib().ncf_corr_batch(ctx.handle, pox, _ptr(t), _ptr(x), poy, _ptr(None if acf else s),
                               _ptr(None if acf else y), B, _ptr(lags), K, ctypes.byref(o),
@@ -394,14 +425,14 @@ def corr_batch_host(offs, t, x, lags, kernel="gaussian", h=1.0, offs_y=None, s=N
     """corr_batch on host arrays (numpy or pinned CPU tensors): the library
     copies inputs in and results out and synchronises before returning."""
     import torch
-    ctx = ctx or default_context()
-    dev = torch.device("cuda", ctx.device)
 
     def host(a):
         if a is None:
             return None
         if isinstance(a, torch.Tensor):
-            return a.contiguous()
+            if a.device.type != "cpu":
+                raise ValueError("corr_batch_host takes host arrays; use corr_batch for device tensors")
+            return a.to(torch.float64).contiguous()  # no copy for a contiguous float64 (pinned) tensor
         return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64))
 
     ox, pox = _host_offs(offs)
@@ -413,6 +444,10 @@ def corr_batch_host(offs, t, x, lags, kernel="gaussian", h=1.0, offs_y=None, s=N
     if out is None:
         out = {"c": torch.empty(B, K, dtype=torch.float64), "b": torch.empty(B, K, dtype=torch.float64),
                "count": torch.empty(B, K, dtype=torch.int64)}
+    else:
+        _check_out(out, (B, K), "cpu")
+    ctx = ctx or default_context()
+    dev = torch.device("cuda", ctx.device)
     o = make_options(kernel, h, path, precision, norm, trunc_R, tol)
     rc = lib().ncf_corr_batch_host(ctx.handle, pox, _ptr(t), _ptr(x), poy, _ptr(s), _ptr(y), B,
                                    _ptr(lags), K, ctypes.byref(o), _ptr(out["c"]), _ptr(out.get("b")),
@@ -441,6 +476,7 @@ class Plan:
         oy, poy = (None, ctypes.c_void_p(0)) if self.acf else _host_offs(offs_y)
         if not self.acf:
             s, y = _dev(s, dev), _dev(y, dev)
+        self.n_x, self.n_y = t.numel(), (0 if self.acf else s.numel())
         o = make_options(kernel, h, path, precision, norm, trunc_R, tol)
         self._h = ctypes.c_void_p()
         rc = lib().ncf_plan_create(self.ctx.handle, pox, _ptr(t), _ptr(x), poy, _ptr(None if self.acf else s),
@@ -454,11 +490,23 @@ class Plan:
         return int(lib().ncf_plan_device_bytes(self._h))
 
     def execute(self, t, x, s=None, y=None, out=None, stream=None):
+        """t, x (and s, y for a CCF): contiguous float64 device tensors of the sizes
+        the plan was built for; the plan reads them as they are."""
         import torch
+        _check_device_input("t", t, self.n_x, self.device)
+        _check_device_input("x", x, self.n_x, self.device)
+        if self.acf:
+            if s is not None or y is not None:
+                raise ValueError("this plan is an ACF: s and y are not taken")
+        else:
+            _check_device_input("s", s, self.n_y, self.device)
+            _check_device_input("y", y, self.n_y, self.device)
         if out is None:
             out = {"c": torch.empty(self.B, self.K, dtype=torch.float64, device=self.device),
                    "b": torch.empty(self.B, self.K, dtype=torch.float64, device=self.device),
                    "count": torch.empty(self.B, self.K, dtype=torch.int64, device=self.device)}
+        else:
+            _check_out(out, (self.B, self.K), self.device)
         rc = lib().ncf_plan_execute(self._h, _ptr(t), _ptr(x), _ptr(s), _ptr(y), _ptr(out["c"]),
                                     _ptr(out.get("b")), _ptr(out.get("count")),
                                     _stream_handle(stream, self.device))
