@@ -19,6 +19,8 @@
 #include <mutex>
 #include <numeric>
 #include <string>
+
+#include <nvtx3/nvToolsExt.h>  // header-only; each launch is a named range for a tracing tool
 #include <vector>
 
 #include "common.cuh"
@@ -64,6 +66,7 @@ static thread_local ncf_ctx *tls_ctx = nullptr;
 
 namespace ncf {
 LaunchMark::LaunchMark(const char *name, cudaStream_t s) : slot(-1), st(s) {
+    nvtxRangePushA(name);  // no-op unless a tracing tool is attached
     ncf_ctx *c = tls_ctx;
     if (!c) return;
     ++c->launches;
@@ -83,6 +86,7 @@ LaunchMark::LaunchMark(const char *name, cudaStream_t s) : slot(-1), st(s) {
 }
 LaunchMark::~LaunchMark() {
     if (slot >= 0 && tls_ctx) cudaEventRecord(tls_ctx->prof.pool[slot + 1], st);
+    nvtxRangePop();
 }
 }  // namespace ncf
 

@@ -172,8 +172,9 @@ void launch_finish_gauss(const double *num, const double *den, const unsigned lo
 }  // namespace ncf
 
 // Launch bookkeeping: every kernel launch in the library goes through
-// NCF_LAUNCH, which counts it and, when the context's profiler is on, brackets
-// it with CUDA events recorded on the launch stream.
+// NCF_LAUNCH, which counts it, marks it as an NVTX range named for the kernel
+// and, when the context's profiler is on, brackets it with CUDA events
+// recorded on the launch stream.
 namespace ncf {
 struct LaunchMark {
     LaunchMark(const char *name, cudaStream_t st);

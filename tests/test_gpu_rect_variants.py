@@ -149,3 +149,14 @@ def test_workspace_sizes_for_any_batch_and_lag_count(B, K):
         r = to_np(api.corr_batch(w.offs, w.t, w.x, w.lags, kernel="gaussian", h=0.5, path="spectral",
                                  precision=prec))
         assert np.all(np.isfinite(r["c"]))
+
+
+def test_same_call_twice_gives_identical_results():
+    # the scan's sums are exact integers added with integer atomics: no run-to-run
+    # difference is allowed, in any variant
+    w = synth.light_curves(B=96, K=40, seed=synth.BASE_SEED + 9)
+    for v in VARIANTS:
+        a = to_np(run_variant(v, lambda: api.corr_batch(w.offs, w.t, w.x, w.lags, kernel="rectangle", h=0.5)))
+        b = to_np(run_variant(v, lambda: api.corr_batch(w.offs, w.t, w.x, w.lags, kernel="rectangle", h=0.5)))
+        for key in ("count", "b", "c"):
+            assert np.array_equal(a[key], b[key]), (v, key)
