@@ -194,6 +194,28 @@ NCF_API ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, cons
                                const double *lags, int64_t K, const ncf_options *opt,
                                double *c_out, double *b_out, int64_t *count_out, void *stream);
 
+/*
+ * Several estimators of one batch from a single upload.  For example, the
+ * Gaussian and the rectangle estimate of the same series (Eq. kernel_estimator
+ * with Eq. Gaussian_kernel and Eq. rectangle_kernel).  It works as
+ * ncf_corr_batch_host but takes n_opts option sets:
+ *   - t, x (s, y) and lags are copied to the device once;
+ *   - each chunk of series is evaluated with opts[0], ..., opts[n_opts - 1] in
+ *     turn;
+ *   - the results are written to the HOST buffers c_out[o], b_out[o] and
+ *     count_out[o], each [B x K].
+ * b_out and count_out may be NULL, and so may any of their entries.
+ * Every result equals the one ncf_corr_batch_host gives for that option set.
+ * Errors are those of ncf_corr_batch_host.  The first failing option set ends
+ * the call; the outputs of the other sets are then undefined.  n_opts < 1, a
+ * NULL opts or a NULL c_out[o] gives NCF_EINVAL.
+ */
+NCF_API ncf_status ncf_corr_batch_host_multi(ncf_ctx *ctx, const int64_t *offs_x, const double *t,
+                                             const double *x, const int64_t *offs_y, const double *s,
+                                             const double *y, int64_t B, const double *lags, int64_t K,
+                                             const ncf_options *opts, int n_opts, double *const *c_out,
+                                             double *const *b_out, int64_t *const *count_out, void *stream);
+
 
 /*
  * The paper's own NUFFT estimators, smoothing step included (Appendix

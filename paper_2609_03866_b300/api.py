@@ -419,22 +419,26 @@ def corr_batch(offs, t, x, lags, kernel="gaussian", h=1.0, offs_y=None, s=None, 
     return out
 
 
+def _host_array(a):
+    """A host float64 array for the host-buffer calls: numpy input is converted,
+    a contiguous float64 CPU tensor (pinned or not) is used as it is."""
+    import torch
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        if a.device.type != "cpu":
+            raise ValueError("the host-buffer calls take host arrays; use corr_batch for device tensors")
+        return a.to(torch.float64).contiguous()  # no copy for a contiguous float64 (pinned) tensor
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64))
+
+
 def corr_batch_host(offs, t, x, lags, kernel="gaussian", h=1.0, offs_y=None, s=None, y=None,
                     path="auto", precision="fp64", norm="none", trunc_R=0.0, tol=0.0,
                     ctx: Context | None = None, stream=None, out=None):
     """corr_batch on host arrays (numpy or pinned CPU tensors): the library
     copies inputs in and results out and synchronises before returning."""
     import torch
-
-    def host(a):
-        if a is None:
-            return None
-        if isinstance(a, torch.Tensor):
-            if a.device.type != "cpu":
-                raise ValueError("corr_batch_host takes host arrays; use corr_batch for device tensors")
-            return a.to(torch.float64).contiguous()  # no copy for a contiguous float64 (pinned) tensor
-        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64))
-
+    host = _host_array
     ox, pox = _host_offs(offs)
     B = ox.size - 1
     acf = s is None
@@ -454,6 +458,49 @@ def corr_batch_host(offs, t, x, lags, kernel="gaussian", h=1.0, offs_y=None, s=N
                                    _ptr(out.get("count")), _stream_handle(stream, dev))
     ctx.check(rc)
     return out
+
+
+def corr_batch_host_multi(offs, t, x, lags, options, offs_y=None, s=None, y=None, ctx: Context | None = None,
+                          stream=None, outs=None):
+    """Several estimators of one batch from a single upload (ncf_corr_batch_host_multi).
+    `options` is a list of dicts of corr_batch's keyword options (kernel, h, path,
+    precision, norm, trunc_R, tol); returns one dict(c, b, count) of host tensors
+    [B, K] per option set, equal to corr_batch_host with that set."""
+    import torch
+    L = lib()
+    if not getattr(L, "_multi_types", False):
+        vp = ctypes.c_void_p
+        vpp = ctypes.POINTER(ctypes.c_void_p)
+        L.ncf_corr_batch_host_multi.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp, ctypes.c_int64,
+                                                ctypes.POINTER(ncf_options), ctypes.c_int, vpp, vpp, vpp, vp]
+        L.ncf_corr_batch_host_multi.restype = ctypes.c_int
+        L._multi_types = True
+    n = len(options)
+    if n < 1:
+        raise ValueError("options: at least one option set")
+    ox, pox = _host_offs(offs)
+    B = ox.size - 1
+    acf = s is None
+    oy, poy = (None, ctypes.c_void_p(0)) if acf else _host_offs(offs_y)
+    t, x, lags, s, y = (_host_array(a) for a in (t, x, lags, s, y))
+    K = lags.numel()
+    if outs is None:
+        outs = [{"c": torch.empty(B, K, dtype=torch.float64), "b": torch.empty(B, K, dtype=torch.float64),
+                 "count": torch.empty(B, K, dtype=torch.int64)} for _ in range(n)]
+    elif len(outs) != n:
+        raise ValueError("outs: one dict of result buffers per option set")
+    for o in outs:
+        _check_out(o, (B, K), "cpu")
+    opts = (ncf_options * n)(*[make_options(**o) for o in options])
+    cp = (ctypes.c_void_p * n)(*[o["c"].data_ptr() for o in outs])
+    bp = (ctypes.c_void_p * n)(*[o["b"].data_ptr() if o.get("b") is not None else 0 for o in outs])
+    np_ = (ctypes.c_void_p * n)(*[o["count"].data_ptr() if o.get("count") is not None else 0 for o in outs])
+    ctx = ctx or default_context()
+    dev = torch.device("cuda", ctx.device)
+    rc = L.ncf_corr_batch_host_multi(ctx.handle, pox, _ptr(t), _ptr(x), poy, _ptr(s), _ptr(y), B, _ptr(lags), K,
+                                     opts, n, cp, bp, np_, _stream_handle(stream, dev))
+    ctx.check(rc)
+    return outs
 
 
 class Plan:

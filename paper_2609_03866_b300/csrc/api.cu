@@ -1238,53 +1238,71 @@ ncf_status ncf_corr_regular(ncf_ctx *ctx, const int64_t *m_x, const double *x, i
     return NCF_OK;
 }
 
-ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
-                               const int64_t *offs_y, const double *s, const double *y, int64_t B,
-                               const double *lags, int64_t K, const ncf_options *opt, double *c_out,
-                               double *b_out, int64_t *count_out, void *stream) {
-    using ncf::al;
-    if (!ctx) return NCF_EINVAL;
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return NCF_ECUDA;
-    if (!offs_x || B < 1 || K < 1 || !t || !x || !lags || !c_out) {
-        ctx->err = "ncf_corr_batch_host: NULL pointer or empty batch";
+}  // extern "C"
+
+namespace ncf {
+
+// The host-buffer calls: one upload of the batch, then n_opts evaluations of it
+// (each option set its own result buffers), chunk by chunk.
+static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                             const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                             const double *lags, int64_t K, const ncf_options *opts, int n_opts,
+                             double *const *c_out, double *const *b_out, int64_t *const *count_out,
+                             cudaStream_t st, const char *who) {
+    if (!offs_x || B < 1 || K < 1 || !t || !x || !lags || !opts || n_opts < 1 || !c_out) {
+        ctx->err = std::string(who) + ": NULL pointer, empty batch or no option set";
         return NCF_EINVAL;
     }
+    for (int o = 0; o < n_opts; ++o)
+        if (!c_out[o]) {
+            ctx->err = std::string(who) + ": c_out of option set " + std::to_string(o) + " is NULL";
+            return NCF_EINVAL;
+        }
     const bool acf = (s == nullptr && y == nullptr);
     if (!acf && (!s || !y || !offs_y)) {
-        ctx->err = "ncf_corr_batch_host: CCF needs s, y and offs_y";
+        ctx->err = std::string(who) + ": CCF needs s, y and offs_y";
         return NCF_EINVAL;
     }
-    cudaStream_t st = (cudaStream_t)stream;
     const int64_t nx = offs_x[B], ny = acf ? 0 : offs_y[B];
-    const size_t need = al(nx * 8) * 2 + al(ny * 8) * 2 + al(K * 8) + al(B * K * 8) * 3;
-    ncf_status rc = ncf::grow(ctx, &ctx->hbuf, &ctx->hbuf_cap, need, st);
+    const size_t need = al(nx * 8) * 2 + al(ny * 8) * 2 + al(K * 8) + (size_t)n_opts * al(B * K * 8) * 3;
+    ncf_status rc = grow(ctx, &ctx->hbuf, &ctx->hbuf_cap, need, st);
     if (rc) return rc;
-    ncf::Arena ar{ctx->hbuf, ctx->hbuf_cap, 0};
+    Arena ar{ctx->hbuf, ctx->hbuf_cap, 0};
     double *dt = ar.take<double>(nx), *dx = ar.take<double>(nx);
     double *ds = acf ? nullptr : ar.take<double>(ny), *dy = acf ? nullptr : ar.take<double>(ny);
     double *dl = ar.take<double>(K);
-    double *dc = ar.take<double>(B * K), *db = ar.take<double>(B * K);
-    int64_t *dn = ar.take<int64_t>(B * K);
-    // Large batches run as up to four chunks of series with about equal points:
-    // the upload of chunk i+1 (copy stream) overlaps the evaluation of chunk i
-    // (the caller's stream), and each chunk's results come back while the next
-    // one runs.  Pinned host buffers are needed for the copies to overlap.
+    std::vector<double *> dc(n_opts), db(n_opts);
+    std::vector<int64_t *> dn(n_opts);
+    for (int o = 0; o < n_opts; ++o) {
+        dc[o] = ar.take<double>(B * K);
+        db[o] = ar.take<double>(B * K);
+        dn[o] = ar.take<int64_t>(B * K);
+    }
+    auto bo = [&](int o) { return b_out ? b_out[o] : nullptr; };
+    auto no = [&](int o) { return count_out ? count_out[o] : nullptr; };
+    // Large batches run as up to four chunks of series: the upload of chunk i+1
+    // (copy stream) overlaps the evaluation of chunk i (the caller's stream), and
+    // each chunk's results come back while the next one runs.  Chunk sizes double
+    // (1/15, 2/15, 4/15, 8/15 of the points): only the first, small upload waits
+    // with nothing to overlap, and as copies outrun the scan-bound evaluations,
+    // each later upload still ends before the chunk ahead of it.  Pinned host
+    // buffers are needed for the copies to overlap.
     const int64_t pts = nx + ny;
     const int C = (int)std::min<int64_t>(B, pts * 16 > (int64_t)(256 << 20) ? 4 : 1);
     std::vector<int64_t> cut(C + 1, B);
     cut[0] = 0;
     for (int c = 1; c < C; ++c) {
-        const int64_t target = pts * c / C;
+        const int64_t target = pts * ((int64_t(1) << c) - 1) / ((int64_t(1) << C) - 1);
         int64_t b = cut[c - 1];
         while (b < B && offs_x[b] + (acf ? 0 : offs_y[b]) < target) ++b;
         cut[c] = std::max(b, cut[c - 1]);
     }
     if (!ctx->copy_st && cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking) != cudaSuccess)
-        return ncf::fail(ctx, NCF_ECUDA, "ncf_corr_batch_host: copy stream creation failed");
+        return fail(ctx, NCF_ECUDA, "%s: copy stream creation failed", who);
     while ((int)ctx->copy_ev.size() < 2 * C + 1) {
         cudaEvent_t e;
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
-            return ncf::fail(ctx, NCF_ECUDA, "ncf_corr_batch_host: event creation failed");
+            return fail(ctx, NCF_ECUDA, "%s: event creation failed", who);
         ctx->copy_ev.push_back(e);
     }
     cudaStream_t cs = ctx->copy_st;
@@ -1305,7 +1323,7 @@ ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, const double
     };
     ok = ok && cudaMemcpyAsync(dl, lags, K * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
     for (int c = 0; c < std::min(C, 2); ++c) ok = ok && upload(c);
-    if (!ok) return ncf::fail(ctx, NCF_ECUDA, "host-to-device copy failed: %s", cudaGetErrorString(cudaGetLastError()));
+    if (!ok) return fail(ctx, NCF_ECUDA, "host-to-device copy failed: %s", cudaGetErrorString(cudaGetLastError()));
     std::vector<int64_t> ox, oy;
     for (int c = 0; c < C; ++c) {
         const int64_t b0 = cut[c], b1 = cut[c + 1], nb = b1 - b0;
@@ -1318,13 +1336,16 @@ ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, const double
                 for (auto &v : oy) v -= y0;
             }
             if (cudaStreamWaitEvent(st, ev_in[c], 0) != cudaSuccess)
-                return ncf::fail(ctx, NCF_ECUDA, "ncf_corr_batch_host: stream wait failed");
-            rc = ncf::corr_batch_impl(ctx, ox.data(), dt + x0, dx + x0, acf ? nullptr : oy.data(),
-                                      acf ? nullptr : ds + y0, acf ? nullptr : dy + y0, nb, dl, K, opt, dc + b0 * K,
-                                      b_out ? db + b0 * K : nullptr, count_out ? dn + b0 * K : nullptr, st);
-            if (rc) {
-                cudaStreamSynchronize(cs);
-                return rc;
+                return fail(ctx, NCF_ECUDA, "%s: stream wait failed", who);
+            for (int o = 0; o < n_opts; ++o) {
+                rc = corr_batch_impl(ctx, ox.data(), dt + x0, dx + x0, acf ? nullptr : oy.data(),
+                                     acf ? nullptr : ds + y0, acf ? nullptr : dy + y0, nb, dl, K, &opts[o],
+                                     dc[o] + b0 * K, bo(o) ? db[o] + b0 * K : nullptr,
+                                     no(o) ? dn[o] + b0 * K : nullptr, st);
+                if (rc) {
+                    cudaStreamSynchronize(cs);
+                    return rc;
+                }
             }
         }
         ok = cudaEventRecord(ev_out[c], st) == cudaSuccess;
@@ -1333,9 +1354,9 @@ ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, const double
         auto d2h = [&](void *h, const void *d) {
             return cudaMemcpyAsync(h, d, nb * K * 8, cudaMemcpyDeviceToHost, cs) == cudaSuccess;
         };
-        if (nb > 0)
-            ok = ok && d2h(c_out + b0 * K, dc + b0 * K) && (!b_out || d2h(b_out + b0 * K, db + b0 * K)) &&
-                 (!count_out || d2h(count_out + b0 * K, dn + b0 * K));
+        for (int o = 0; o < n_opts && nb > 0; ++o)
+            ok = ok && d2h(c_out[o] + b0 * K, dc[o] + b0 * K) && (!bo(o) || d2h(bo(o) + b0 * K, db[o] + b0 * K)) &&
+                 (!no(o) || d2h(no(o) + b0 * K, dn[o] + b0 * K));
         if (!ok) break;
     }
     if (!ok || cudaStreamSynchronize(cs) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
@@ -1343,6 +1364,31 @@ ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, const double
         return NCF_ECUDA;
     }
     return NCF_OK;
+}
+
+}  // namespace ncf
+
+extern "C" {
+
+ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                               const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                               const double *lags, int64_t K, const ncf_options *opt, double *c_out,
+                               double *b_out, int64_t *count_out, void *stream) {
+    if (!ctx) return NCF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return NCF_ECUDA;
+    return ncf::host_batch(ctx, offs_x, t, x, offs_y, s, y, B, lags, K, opt, 1, &c_out, &b_out, &count_out,
+                           (cudaStream_t)stream, "ncf_corr_batch_host");
+}
+
+ncf_status ncf_corr_batch_host_multi(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                                     const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                                     const double *lags, int64_t K, const ncf_options *opts, int n_opts,
+                                     double *const *c_out, double *const *b_out, int64_t *const *count_out,
+                                     void *stream) {
+    if (!ctx) return NCF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return NCF_ECUDA;
+    return ncf::host_batch(ctx, offs_x, t, x, offs_y, s, y, B, lags, K, opts, n_opts, c_out, b_out, count_out,
+                           (cudaStream_t)stream, "ncf_corr_batch_host_multi");
 }
 
 ncf_status ncf_plan_create(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,

@@ -44,3 +44,13 @@ def test_check_device_input_wants_float64_of_the_planned_size():
                 torch.zeros(18, dtype=torch.float64)[::2], np.zeros(9)):
         with pytest.raises(ValueError):
             api._check_device_input("t", bad, 9, "cpu")
+
+
+def test_multi_host_call_refuses_mismatched_result_buffers():
+    opts = [dict(kernel="rectangle", h=0.5), dict(kernel="gaussian", h=0.5)]
+    with pytest.raises(ValueError):   # one dict of buffers per option set
+        api.corr_batch_host_multi(OFFS, T, X, LAGS, opts, outs=[host_out()])
+    with pytest.raises(ValueError):
+        api.corr_batch_host_multi(OFFS, T, X, LAGS, opts, outs=[host_out(), host_out(c=torch.empty(2, 2))])
+    with pytest.raises(ValueError):
+        api.corr_batch_host_multi(OFFS, T, X, LAGS, [])

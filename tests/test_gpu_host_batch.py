@@ -51,3 +51,37 @@ def test_small_host_batch_ccf_and_pearson():
                         offs_y=c.offs_y, s=pinned(c.s), y=pinned(c.y), out=out)
     ref = to_np(api.corr(c.t, c.x, c.lags, kernel="gaussian", h=0.5, s=c.s, y=c.y))
     assert max_abs(out["c"].numpy()[0], ref["c"]) < 1e-10
+
+
+def test_several_estimators_from_one_upload_equal_separate_calls():
+    # ncf_corr_batch_host_multi: the same chunks (and spectral periods) as the
+    # single call, so each option set matches its own host call: the rectangle
+    # exactly, the Gaussian up to the order of the spreading's atomic additions
+    w = synth.light_curves(B=700, n_lo=20_000, n_hi=200_000, K=64, seed=synth.BASE_SEED + 77)
+    opts = [dict(kernel="gaussian", h=0.5, path="spectral", precision="fp32"),
+            dict(kernel="rectangle", h=0.5),
+            dict(kernel="gaussian", h=0.5, path="spectral", precision="fp64", norm="lag0")]
+    tols = [1e-6, 0.0, 1e-12]
+    outs = api.corr_batch_host_multi(w.offs, pinned(w.t), pinned(w.x), pinned(w.lags), opts)
+    for o, tol, got in zip(opts, tols, outs):
+        ref = host_call(w, **o)
+        if tol == 0.0:
+            for key in ("c", "b", "count"):
+                assert np.array_equal(got[key].numpy(), ref[key]), (o, key)
+        else:
+            assert max_abs(got["c"].numpy(), ref["c"]) <= tol, o
+            assert np.allclose(got["b"].numpy(), ref["b"], rtol=10 * tol, atol=0), o
+
+
+def test_several_estimators_ccf_with_optional_outputs_left_out():
+    c = synth.ou_ccf(nA=3000, nB=2400, K=17)
+    opts = [dict(kernel="rectangle", h=0.5), dict(kernel="gaussian", h=0.5, path="windowed", trunc_R=8.0)]
+    outs = [{"c": torch.empty(1, c.lags.size, dtype=torch.float64)},
+            {"c": torch.empty(1, c.lags.size, dtype=torch.float64),
+             "count": torch.empty(1, c.lags.size, dtype=torch.int64)}]
+    api.corr_batch_host_multi(c.offs, c.t, c.x, c.lags, opts, offs_y=c.offs_y, s=c.s, y=c.y, outs=outs)
+    for o, got in zip(opts, outs):
+        ref = to_np(api.corr(c.t, c.x, c.lags, s=c.s, y=c.y, **o))
+        assert max_abs(got["c"].numpy()[0], ref["c"]) < 1e-10
+        if "count" in got:
+            assert np.array_equal(got["count"].numpy()[0], ref["count"])
