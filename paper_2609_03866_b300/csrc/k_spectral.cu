@@ -868,7 +868,11 @@ constexpr int kCoefRun = 32;  // consecutive modes per thread of the deconvoluti
 // nodes are summed (twice).  Along a thread's run of modes the cosines follow
 // the rotation cos(pi (m+1) a) = Re[exp(i pi m a) exp(i pi a)], restarted from
 // sincospi at every run.
-__global__ void paper_coef_kernel(const double2 *__restrict__ Gx, const double2 *__restrict__ Gy, int nf,
+// G: the FFT of the spread grid.  packed = 0: one series, its values in the real
+// part (the imaginary part holds the unit weights, unused here); packed = 1: the
+// CCF's two series, x in the real and y in the imaginary part, so that one FFT
+// serves both transforms and Hermitian symmetry separates them.
+__global__ void paper_coef_kernel(const double2 *__restrict__ G, int packed, int nf,
                                   int64_t Mh, int W, const double *__restrict__ gx,
                                   const double *__restrict__ gphi, int nq_half, double2 *__restrict__ Fx,
                                   double2 *__restrict__ Fy, double *__restrict__ invph) {
@@ -898,13 +902,16 @@ __global__ void paper_coef_kernel(const double2 *__restrict__ Gx, const double2 
         const double inv = 1.0 / (W * acc[j]);  // (W/2) x 2 x (sum over the positive nodes)
         invph[m] = inv;
         double2 X, Wt;
-        unpack(Gx, nf, m, X, Wt);
+        unpack(G, nf, m, X, Wt);
         Fx[m] = make_double2(X.x * inv, X.y * inv);
-        if (Gy) {
-            unpack(Gy, nf, m, X, Wt);
-            Fy[m] = make_double2(X.x * inv, X.y * inv);
-        }
+        if (packed) Fy[m] = make_double2(Wt.x * inv, Wt.y * inv);
     }
+}
+
+// the CCF's second series into the imaginary part of the first one's grid
+__global__ void paper_pack_kernel(double2 *__restrict__ gx, const double2 *__restrict__ gy, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) gx[i].y = gy[i].x;
 }
 
 struct PaperBufs {
@@ -1035,19 +1042,19 @@ void paper_modes_run(const PaperModes &pm, const SpecSide &x, const SpecSide *y,
                        poly, grid));
     };
     spread(x, bf.grid_x);
-    if (ccf) spread(*y, bf.grid_y);
+    if (ccf) {
+        spread(*y, bf.grid_y);
+        NCF_LAUNCH("paper_pack_kernel", st,
+                   paper_pack_kernel<<<(unsigned)((pm.nf + 255) / 256), 256, 0, st>>>(bf.grid_x, bf.grid_y,
+                                                                                     pm.nf));
+    }
     NCF_LAUNCH("twiddle_kernel", st,
                twiddle_kernel<double2><<<twiddle_blocks(pm.nf), 256, 0, st>>>(bf.tw, pm.nf));
-    double2 *Gx = fft_forward_f64(bf.grid_x, bf.scratch, bf.tw, pm.lg, 1, st);
-    if (Gx == bf.scratch && ccf) {
-        cudaMemcpyAsync(bf.grid_x, bf.scratch, (size_t)pm.nf * sizeof(double2), cudaMemcpyDeviceToDevice, st);
-        Gx = bf.grid_x;
-    }
-    double2 *Gy = ccf ? fft_forward_f64(bf.grid_y, bf.scratch, bf.tw, pm.lg, 1, st) : nullptr;
+    const double2 *G = fft_forward_f64(bf.grid_x, bf.scratch, bf.tw, pm.lg, 1, st);
     const int64_t threads = (pm.Mh + kCoefRun) / kCoefRun;
     NCF_LAUNCH("paper_coef_kernel", st,
                paper_coef_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(
-                   Gx, Gy, pm.nf, pm.Mh, pm.W, bf.d_gx, bf.d_gphi, pm.nq / 2, bf.Fx, bf.Fy, bf.invph));
+                   G, ccf ? 1 : 0, pm.nf, pm.Mh, pm.W, bf.d_gx, bf.d_gphi, pm.nq / 2, bf.Fx, bf.Fy, bf.invph));
     *Fx = bf.Fx;
     *Fy = bf.Fy;
 }
