@@ -860,52 +860,50 @@ __global__ void spectral_guard_kernel(const SeriesStats *__restrict__ sx, const 
 // The paper's own NUFFT estimators (Algorithms 2-4, smoothing step included):
 // deconvolved type-1 coefficients on the padded period of Algorithm 1.
 // ---------------------------------------------------------------------------
-constexpr int kCoefRun = 32;  // consecutive modes per thread of the deconvolution
+// phihat_m = (W/2) int_{-1}^{1} phi(z) cos(pi m W z / n_f) dz varies on a scale of
+// about n_f / W modes (its value falls by a factor of about 4 from m = 0 to the
+// band edge), so Gauss-Legendre quadrature runs only at every kPhiStep-th mode and
+// the modes between come from 8-point Lagrange interpolation (nodes -3 .. 4 around
+// them): the interpolation error, (pi W kPhiStep / n_f)^8 / 8! relative, is far
+// below the quadrature's own rounding (about 3e-15).
+constexpr int kPhiStep = 64;
+constexpr int kPhiTaps = 8;
 
-// F_m = X_m / phihat_m for m = 0 .. Mh, X_m from the Hermitian unpack of the
-// grid transform.  phihat_m = (W/2) int_{-1}^{1} phi(z) cos(pi m W z / n_f) dz by
-// Gauss-Legendre quadrature; the integrand is even, so only the nq/2 positive
-// nodes are summed (twice).  Along a thread's run of modes the cosines follow
-// the rotation cos(pi (m+1) a) = Re[exp(i pi m a) exp(i pi a)], restarted from
-// sincospi at every run.
+// coarse[i] = the positive-node half of the quadrature at mode (i - 3) kPhiStep
+// (phihat is even in m, so the three leading negative modes are valid too)
+__global__ void paper_phihat_kernel(int nf, int W, const double *__restrict__ gx, const double *__restrict__ gphi,
+                                    int nq_half, int64_t n_coarse, double *__restrict__ coarse) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_coarse) return;
+    const double k = (double)((i - 3) * kPhiStep);
+    double acc = 0.0;
+    for (int q = 0; q < nq_half; ++q) acc = fma(gphi[q], cospi(k * ((double)W / nf * gx[q])), acc);
+    coarse[i] = acc;
+}
+
+// F_m = X_m / phihat_m for m = 0 .. Mh, X_m from the Hermitian unpack of the grid
+// transform, phihat_m interpolated from the coarse quadrature (lagw[r][j]: the
+// Lagrange weight of node j - 3 at offset r / kPhiStep).
 // G: the FFT of the spread grid.  packed = 0: one series, its values in the real
 // part (the imaginary part holds the unit weights, unused here); packed = 1: the
 // CCF's two series, x in the real and y in the imaginary part, so that one FFT
 // serves both transforms and Hermitian symmetry separates them.
-__global__ void paper_coef_kernel(const double2 *__restrict__ G, int packed, int nf,
-                                  int64_t Mh, int W, const double *__restrict__ gx,
-                                  const double *__restrict__ gphi, int nq_half, double2 *__restrict__ Fx,
-                                  double2 *__restrict__ Fy, double *__restrict__ invph) {
-    const int64_t m0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kCoefRun;
-    if (m0 > Mh) return;
-    double acc[kCoefRun];
+__global__ void paper_coef_kernel(const double2 *__restrict__ G, int packed, int nf, int64_t Mh, int W,
+                                  const double *__restrict__ coarse, const double *__restrict__ lagw,
+                                  double2 *__restrict__ Fx, double2 *__restrict__ Fy, double *__restrict__ invph) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m > Mh) return;
+    const int64_t c = m / kPhiStep;
+    const double *wr = lagw + (m - c * kPhiStep) * kPhiTaps;
+    double acc = 0.0;
 #pragma unroll
-    for (int j = 0; j < kCoefRun; ++j) acc[j] = 0.0;
-    for (int q = 0; q < nq_half; ++q) {
-        const double a = (double)W / nf * gx[q];
-        const double w = gphi[q];
-        double c, sn, rc, rs;
-        sincospi((double)m0 * a, &sn, &c);
-        sincospi(a, &rs, &rc);
-#pragma unroll
-        for (int j = 0; j < kCoefRun; ++j) {
-            acc[j] = fma(w, c, acc[j]);
-            const double c2 = fma(c, rc, -sn * rs);
-            sn = fma(sn, rc, c * rs);
-            c = c2;
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < kCoefRun; ++j) {
-        const int64_t m = m0 + j;
-        if (m > Mh) break;
-        const double inv = 1.0 / (W * acc[j]);  // (W/2) x 2 x (sum over the positive nodes)
-        invph[m] = inv;
-        double2 X, Wt;
-        unpack(G, nf, m, X, Wt);
-        Fx[m] = make_double2(X.x * inv, X.y * inv);
-        if (packed) Fy[m] = make_double2(Wt.x * inv, Wt.y * inv);
-    }
+    for (int j = 0; j < kPhiTaps; ++j) acc = fma(wr[j], coarse[c + j], acc);
+    const double inv = 1.0 / (W * acc);  // (W/2) x 2 x (sum over the positive nodes)
+    invph[m] = inv;
+    double2 X, Wt;
+    unpack(G, nf, m, X, Wt);
+    Fx[m] = make_double2(X.x * inv, X.y * inv);
+    if (packed) Fy[m] = make_double2(Wt.x * inv, Wt.y * inv);
 }
 
 // the CCF's second series into the imaginary part of the first one's grid
@@ -916,9 +914,30 @@ __global__ void paper_pack_kernel(double2 *__restrict__ gx, const double2 *__res
 
 struct PaperBufs {
     double2 *grid_x, *grid_y, *scratch, *tw, *Fx, *Fy;
-    double *d_tc, *d_gx, *d_gphi, *invph;
+    double *d_tc, *d_gx, *d_gphi, *invph, *coarse, *lagw;
     size_t used;
 };
+
+// coarse quadrature samples: modes -3 kPhiStep .. (Mh / kPhiStep + 4) kPhiStep
+int64_t paper_coarse_count(const PaperModes &pm) { return pm.Mh / kPhiStep + 8; }
+
+// Lagrange weights of the nodes -3 .. 4 at t = r / kPhiStep, r = 0 .. kPhiStep - 1
+const std::vector<double> &paper_lagrange_weights() {
+    static const std::vector<double> w = [] {
+        std::vector<double> v((size_t)kPhiStep * kPhiTaps);
+        for (int r = 0; r < kPhiStep; ++r) {
+            const long double t = (long double)r / kPhiStep;
+            for (int j = 0; j < kPhiTaps; ++j) {
+                long double l = 1.0L;
+                for (int i = 0; i < kPhiTaps; ++i)
+                    if (i != j) l *= (t - (i - 3)) / (long double)(j - i);
+                v[(size_t)r * kPhiTaps + j] = (double)l;
+            }
+        }
+        return v;
+    }();
+    return w;
+}
 
 PaperBufs carve_paper(const PaperModes &pm, bool ccf, char *ws) {
     PaperBufs b{};
@@ -933,6 +952,8 @@ PaperBufs carve_paper(const PaperModes &pm, bool ccf, char *ws) {
     b.d_gx = take<double>(ws, used, pm.nq / 2);
     b.d_gphi = take<double>(ws, used, pm.nq / 2);
     b.invph = take<double>(ws, used, pm.Mh + 1);
+    b.coarse = take<double>(ws, used, paper_coarse_count(pm));
+    b.lagw = take<double>(ws, used, kPhiStep * kPhiTaps);
     b.used = used + 256;
     return b;
 }
@@ -1010,7 +1031,9 @@ ncf_status paper_modes_plan(double L, double tc, int64_t N1, PaperModes *pm, std
 
 size_t paper_modes_bytes(const PaperModes &pm, bool ccf) { return carve_paper(pm, ccf, nullptr).used; }
 
-size_t paper_modes_pinned_bytes(const PaperModes &pm) { return al(8) + 2 * al(pm.nq / 2 * 8); }
+size_t paper_modes_pinned_bytes(const PaperModes &pm) {
+    return al(8) + 2 * al(pm.nq / 2 * 8) + al((size_t)kPhiStep * kPhiTaps * 8);
+}
 
 void paper_modes_run(const PaperModes &pm, const SpecSide &x, const SpecSide *y, char *ws, char *pinned,
                      double2 **Fx, double2 **Fy, cudaStream_t st) {
@@ -1025,6 +1048,7 @@ void paper_modes_run(const PaperModes &pm, const SpecSide &x, const SpecSide *y,
     up(bf.d_tc, &pm.tc, 8);
     up(bf.d_gx, pm.gx.data(), pm.nq / 2 * 8);
     up(bf.d_gphi, pm.gphi.data(), pm.nq / 2 * 8);
+    up(bf.lagw, paper_lagrange_weights().data(), (size_t)kPhiStep * kPhiTaps * 8);
     constexpr size_t smem = spread_smem_bytes<double>();
     static bool attr = false;
     if (!attr) {
@@ -1051,10 +1075,13 @@ void paper_modes_run(const PaperModes &pm, const SpecSide &x, const SpecSide *y,
     NCF_LAUNCH("twiddle_kernel", st,
                twiddle_kernel<double2><<<twiddle_blocks(pm.nf), 256, 0, st>>>(bf.tw, pm.nf));
     const double2 *G = fft_forward_f64(bf.grid_x, bf.scratch, bf.tw, pm.lg, 1, st);
-    const int64_t threads = (pm.Mh + kCoefRun) / kCoefRun;
+    const int64_t n_coarse = paper_coarse_count(pm);
+    NCF_LAUNCH("paper_phihat_kernel", st,
+               paper_phihat_kernel<<<(unsigned)((n_coarse + 127) / 128), 128, 0, st>>>(
+                   pm.nf, pm.W, bf.d_gx, bf.d_gphi, pm.nq / 2, n_coarse, bf.coarse));
     NCF_LAUNCH("paper_coef_kernel", st,
-               paper_coef_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(
-                   G, ccf ? 1 : 0, pm.nf, pm.Mh, pm.W, bf.d_gx, bf.d_gphi, pm.nq / 2, bf.Fx, bf.Fy, bf.invph));
+               paper_coef_kernel<<<(unsigned)((pm.Mh + 256) / 256), 256, 0, st>>>(
+                   G, ccf ? 1 : 0, pm.nf, pm.Mh, pm.W, bf.coarse, bf.lagw, bf.Fx, bf.Fy, bf.invph));
     *Fx = bf.Fx;
     *Fy = bf.Fy;
 }
