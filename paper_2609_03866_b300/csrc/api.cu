@@ -652,7 +652,7 @@ ncf_status launch(ncf_ctx *ctx, Eval &ev, bool stats_fresh, bool guard, double *
 // pair inside the window, O(n K n_window); the spectral path costs the
 // spreading, the FFT and the mode sums, O(n W + n_f log n_f + M K) per series.
 // The crossover in K is the paper's K* (Sec. 5.1); here it is a cost model
-// with constants measured on B300 (windowed 56 ps per pair; FP64 spreading
+// with constants measured on B300 (windowed 44 ps per pair; FP64 spreading
 // 0.4 ns per point; FP64 FFT 16 B per cell and pass at 5 TB/s; FP64 mode sums
 // at 0.57 T FMA/s).
 void choose_path(Eval &ev) {
@@ -675,7 +675,7 @@ void choose_path(Eval &ev) {
     double nf = 1.0;
     while (nf < 4.0 * M + 16.0) nf *= 2.0;
     const double passes = std::ceil(std::log2(nf) / 3.0) * (ev.acf ? 1.0 : 2.0);
-    const double t_win = win * 56e-12;
+    const double t_win = win * 44e-12;
     const double t_spec = spread * 0.4e-9 + (double)ev.B * nf * 16.0 * 2.0 * passes / 5e12 +
                           (double)ev.B * M * (ev.K + 1.0) * 2.0 * (ev.acf ? 1.0 : 2.0) / 0.57e12;
     ev.path = t_win < t_spec ? NCF_PATH_WINDOWED : NCF_PATH_SPECTRAL;
