@@ -54,7 +54,7 @@ __device__ __forceinline__ double cos_half_range(double x) {
 // enter sums, whose scale is the peak weight 1).  e^r - 1 by its Taylor
 // polynomial of degree 4 (remainder below 4e-17); the table 2^(j/256) is filled
 // per CTA from exp2, and 2^m is added to the exponent field as an integer.
-// 8 FP64 operations; within 1.3 ulp for -1 < z <= 0 and 1.3e-16 absolute for all
+// 8 FP64 operations; within 1.5 ulp for -1 < z <= 0 and 1.3e-16 absolute for all
 // z <= 0 (for a correctly rounded table).
 constexpr double kExpInvL = 369.3299304675746;         // 256 / ln 2
 constexpr double kExpC = 0x1.62e42fefa39efp-9;        // fl(ln2 / 256)
