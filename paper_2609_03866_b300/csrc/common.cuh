@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstddef>
 #include <string>
@@ -169,6 +170,25 @@ void launch_finish_gauss(const double *num, const double *den, const unsigned lo
                          int64_t B, int64_t K, const double *scale, const int *status, double *c,
                          double *b, int64_t *count, cudaStream_t st);
 
+}  // namespace ncf
+
+namespace ncf {
+// Runs set() once per device for one call site: kernel attributes such as the
+// dynamic shared-memory limit belong to a device, and call sites are reached from
+// several threads (the server's slots).  Two threads may both run set() the first
+// time; it only repeats the same idempotent settings.
+template <typename F>
+inline void once_per_device(std::atomic<unsigned long long> &done, F &&set) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        set();
+        return;
+    }
+    const unsigned long long bit = 1ull << dev;
+    if (done.load(std::memory_order_acquire) & bit) return;
+    set();
+    done.fetch_or(bit, std::memory_order_release);
+}
 }  // namespace ncf
 
 // Launch bookkeeping: every kernel launch in the library goes through

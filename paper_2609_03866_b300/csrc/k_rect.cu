@@ -958,16 +958,15 @@ ncf_status rect_launch(const RectArgs &a, const RectPrepared &r, cudaStream_t st
     NCF_LAUNCH("rect_range_kernel", st,
                rect_range_kernel<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(
                    a.Tx, a.offs_x, a.Sy, tiles, r.n_tiles, (int)r.G, r.gmin, r.gmax, a.fs.eta, ranges));
-    static bool attr_set = false;
+    static std::atomic<unsigned long long> attr_done{0};
     const size_t smem = sizeof(RectSmem);
-    if (!attr_set) {
+    once_per_device(attr_done, [&] {
         cudaFuncSetAttribute(rect_scan_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(rect_scan_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(rect_scan_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(rect_scan_pt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(PtSmem));
-        attr_set = true;
-    }
+    });
 #define NCF_RECT_SCAN(RUN)                                                                              \
     NCF_LAUNCH("rect_scan_kernel", st,                                                                 \
                rect_scan_kernel<RUN><<<(unsigned)nr, kRectWarps * 32, smem, st>>>(                     \

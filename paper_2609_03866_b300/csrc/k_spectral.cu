@@ -743,12 +743,11 @@ ncf_status launch_typed(const SpectralArgs &a, const SpectralPrepared &p, char *
     // spreading
     const double a_scale = (double)p.nf / p.L;
     constexpr size_t smem = spread_smem_bytes<R>();
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr_done{0};
+    once_per_device(attr_done, [&] {
         cudaFuncSetAttribute(spread_kernel<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(spread_kernel<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    });
     EsPoly<R, 8, PolyDeg<8>::D> poly8{};
     EsPoly<R, 16, PolyDeg<16>::D> poly16{};
     for (size_t i = 0; i < p.poly.size(); ++i) {
@@ -1050,11 +1049,10 @@ void paper_modes_run(const PaperModes &pm, const SpecSide &x, const SpecSide *y,
     up(bf.d_gphi, pm.gphi.data(), pm.nq / 2 * 8);
     up(bf.lagw, paper_lagrange_weights().data(), (size_t)kPhiStep * kPhiTaps * 8);
     constexpr size_t smem = spread_smem_bytes<double>();
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr_done{0};
+    once_per_device(attr_done, [&] {
         cudaFuncSetAttribute(spread_kernel<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    });
     EsPoly<double, 16, PolyDeg<16>::D> poly{};
     for (size_t i = 0; i < pm.poly.size(); ++i) poly.c[i] = pm.poly[i];
     const double a_scale = (double)pm.nf / pm.L;

@@ -258,12 +258,11 @@ bool contract_tc_supported(int64_t M2) { return M2 % kTcKB == 0; }
 
 void launch_contract_tc(const float *Anum, const float *Aden, const float *E, int64_t B, int64_t M2,
                         int64_t Kp, double *acc_num, double *acc_den, int *status, cudaStream_t st) {
-    static bool attr = false;
+    static std::atomic<unsigned long long> attr_done{0};
     const size_t smem = contract_tc_smem_bytes();
-    if (!attr) {
+    once_per_device(attr_done, [&] {
         cudaFuncSetAttribute(contract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    });
     dim3 grid((unsigned)((B + kTcM - 1) / kTcM), (unsigned)((Kp + kTcN - 1) / kTcN),
               (unsigned)((M2 + kChunkModes - 1) / kChunkModes));
     NCF_LAUNCH("contract_tc_kernel", st,
