@@ -359,6 +359,34 @@ NCF_API ncf_status ncf_plan_execute(ncf_plan *plan, const double *t, const doubl
                                     void *stream);
 NCF_API ncf_status ncf_plan_status(ncf_plan *plan, void *stream, int32_t *flags);
 NCF_API size_t ncf_plan_device_bytes(const ncf_plan *plan);
+
+/*
+ * Device footprint of an evaluation, known before anything is allocated (the
+ * paper's single calling convention, Sec. 2.6 "Unified API": the same options,
+ * sizes and lag count as the call it sizes).  Host arithmetic only: no GPU work,
+ * no allocation, no synchronisation; ctx may be NULL (no error text is kept).
+ *   n_x        total points of the x side of the batch (sum over its B series)
+ *   n_y        total points of the y side, or 0 for ACFs
+ *   B, K       series and lags (K >= 1; each series needs >= 2 points)
+ *   span       the largest time span of one series (for a CCF, of the union of
+ *              its two series); the spectral grid grows with span / h
+ *   max_abs_lag  the largest |tau_k|
+ *   opt        the options of the call
+ * *device_bytes receives an upper bound of the device memory that
+ * ncf_corr_batch (or ncf_corr for B = 1) asks its context's workspace for, and
+ * of what ncf_plan_create allocates (ncf_plan_device_bytes), for any batch of
+ * these sizes whose largest span is at most `span`: the bound holds for every
+ * split of the points into the B series.  With NCF_PATH_AUTO for the FP64
+ * Gaussian, whose path is chosen from the data, it covers both paths.  The
+ * request server admits requests against its budget with this bound.  *pinned_bytes (may be NULL)
+ * receives the context's pinned host staging.  Not included: the caller's own
+ * inputs and outputs, and the uploaded copies of the host-buffer calls (16 bytes
+ * per point plus 8 per lag).  Returns NCF_EINVAL or NCF_EUNSUPPORTED for options
+ * or sizes that the calls would refuse (a spectral grid beyond 2^28 cells).
+ */
+NCF_API ncf_status ncf_workspace_bytes(ncf_ctx *ctx, int64_t n_x, int64_t n_y, int64_t B, int64_t K,
+                                       double span, double max_abs_lag, const ncf_options *opt,
+                                       size_t *device_bytes, size_t *pinned_bytes);
 NCF_API void ncf_plan_destroy(ncf_plan *plan);
 
 /*

@@ -20,16 +20,23 @@
  *      and prefix-sum numerators inside the closed window [c - h, c + h].
  *      O((n_x + n_y) * K).  Used where O1's n^2 K is too slow.
  *
- * Conventions (the readings are listed with their reasons in the design notes):
+ * Conventions, with the reading taken where the paper leaves a choice open:
  *  - outer index j runs over (s, y), window index i over (t, x); the window
  *    centre is c_j = s_j + eps * tau_k with eps = +1 for the ACF (s = t, y = x)
- *    and eps = -1 for the CCF (Sec. "Effective pair count algorithms");
- *  - rectangle: h is the half-width; a pair counts iff
- *    fl(c_j - h) <= t_i <= fl(c_j + h), every operation one FP64 rounding
- *    (compile with -ffp-contract=off so no FMA changes a rounding);
+ *    and eps = -1 for the CCF (Sec. "Effective pair count algorithms"), so a
+ *    positive lag pairs s_j with t_i near s_j - tau: y lags x;
+ *  - rectangle: h is the half-width, as in Algorithms 6 and 8, whose window is
+ *    [c - h, c + h] (Eq. rectangle_kernel writes |d| <= h/2 with h the full
+ *    width; the package's parameter is the algorithms' half-width).  A pair
+ *    counts iff fl(c_j - h) <= t_i <= fl(c_j + h), closed at both ends as in
+ *    Algorithm 6, every operation one FP64 rounding on the caller's own times
+ *    (compile with -ffp-contract=off so no FMA changes a rounding), so that the
+ *    exact integer counts have one definition;
  *  - Gaussian: b(d) = exp(-d^2 / (2 h^2)) / (sqrt(2 pi) h), Eq. Gaussian_kernel,
- *    with d = t_i - c_j.  trunc_R == 0 means untruncated (all pairs); trunc_R > 0
- *    keeps only fl(c_j - fl(R h)) <= t_i < fl(c_j + fl(R h)) as in Algorithm 5.
+ *    with d = t_i - c_j.  trunc_R == 0 means untruncated (all pairs), as the
+ *    equation is written; trunc_R > 0 keeps only
+ *    fl(c_j - fl(R h)) <= t_i < fl(c_j + fl(R h)), the half-open window of
+ *    Algorithm 5 (which takes R = 6).
  *
  * All inputs are standardised values already (the Python wrapper does the
  * standardisation in FP64, Sec. "Prior standardization").

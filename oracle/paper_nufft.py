@@ -23,7 +23,7 @@ NUFFT), with FINUFFT's conventions that the paper states (Sec. "Sign convention
 and the non-Hermitian cross-spectrum"): type 1 uses exp(+i k t~), type 2
 exp(-i k tau~), and the N1 modes are k = -floor(N1/2) .. ceil(N1/2) - 1.
 
-Readings where the paper is not explicit (each one also in the design notes):
+Readings where the paper is not explicit, each with its reason:
   - S_h, Gaussian: weights exp(-j^2 / (2 h^2)) for |j| <= r, r = int(4 h + 0.5),
     normalised to unit sum; S_h, rectangle: the mean over round(2 h) consecutive
     entries j = i - size//2 .. i - size//2 + size - 1 (round half to even).

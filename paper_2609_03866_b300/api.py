@@ -99,6 +99,10 @@ def lib():
             L.ncf_plan_device_bytes.restype = ctypes.c_size_t
             L.ncf_plan_destroy.argtypes = [vp]
             L.ncf_plan_destroy.restype = None
+            L.ncf_workspace_bytes.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                              ctypes.c_double, ctypes.c_double, ctypes.POINTER(ncf_options),
+                                              ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
+            L.ncf_workspace_bytes.restype = ctypes.c_int
             for name in ("ncf_corr_batch", "ncf_corr_batch_host"):
                 fn = getattr(L, name)
                 fn.argtypes = [vp, i64p, dp, dp, i64p, dp, dp, ctypes.c_int64, dp, ctypes.c_int64,
@@ -130,6 +134,22 @@ def make_options(kernel="gaussian", h=1.0, path="auto", precision="fp64", norm="
     o.trunc_R = float(trunc_R)
     o.tol = float(tol)
     return o
+
+
+def workspace_bytes(n_x, B, K, span, max_abs_lag, n_y=0, kernel="gaussian", h=1.0, path="auto",
+                    precision="fp64", norm="none", trunc_R=0.0, tol=0.0, ctx: "Context | None" = None):
+    """Device (and pinned host) bytes an evaluation of these sizes needs, before any
+    allocation (ncf_workspace_bytes; host arithmetic only, no GPU needed).
+    Returns (device_bytes, pinned_bytes)."""
+    o = make_options(kernel, h, path, precision, norm, trunc_R, tol)
+    d, p = ctypes.c_size_t(), ctypes.c_size_t()
+    h_ctx = ctx.handle if ctx is not None else None
+    rc = lib().ncf_workspace_bytes(h_ctx, int(n_x), int(n_y), int(B), int(K), float(span), float(max_abs_lag),
+                                   ctypes.byref(o), ctypes.byref(d), ctypes.byref(p))
+    if rc != 0:
+        msg = lib().ncf_last_error(h_ctx).decode() if ctx is not None else ""
+        raise NcfError(rc, status_name(rc), msg or "ncf_workspace_bytes refused the sizes or options")
+    return int(d.value), int(p.value)
 
 
 class Context:

@@ -105,7 +105,7 @@ ncf_status fail(ncf_ctx *ctx, ncf_status s, const char *fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
-    ctx->err = buf;
+    if (ctx) ctx->err = buf;
     return s;
 }
 
@@ -159,6 +159,7 @@ struct Side {
     const double *t = nullptr, *v = nullptr;
     std::vector<int64_t> offs, chunk_base;
     int64_t n_total = 0, n_chunks = 0, n_max = 0;
+    int64_t rect_tiles = 0, scan_tiles = 0;  // outer tiles of the rectangle and windowed scans
     // device
     int64_t *d_offs = nullptr, *d_chunk_base = nullptr;
     int32_t *d_cs = nullptr;  // series of each chunk
@@ -181,6 +182,25 @@ void plan_side(Side &sd, const int64_t *offs, int64_t B) {
     sd.chunk_base[B] = c;
     sd.n_chunks = c;
     sd.n_total = offs[B];
+    sd.rect_tiles = rect_tiles_of(sd.offs, B);
+    const int64_t tj = scan_tile_points();
+    sd.scan_tiles = 0;
+    for (int64_t b = 0; b < B; ++b) sd.scan_tiles += (offs[b + 1] - offs[b] + tj - 1) / tj;
+}
+
+// The largest sum over series of ceil(n_b / chunk) for any split of n points
+// into B series: n / chunk + B (chunk - 1) / chunk, rounded down.
+int64_t chunks_bound(int64_t n, int64_t B, int64_t chunk) { return (n + B * (chunk - 1)) / chunk; }
+
+// Host-side counts of a side described only by its size: every count that the
+// workspace depends on takes its largest value over the splits of n points into
+// B series (each of at least 2 points).
+void bound_side(Side &sd, int64_t n, int64_t B) {
+    sd.n_total = n;
+    sd.n_max = n - 2 * (B - 1);
+    sd.n_chunks = chunks_bound(n, B, kPrepChunk);
+    sd.rect_tiles = chunks_bound(n, B, rect_tile_points());
+    sd.scan_tiles = chunks_bound(n, B, scan_tile_points());
 }
 
 std::vector<ScanTile> make_tiles(const std::vector<int64_t> &offs, int64_t B, int tileJ) {
@@ -263,13 +283,12 @@ struct Eval {
     Side &outer() { return acf ? X : Y; }
 };
 
-ncf_status check_args(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
-                      const int64_t *offs_y, const double *s, const double *y, int64_t B,
-                      const double *lags, int64_t K, const ncf_options *opt, Eval &ev) {
+// Options, sizes and the path they select (AUTO resolved where the options alone
+// decide it; the FP64 Gaussian stays AUTO until the statistics are known).
+ncf_status check_options(ncf_ctx *ctx, const ncf_options *opt, int64_t B, int64_t K, int *path_out) {
     if (!opt) return fail(ctx, NCF_EINVAL, "options are NULL");
     if (B < 1) return fail(ctx, NCF_EINVAL, "B = %lld (need >= 1)", (long long)B);
     if (K < 1) return fail(ctx, NCF_EINVAL, "K = %lld (need >= 1)", (long long)K);
-    if (!t || !x || !lags) return fail(ctx, NCF_EINVAL, "NULL t, x or lags");
     if (!(opt->h > 0.0) || !std::isfinite(opt->h))
         return fail(ctx, NCF_EINVAL, "h = %g (need finite h > 0)", opt->h);
     if (opt->kernel != NCF_GAUSSIAN && opt->kernel != NCF_RECTANGLE && opt->kernel != NCF_HANNING)
@@ -282,11 +301,6 @@ ncf_status check_args(ncf_ctx *ctx, const int64_t *offs_x, const double *t, cons
         return fail(ctx, NCF_EINVAL, "unknown normalisation %d", opt->norm);
     if (!(opt->trunc_R >= 0.0) || !(opt->tol >= 0.0) || opt->tol >= 1.0)
         return fail(ctx, NCF_EINVAL, "trunc_R must be >= 0 and tol in [0, 1)");
-    const bool acf = (s == nullptr && y == nullptr);
-    if (!acf && (!s || !y || !offs_y)) return fail(ctx, NCF_EINVAL, "CCF needs s, y and offs_y");
-    ncf_status rc = check_offsets(ctx, offs_x, B, "offs_x");
-    if (rc) return rc;
-    if (!acf && (rc = check_offsets(ctx, offs_y, B, "offs_y"))) return rc;
     int path = opt->path;
     if (opt->kernel == NCF_GAUSSIAN && path == NCF_PATH_WINDOWED && opt->precision == NCF_FP32)
         return fail(ctx, NCF_EUNSUPPORTED, "the windowed Gaussian path is FP64 only");
@@ -298,6 +312,21 @@ ncf_status check_args(ncf_ctx *ctx, const int64_t *offs_x, const double *t, cons
         else if (opt->precision == NCF_FP32) path = NCF_PATH_SPECTRAL;
         // FP64 Gaussian: decided after the statistics pass (choose_path)
     }
+    *path_out = path;
+    return NCF_OK;
+}
+
+ncf_status check_args(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                      const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                      const double *lags, int64_t K, const ncf_options *opt, Eval &ev) {
+    int path = 0;
+    ncf_status rc = check_options(ctx, opt, B, K, &path);
+    if (rc) return rc;
+    if (!t || !x || !lags) return fail(ctx, NCF_EINVAL, "NULL t, x or lags");
+    const bool acf = (s == nullptr && y == nullptr);
+    if (!acf && (!s || !y || !offs_y)) return fail(ctx, NCF_EINVAL, "CCF needs s, y and offs_y");
+    if ((rc = check_offsets(ctx, offs_x, B, "offs_x"))) return rc;
+    if (!acf && (rc = check_offsets(ctx, offs_y, B, "offs_y"))) return rc;
     ev.acf = acf;
     ev.B = B;
     ev.K = K;
@@ -437,20 +466,18 @@ ncf_status main_bytes(ncf_ctx *ctx, Eval &ev, size_t *dev, size_t *pin) {
     const int64_t B = ev.B, K = ev.K;
     if (rect_scan(ev)) {
         const Side &O = ev.outer();
-        const size_t rw = rect_workspace_bytes(rect_tiles_of(O.offs, B), K);
-        const size_t rwx = ev.lag0 ? rect_workspace_bytes(rect_tiles_of(ev.X.offs, B), 1) : 0;
-        const size_t rwy = (ev.lag0 && !ev.acf) ? rect_workspace_bytes(rect_tiles_of(ev.Y.offs, B), 1) : 0;
+        const size_t rw = rect_workspace_bytes(O.rect_tiles, K);
+        const size_t rwx = ev.lag0 ? rect_workspace_bytes(ev.X.rect_tiles, 1) : 0;
+        const size_t rwy = (ev.lag0 && !ev.acf) ? rect_workspace_bytes(ev.Y.rect_tiles, 1) : 0;
         *dev = al(K * 8) + key_bytes(ev.X) + (ev.acf ? 0 : key_bytes(ev.Y)) + al(B * K * 8) * 3 +
                al(B * 8) * 8 + 1024 + rw + rwx + rwy;
-        *pin = rect_staging_bytes(rect_tiles_of(O.offs, B), K) +
-               (ev.lag0 ? rect_staging_bytes(rect_tiles_of(ev.X.offs, B), 1) : 0) +
-               ((ev.lag0 && !ev.acf) ? rect_staging_bytes(rect_tiles_of(ev.Y.offs, B), 1) : 0);
+        *pin = rect_staging_bytes(O.rect_tiles, K) + (ev.lag0 ? rect_staging_bytes(ev.X.rect_tiles, 1) : 0) +
+               ((ev.lag0 && !ev.acf) ? rect_staging_bytes(ev.Y.rect_tiles, 1) : 0);
         return NCF_OK;
     }
     if (ev.path == NCF_PATH_WINDOWED) {
-        const int tj = scan_tile_points();
-        const int64_t nt = (int64_t)make_tiles(ev.outer().offs, B, tj).size();
-        const int64_t nxt = (ev.lag0 && !ev.acf) ? (int64_t)make_tiles(ev.X.offs, B, tj).size() : 0;
+        const int64_t nt = ev.outer().scan_tiles;
+        const int64_t nxt = (ev.lag0 && !ev.acf) ? ev.X.scan_tiles : 0;
         *dev = al(B * K * 8) * 3 + al(B * 8) * 8 + al(nt * sizeof(ScanTile)) + al(nxt * sizeof(ScanTile)) +
                al(K * 8) + 1024;
         *pin = al(nt * sizeof(ScanTile)) + al(nxt * sizeof(ScanTile)) + 256;
@@ -1471,6 +1498,60 @@ ncf_status ncf_plan_status(ncf_plan *plan, void *stream, int32_t *flags) {
 }
 
 size_t ncf_plan_device_bytes(const ncf_plan *plan) { return plan ? plan->pre_cap + plan->main_cap : 0; }
+
+ncf_status ncf_workspace_bytes(ncf_ctx *ctx, int64_t n_x, int64_t n_y, int64_t B, int64_t K, double span,
+                               double max_abs_lag, const ncf_options *opt, size_t *device_bytes,
+                               size_t *pinned_bytes) {
+    using namespace ncf;
+    if (ctx) ctx->err.clear();
+    if (!device_bytes) return fail(ctx, NCF_EINVAL, "device_bytes is NULL");
+    *device_bytes = 0;
+    if (pinned_bytes) *pinned_bytes = 0;
+    int path = 0;
+    ncf_status rc = check_options(ctx, opt, B, K, &path);
+    if (rc) return rc;
+    const bool acf = n_y == 0;
+    if (n_x < 2 * B || (!acf && n_y < 2 * B))
+        return fail(ctx, NCF_EINVAL, "n_x = %lld, n_y = %lld: every series needs >= 2 points", (long long)n_x,
+                    (long long)n_y);
+    if (!(span >= 0.0) || !std::isfinite(span) || !(max_abs_lag >= 0.0) || !std::isfinite(max_abs_lag))
+        return fail(ctx, NCF_EINVAL, "span and max_abs_lag must be finite and >= 0");
+    Eval ev;
+    ev.acf = acf;
+    ev.B = B;
+    ev.K = K;
+    ev.opt = *opt;
+    ev.lag0 = opt->norm == NCF_NORM_LAG0;
+    bound_side(ev.X, n_x, B);
+    if (!acf) bound_side(ev.Y, n_y, B);
+    // every series spans `span` (the spectral grid grows with the largest span)
+    SeriesStats st{};
+    st.t_first = 0.0;
+    st.t_last = span;
+    st.n = 2;
+    ev.X.stats.assign(B, st);
+    if (!acf) ev.Y.stats.assign(B, st);
+    ev.lagv.assign(K, max_abs_lag);
+    ev.max_tau = max_abs_lag;
+    ev.t_abs = span;
+    const size_t pre = pre_bytes(ev);
+    const size_t analyze_pin = al((B + 1) * 8) * 4 + al(B * sizeof(SeriesStats)) * 2 + al(K * 8);
+    // the FP64 Gaussian's path is chosen from the data: the larger of both paths
+    std::vector<int> paths;
+    if (path == NCF_PATH_AUTO) paths = {NCF_PATH_WINDOWED, NCF_PATH_SPECTRAL};
+    else paths = {path};
+    size_t dev = 0, pin = analyze_pin;
+    for (int pth : paths) {
+        ev.path = pth;
+        size_t d = 0, p = 0;
+        if ((rc = main_bytes(ctx, ev, &d, &p))) return rc;
+        dev = std::max(dev, d);
+        pin = std::max(pin, p);
+    }
+    *device_bytes = pre + dev;
+    if (pinned_bytes) *pinned_bytes = pin;
+    return NCF_OK;
+}
 
 void ncf_plan_destroy(ncf_plan *plan) {
     if (!plan) return;

@@ -176,7 +176,9 @@ namespace ncf {
 // Runs set() once per device for one call site: kernel attributes such as the
 // dynamic shared-memory limit belong to a device, and call sites are reached from
 // several threads (the server's slots).  Two threads may both run set() the first
-// time; it only repeats the same idempotent settings.
+// time; it only repeats the same idempotent settings.  set() returns whether every
+// setting took; a device is marked done only then, so a failed setting is tried
+// again on the next call (and the launch after it reports the error).
 template <typename F>
 inline void once_per_device(std::atomic<unsigned long long> &done, F &&set) {
     int dev = 0;
@@ -186,8 +188,12 @@ inline void once_per_device(std::atomic<unsigned long long> &done, F &&set) {
     }
     const unsigned long long bit = 1ull << dev;
     if (done.load(std::memory_order_acquire) & bit) return;
-    set();
-    done.fetch_or(bit, std::memory_order_release);
+    if (set()) done.fetch_or(bit, std::memory_order_release);
+}
+// the dynamic shared-memory limit of one kernel; true when it took
+template <typename K>
+inline bool set_smem_limit(K *kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
 }
 }  // namespace ncf
 

@@ -1,5 +1,5 @@
-// fft.cuh -- complex helpers and the Stockham radix-2/4/8 butterflies shared
-// by the global-memory FFT passes and the shared-memory per-series FFT.
+// fft.cuh -- complex helpers and the Stockham radix-2/4/8 butterflies of the
+// global-memory FFT passes (one launch per pass over every grid of a batch).
 //
 // Convention: G_k = sum_l g_l exp(+2 pi i k l / n) (the sign that maps spread
 // samples at phase u to sum_j z_j exp(+2 pi i m u_j), Eq. nufft_type1).

@@ -961,11 +961,8 @@ ncf_status rect_launch(const RectArgs &a, const RectPrepared &r, cudaStream_t st
     static std::atomic<unsigned long long> attr_done{0};
     const size_t smem = sizeof(RectSmem);
     once_per_device(attr_done, [&] {
-        cudaFuncSetAttribute(rect_scan_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(rect_scan_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(rect_scan_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(rect_scan_pt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(PtSmem));
+        return set_smem_limit(rect_scan_kernel<16>, smem) & set_smem_limit(rect_scan_kernel<32>, smem) &
+               set_smem_limit(rect_scan_kernel<64>, smem) & set_smem_limit(rect_scan_pt_kernel, sizeof(PtSmem));
     });
 #define NCF_RECT_SCAN(RUN)                                                                              \
     NCF_LAUNCH("rect_scan_kernel", st,                                                                 \

@@ -59,12 +59,18 @@ __device__ __forceinline__ double cos_half_range(double x) {
 constexpr double kExpInvL = 369.3299304675746;         // 256 / ln 2
 constexpr double kExpC = 0x1.62e42fefa39efp-9;        // fl(ln2 / 256)
 constexpr int kExpTable = 256;
-// below N = -1021 * 256 (z < -707.7) the weight is returned as 0: above it the
-// result and every intermediate stay normal numbers
+// Below N = -1021 * 256 (z < -707.7) the weight is returned as 0: above it the
+// result and every intermediate stay normal numbers.  The test reads all 64 bits
+// of nd: while N >= -2^51, nd = 1.5 2^52 + N exactly and its bit pattern, read as
+// an integer, is 0x4338000000000000 + N; any smaller nd (more negative z, down to
+// -inf) has a smaller pattern (or a negative one), so the guard holds for every
+// z <= 0.  A test on the low word alone would wrap once |N| >= 2^31
+// (|z| > 5.8e6, a pair 3400 h from the centre under a wide window).
+constexpr long long kExpFloor = 0x4338000000000000ll - 1021ll * kExpTable;
 __device__ __forceinline__ double exp_neg(double z, const double *__restrict__ T) {
     const double nd = fma(z, kExpInvL, 0x1.8p52);       // N in the low bits
+    if (__double_as_longlong(nd) < kExpFloor) return 0.0;
     const int n = (int)__double2loint(nd);
-    if (n < -1021 * kExpTable) return 0.0;
     const double N = nd - 0x1.8p52;
     const double r = fma(-N, kExpC, z);
     const double p = r * fma(r, fma(r, fma(r, 1.0 / 24.0, 1.0 / 6.0), 0.5), 1.0);

@@ -745,8 +745,7 @@ ncf_status launch_typed(const SpectralArgs &a, const SpectralPrepared &p, char *
     constexpr size_t smem = spread_smem_bytes<R>();
     static std::atomic<unsigned long long> attr_done{0};
     once_per_device(attr_done, [&] {
-        cudaFuncSetAttribute(spread_kernel<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(spread_kernel<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return set_smem_limit(spread_kernel<R, 8>, smem) & set_smem_limit(spread_kernel<R, 16>, smem);
     });
     EsPoly<R, 8, PolyDeg<8>::D> poly8{};
     EsPoly<R, 16, PolyDeg<16>::D> poly16{};
@@ -1050,9 +1049,7 @@ void paper_modes_run(const PaperModes &pm, const SpecSide &x, const SpecSide *y,
     up(bf.lagw, paper_lagrange_weights().data(), (size_t)kPhiStep * kPhiTaps * 8);
     constexpr size_t smem = spread_smem_bytes<double>();
     static std::atomic<unsigned long long> attr_done{0};
-    once_per_device(attr_done, [&] {
-        cudaFuncSetAttribute(spread_kernel<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    });
+    once_per_device(attr_done, [&] { return set_smem_limit(spread_kernel<double, 16>, smem); });
     EsPoly<double, 16, PolyDeg<16>::D> poly{};
     for (size_t i = 0; i < pm.poly.size(); ++i) poly.c[i] = pm.poly[i];
     const double a_scale = (double)pm.nf / pm.L;

@@ -260,9 +260,7 @@ void launch_contract_tc(const float *Anum, const float *Aden, const float *E, in
                         int64_t Kp, double *acc_num, double *acc_den, int *status, cudaStream_t st) {
     static std::atomic<unsigned long long> attr_done{0};
     const size_t smem = contract_tc_smem_bytes();
-    once_per_device(attr_done, [&] {
-        cudaFuncSetAttribute(contract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    });
+    once_per_device(attr_done, [&] { return set_smem_limit(contract_tc_kernel, smem); });
     dim3 grid((unsigned)((B + kTcM - 1) / kTcM), (unsigned)((Kp + kTcN - 1) / kTcN),
               (unsigned)((M2 + kChunkModes - 1) / kChunkModes));
     NCF_LAUNCH("contract_tc_kernel", st,

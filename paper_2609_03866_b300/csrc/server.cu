@@ -65,39 +65,27 @@ struct Slot {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Upper estimate of the device memory one request needs (inputs, outputs and
-// the context workspace of its path), read from its host buffers; used for
-// admission against the server's budget.
+// Device memory one request needs: the slot buffer of run_one (its own copies of
+// the inputs, its lags and outputs) plus the context workspace of its ncf_corr
+// call, sized by ncf_workspace_bytes from the request's sizes, time span and
+// largest lag before anything is allocated; used for admission against the
+// server's budget.  A request whose sizes the library refuses is charged its
+// buffers only: ncf_corr then rejects it before allocating.
 size_t estimate_bytes(const ncf_request &r, const Resident *rx, const Resident *ry) {
     const bool acf = r.s == nullptr && ry == nullptr;
-    const int64_t nx = rx ? rx->n : r.nx, ny = acf ? 0 : (ry ? ry->n : r.ny);
-    const double n = (double)nx + (double)ny;
-    const double copied = (double)(rx ? 0 : nx) + (double)(ry ? 0 : ny);
-    const double K = (double)r.K;
-    double bytes = 16.0 * copied + 32.0 * K + 64.0 * n + 4096.0;  // inputs, outputs, statistics, keys, tables
-    const bool sinc = r.opt.kernel == NCF_RECTANGLE && r.opt.path == NCF_PATH_SPECTRAL;
-    const bool spectral = (r.opt.kernel == NCF_GAUSSIAN && r.opt.path != NCF_PATH_WINDOWED) || sinc;
-    if (spectral) {
-        double lo = rx ? rx->t_first : r.t[0], hi = rx ? rx->t_last : r.t[nx - 1];
-        if (!acf) {
-            lo = std::min(lo, ry ? ry->t_first : r.s[0]);
-            hi = std::max(hi, ry ? ry->t_last : r.s[ny - 1]);
-        }
-        double max_tau = 0.0;
-        for (int64_t k = 0; k < r.K; ++k) max_tau = std::max(max_tau, std::fabs(r.lags[k]));
-        const bool fp32 = r.opt.precision == NCF_FP32;
-        const double h = r.opt.h > 0.0 ? r.opt.h : 1.0;
-        const double L = (hi - lo) + max_tau + 9.0 * h;
-        // the spectral-sinc rectangle keeps L / (h tol) modes
-        const double M = sinc ? L / (h * (r.opt.tol > 0.0 ? r.opt.tol : 1e-3)) + 32.0
-                              : L * (fp32 ? 1.09 : 1.41) / h + 32.0;
-        double nf = 16.0;
-        while (nf < 4.0 * M + 16.0) nf *= 2.0;
-        const double cell = fp32 ? 8.0 : 16.0, real = fp32 ? 4.0 : 8.0;
-        const double M2 = acf ? M : 2.0 * M;
-        bytes += nf * cell * (acf ? 2.0 : 3.0) + 2.0 * M2 * real + M2 * (K + 4.0) * real + nf * cell;
+    const int64_t nx = rx ? rx->n : r.nx, ny = acf ? 0 : (ry ? ry->n : r.ny), K = r.K;
+    const int64_t cx = rx ? 0 : nx, cy = ry ? 0 : ny;  // points copied for this request
+    const size_t own = align256(cx * 8) * 2 + align256(cy * 8) * 2 + align256(K * 8) * 4;
+    double lo = rx ? rx->t_first : r.t[0], hi = rx ? rx->t_last : r.t[nx - 1];
+    if (!acf) {
+        lo = std::min(lo, ry ? ry->t_first : r.s[0]);
+        hi = std::max(hi, ry ? ry->t_last : r.s[ny - 1]);
     }
-    return align256((size_t)bytes);
+    double max_tau = 0.0;
+    for (int64_t k = 0; k < K; ++k) max_tau = std::max(max_tau, std::fabs(r.lags[k]));
+    size_t ws = 0;
+    if (ncf_workspace_bytes(nullptr, nx, ny, 1, K, hi - lo, max_tau, &r.opt, &ws, nullptr) != NCF_OK) ws = 0;
+    return own + ws;
 }
 
 }  // namespace

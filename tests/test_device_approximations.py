@@ -18,6 +18,8 @@ mp.mp.dps = 40
 
 
 def fma(a, b, c):
+    if not all(math.isfinite(v) for v in (a, b, c)):
+        return a * b + c
     return float(Fraction(a) * Fraction(b) + Fraction(c))
 
 
@@ -63,12 +65,17 @@ def test_exp_neg_within_1p5_ulp_near_the_peak_and_1p3e16_absolute():
     def ll2d(v):
         return struct.unpack("<d", struct.pack("<q", v))[0]
 
+    src = _src()
+    assert "constexpr long long kExpFloor = 0x4338000000000000ll - 1021ll * kExpTable;" in src
+    assert "if (__double_as_longlong(nd) < kExpFloor) return 0.0;" in src
+    floor = 0x4338000000000000 - 1021 * 256
+
     def exp_neg(z):
         nd = fma(z, inv_l, magic)
+        if d2ll(nd) < floor:
+            return 0.0
         n = d2ll(nd) & 0xFFFFFFFF
         n = n - (1 << 32) if n >= 1 << 31 else n
-        if n < -1021 * 256:
-            return 0.0
         N = nd - magic
         r = fma(-N, c, z)
         p = r * fma(r, fma(r, fma(r, 1.0 / 24.0, 1.0 / 6.0), 0.5), 1.0)
@@ -84,3 +91,12 @@ def test_exp_neg_within_1p5_ulp_near_the_peak_and_1p3e16_absolute():
     assert worst_ulp < 1.5, worst_ulp
     assert worst_abs < 1.3e-16, worst_abs
     assert exp_neg(-800.0) == 0.0
+    # far from the window centre (a wide or untruncated window): d / h = 3500, 4000,
+    # 6000 and beyond, where a guard on the low word alone would wrap
+    for d in (3500.0, 4000.0, 6000.0, 1e5, 1e150):
+        assert exp_neg(-d * d / 2.0) == 0.0, d
+    assert exp_neg(-math.inf) == 0.0
+    # the last arguments above the floor still give the exponential (relative error
+    # below |z| 3.4e-17 from the reduction, plus the polynomial's and the table's)
+    for z in (-707.0, -700.0):
+        assert abs(exp_neg(z) / float(mp.e ** z) - 1.0) < 5e-14, z

@@ -98,6 +98,19 @@ def test_gaussian_windowed_very_wide_window_underflows_to_zero_weights():
     assert max_abs(got["c"], full["c"]) < TOL
 
 
+@pytest.mark.parametrize("R", [1e4, float("inf")])
+def test_gaussian_windowed_untruncated_window_far_pairs_weigh_zero(R):
+    """A window far wider than the series (pairs up to 2e4 h apart, z down to -2e8):
+    every far pair must weigh 0, so the result equals the untruncated definition.
+    With h = 0.05 d the AR(1) series spans 2e4 h."""
+    w = synth.ar1_acf()
+    ref = oracle.corr(w.t, w.x, w.lags, "gaussian", 0.05)
+    got = gpu(w.t, w.x, w.lags, kernel="gaussian", h=0.05, path="windowed", trunc_R=R)
+    assert max_abs(got["c"], ref["c"]) < TOL
+    assert np.max(np.abs(got["b"] - ref["b"]) / ref["b"]) < 1e-12
+    assert np.all(np.isfinite(got["c"])) and np.all(got["b"] > 0)
+
+
 def test_gaussian_windowed_paper_window_counts_exact():
     w = synth.ou_ccf(nA=4000, nB=3000, K=41)
     ref = oracle.corr(w.t, w.x, w.lags, "gaussian", 0.5, s=w.s, y=w.y, trunc_R=6, method="windowed")
