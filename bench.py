@@ -9,16 +9,22 @@ nightly cadence with seasonal and weather gaps; shared 256-lag grid on
 [0, 200] d; Gaussian kernel h = 0.5 d and rectangle half-width 0.5 d.
 
 A step is the whole hot path over the batch: the Gaussian ACFs through the
-batched FP32 form (spreading, FFT, spectra, mode-to-lag contraction) and the
-rectangle ACFs through the exact pair-count scan, each with its statistics
-pass and normalisation.  Series-lags per step = 2 * 4096 * 256.
+batched FP32 form (statistics, spreading, FFT, spectra, mode-to-lag
+contraction on tensor cores) and the rectangle ACFs through the exact
+pair-count scan, each with its statistics pass and normalisation.  Each is a
+plan (analysis done once) whose launches are captured in a CUDA graph; a step
+replays both graphs.  Series-lags per step = 2 * 4096 * 256 (one per estimator).
 
-One JSON line is printed (rank 0): the device-timed throughput (`value`), the
-same metric end to end through the host-buffer C call that evaluates both
-estimators from one upload of the batch (`e2e`), the plain FP64
-GPU path on the same batch (`fp64_plain`), accuracy against the FP64 oracle on
-sampled series, the roofline of the dominant kernel, and the oracle timed on
-this host's cores (`cpu_baseline`).  `--impl reference` times only the oracle.
+One JSON line is printed (rank 0): the device-timed throughput (`value`) and
+each estimator's own rate; the same metric end to end through the host-buffer
+C call that evaluates both estimators from one upload of the batch (`e2e`);
+the spec comparison of the FP32 form with the plain FP64 GPU path (the
+faster of the FP64 spectral and FP64 windowed paths) on the Gaussian, with the
+FP32 form's error on every value; accuracy against the FP64 oracle on sampled
+series; the roofline of the dominant kernel; the single-series FP64 ACF and the
+10^7-point MJD-offset precision workloads; serving; the library's device
+memory high-water mark; and the oracle timed on this host's cores
+(`cpu_baseline`).  `--impl reference` times only the oracle.
 """
 from __future__ import annotations
 
@@ -38,7 +44,8 @@ sys.path.insert(0, ROOT)
 B_SERIES = 4096
 K_LAGS = 256
 H = 0.5
-METRIC = "series*lags/s, batched FP32 form (Gaussian) + exact rectangle scan, 4096 light curves x 256 lags"
+METRIC = ("series*lags/s, batched FP32 form (Gaussian) + exact rectangle scan, 4096 light curves x 256 lags, "
+          "one series*lag per estimator")
 WORKLOAD = "light_curves: 4096 series, n log-uniform [200, 2e5], 256 lags on [0, 200] d, Gaussian h=0.5 + rectangle h=0.5"
 
 
@@ -47,6 +54,15 @@ WORKLOAD = "light_curves: 4096 series, n log-uniform [200, 2e5], 256 lags on [0,
 # this command.  Reported as the roofline's traffic only for that workload; update or
 # remove an entry whenever its kernel changes.
 MEASURED_TRAFFIC = {("rect_scan_pt_kernel", 4096): 3.02e9 + 31.02e6}
+
+
+# Integer rates of this GPU measured by a probe of independent instruction chains
+# (ops per clock per SM): IADD3 120 (full rate), LOP3 / SHF / IMAD / IMAD.WIDE 60
+# (half rate).  The scan's 16 algorithmic int32 operations per item are 8 of each
+# kind (the 64-bit adds and differences full rate; the compares and the limb
+# multiply-adds half rate): 8/120 + 8/60 = 0.2 clock per item per SM, i.e. 80
+# operations per clock per SM.
+INT_OPS_PER_CLK_SM = 80.0
 
 
 def peaks():
@@ -341,6 +357,138 @@ def paper_run(api, device, h=0.5):
     return out
 
 
+def fp64_plain_run(api, ctx, stream, w, offs, t, x, lags, out_g, c32, g_ms, world):
+    """The spec comparison on the Gaussian: the FP32 form against the plain
+    FP64 GPU path, the faster of (i) the FP64 spectral path on the whole batch and
+    (ii) the FP64 windowed path (8h window), timed on 16 series at evenly spaced
+    size ranks and extrapolated to the batch by its work (points x lags x points
+    in the window, the cost model of the windowed scan).  The FP32 form's error is
+    taken against the FP64 spectral result on every value of the batch."""
+    import torch
+    B, K = w.B, lags.numel()
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    spec_ms = timed(lambda: api.corr_batch(offs, t, x, lags, kernel="gaussian", h=H, path="spectral",
+                                           precision="fp64", ctx=ctx, stream=stream, out=out_g))
+    c64 = out_g["c"].clone()
+    diff = (c32 - c64).abs()
+    # windowed: a sample of series at evenly spaced size ranks
+    n = np.diff(offs)
+    span = np.array([w.t[offs[b + 1] - 1] - w.t[offs[b]] for b in range(B)])
+    R = 8.0
+    work = n.astype(np.float64) * K * np.minimum(n, n / np.maximum(span, 1e-300) * 2 * R * H + 1)
+    rank = np.argsort(n)
+    sample = rank[np.linspace(0, B - 1, 16).astype(int)]
+    so = np.concatenate([[0], np.cumsum(n[sample])]).astype(np.int64)
+    ts = np.concatenate([w.t[offs[b]:offs[b + 1]] for b in sample])
+    xs = np.concatenate([w.x[offs[b]:offs[b + 1]] for b in sample])
+    dev = t.device
+    tsd, xsd = torch.from_numpy(ts).to(dev), torch.from_numpy(xs).to(dev)
+    win_sample_ms = timed(lambda: api.corr_batch(so, tsd, xsd, lags, kernel="gaussian", h=H, path="windowed",
+                                                 precision="fp64", trunc_R=R, ctx=ctx, stream=stream), reps=1)
+    win_ms = win_sample_ms * work.sum() / work[sample].sum()
+    plain_ms = min(spec_ms, win_ms)
+    return {
+        "gaussian_fp32_form": {"ms": g_ms, "value": B * K * world / (g_ms / 1e3), "unit": "series*lags/s",
+                               "max_abs_err_vs_fp64_every_value": float(diff.max().item()),
+                               "rms_err_vs_fp64": float(diff.pow(2).mean().sqrt().item()),
+                               "values_compared": int(diff.numel())},
+        "plain_fp64_gpu_path": {"ms": plain_ms, "value": B * K * world / (plain_ms / 1e3),
+                                "unit": "series*lags/s",
+                                "path": "FP64 spectral" if spec_ms <= win_ms else "FP64 windowed (extrapolated)"},
+        "fp64_spectral_ms": spec_ms,
+        "fp64_windowed_ms_extrapolated": win_ms,
+        "fp64_windowed_sample": {"series": int(len(sample)), "points": int(n[sample].sum()), "ms": win_sample_ms,
+                                 "share_of_batch_work": float(work[sample].sum() / work.sum())},
+        "speedup_fp32_form": plain_ms / g_ms,
+        "target": "FP32 form within 1e-5 of FP64 on every value and faster than the plain FP64 GPU path",
+        "met": bool(diff.max().item() <= 1e-5 and g_ms < plain_ms),
+    }
+
+
+def single_acf_run(api, device):
+    """A single ACF in FP64: AR(1) (phi = 0.9) at 2000 uniform times on [0, 1000] d,
+    50 lags on [0, 100] d; Gaussian h = 1 (path chosen by the cost model) and
+    rectangle half-width 1; every value against the oracle's direct double sum,
+    counts exactly."""
+    import torch
+    import oracle
+    from paper_2609_03866_b300 import synth
+    w = synth.ar1_acf(n=2000, K=50)
+    dev = torch.device("cuda", device)
+    t, x, lags = (torch.from_numpy(a).to(dev) for a in (w.t, w.x, w.lags))
+    ctx = api.Context(device)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for kernel in ("gaussian", "rectangle"):
+        call = lambda: api.corr(t, x, lags, kernel=kernel, h=1.0, ctx=ctx, stream=stream)
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            r = call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        ref = oracle.corr(w.t, w.x, w.lags, kernel, 1.0)
+        got = {k: v.cpu().numpy() for k, v in r.items()}
+        d = {"ms": ms, "value": w.lags.size / (ms / 1e3), "unit": "series*lags/s",
+             "max_abs_err_vs_oracle": float(np.max(np.abs(got["c"] - ref["c"]))), "tolerance": 1e-10}
+        if kernel == "rectangle":
+            d["counts_bit_exact"] = bool(np.array_equal(got["count"], ref["count"]))
+        out[kernel] = d
+    ctx.close()
+    out["workload"] = "AR(1) phi = 0.9, n = 2000 on [0, 1000] d, 50 lags on [0, 100] d, h = 1 (one call, FP64)"
+    return out
+
+
+def precision_run(api, device, h=0.1):
+    """The precision workload: one ACF of 10^7 points at times 60000 + U[0, 20000] d
+    (MJD scale), an OU-modulated 27-d sinusoid plus flicker noise, 1000 lags on
+    [0, 200] d, Gaussian h = 0.1 d: the FP32 form (FP32 spreading and FFT, tensor-
+    core lag evaluation) against the FP64 spectral path on every lag."""
+    import torch
+    from paper_2609_03866_b300 import synth
+    w = synth.quasi_periodic(n=10_000_000, K=1000)
+    dev = torch.device("cuda", device)
+    t, x, lags = (torch.from_numpy(a).to(dev) for a in (w.t, w.x, w.lags))
+    ctx = api.Context(device)
+    stream = torch.cuda.current_stream(dev)
+    res, ms = {}, {}
+    for prec in ("fp32", "fp64"):
+        call = lambda: api.corr(t, x, lags, kernel="gaussian", h=h, path="spectral", precision=prec, ctx=ctx,
+                                stream=stream)
+        call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res[prec] = call()["c"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms[prec] = e0.elapsed_time(e1)
+    d = (res["fp32"] - res["fp64"]).abs()
+    plan = ctx.last_plan()
+    ctx.close()
+    return {"workload": "10^7 points at 60000 + U[0, 20000] d, 1000 lags on [0, 200] d, Gaussian h = 0.1 d",
+            "fp32_form_ms": ms["fp32"], "fp64_ms": ms["fp64"],
+            "fp32_form_value": 1000 / (ms["fp32"] / 1e3), "fp64_value": 1000 / (ms["fp64"] / 1e3),
+            "unit": "series*lags/s", "max_abs_diff_fp32_vs_fp64": float(d.max().item()),
+            "rms_abs_diff_fp32_vs_fp64": float(d.pow(2).mean().sqrt().item()), "lags_compared": int(d.numel()),
+            "grid": plan["grid"], "modes": plan["modes"]}
+
+
 def serve_pool(n_pool=32, n_lo=1_000, n_hi=5_000_000, seed=11):
     """Request templates of the serving mix: half ACF light curves, half seasonal OU
     CCFs (n_B = 0.8 n_A); n log-uniform in [n_lo, n_hi]; K in {64, 256, 1024};
@@ -365,27 +513,45 @@ def serve_pool(n_pool=32, n_lo=1_000, n_hi=5_000_000, seed=11):
     return pool
 
 
-def serve_run(api, device, n_req=160, slots=4, seed=11):
+def serve_run(api, device, n_req=5000, slots=4, seed=11):
     """Request stream through the serving loop.  A closed loop (slots requests
     kept in flight) gives the saturation throughput; open Poisson streams at 0.5,
     0.8 and 1.0 of it give the latency a client sees (queueing on the client
-    while no slot is free + the server's submit-to-done time)."""
+    while no slot is free + the server's submit-to-done time).  Every template's
+    series are also resident on the device; half the requests name them by
+    handle, the other half send their host arrays and pay their own upload."""
     rng = np.random.default_rng(seed)
     pool = serve_pool(seed=seed)
     order = rng.integers(0, len(pool), size=n_req)
-    srv = api.Server(device=device, slots=slots, mem_budget_bytes=24 << 30)
-    # the series are resident: uploaded once, named by handle in every request
-    reqs = []
+    host = rng.random(n_req) < 0.5
+    srv = api.Server(device=device, slots=slots, mem_budget_bytes=48 << 30)
+    reqs, hreqs = [], []
     for r in pool:
         q = {k: v for k, v in r.items() if k not in ("t", "x", "s", "y")}
         q["x_series"] = srv.put(r["t"], r["x"])
         if "s" in r:
             q["y_series"] = srv.put(r["s"], r["y"])
         reqs.append(q)
+        hreqs.append(dict(r))
 
     def submit(i, block=False):
         while True:
-            r = dict(reqs[int(order[i % n_req])] if i >= 0 else reqs[-1 - i])
+            if i >= 0:
+                j = int(order[i % n_req])
+                r = dict(hreqs[j] if host[i % n_req] else reqs[j])
+            else:
+                r = dict(reqs[-1 - i])
+            if "x_series" not in r:
+                t_, x_ = r.pop("t"), r.pop("x")
+                try:
+                    return srv.submit(t_, x_, r.pop("lags"), **r)
+                except api.NcfError as e:
+                    if e.status != api.Server.EBUSY:
+                        raise
+                    if not block:
+                        return None
+                    time.sleep(1e-3)
+                    continue
             try:
                 return srv.submit(None, None, r.pop("lags"), **r)
             except api.NcfError as e:
@@ -437,14 +603,16 @@ def serve_run(api, device, n_req=160, slots=4, seed=11):
                 time.sleep(50e-6)
         span = time.perf_counter() - t0
         loads.append({"offered": load, "offered_per_s": load * rate, "achieved_per_s": n_req / span,
-                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))})
+                      "samples": len(lat), "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99))})
     srv.close()
-    return {"requests": n_req, "slots": slots, "saturation_requests_per_s": rate,
+    return {"requests_per_level": n_req, "slots": slots, "saturation_requests_per_s": rate,
             "value": done_k / dt_closed, "unit": "series*lags/s", "loads": loads,
-            "p50_ms": loads[1]["p50_ms"], "p99_ms": loads[1]["p99_ms"],
+            "p50_ms": loads[1]["p50_ms"], "p99_ms": loads[1]["p99_ms"], "latency_samples": loads[1]["samples"],
             "mix": "50% ACF light curves / 50% OU CCF (n_B = 0.8 n_A), n log-uniform [1e3, 5e6], "
                    "K in {64, 256, 1024}, Gaussian FP32 form or rectangle exact scan, h = 0.5; "
-                   "requests drawn from 32 seeded templates whose series are resident on the device"}
+                   "requests drawn from 32 seeded templates; half name device-resident series, "
+                   f"half send host arrays and pay their upload ({int(host.sum())} of {n_req})"}
 
 def main():
     ap = argparse.ArgumentParser()
@@ -500,73 +668,84 @@ def main():
     out_r = {"c": torch.empty(B, K, dtype=torch.float64, device=dev),
              "b": torch.empty(B, K, dtype=torch.float64, device=dev),
              "count": torch.empty(B, K, dtype=torch.int64, device=dev)}
+    G_OPT = dict(kernel="gaussian", h=H, path="spectral", precision="fp32")
+    R_OPT = dict(kernel="rectangle", h=H)
 
-    def step(prec="fp32"):
-        api.corr_batch(offs, t, x, lags, kernel="gaussian", h=H, path="spectral", precision=prec,
-                       ctx=ctx, stream=stream, out=out_g)
-        api.corr_batch(offs, t, x, lags, kernel="rectangle", h=H, ctx=ctx, stream=stream, out=out_r)
-
+    # ---- the step: one plan per estimator, its launches captured in a CUDA graph ----
+    plan_g = api.Plan(offs, t, x, lags, **G_OPT, ctx=ctx, stream=stream)
+    plan_r = api.Plan(offs, t, x, lags, **R_OPT, ctx=ctx, stream=stream)
     for _ in range(max(args.warmup, 3)):
-        step()
+        plan_g.execute(t, x, out=out_g, stream=stream)
+        plan_r.execute(t, x, out=out_r, stream=stream)
+    torch.cuda.synchronize()
+    graphs, graph_launches = [], 0
+    cs = torch.cuda.Stream(dev)
+    cs.wait_stream(stream)
+    for plan, out in ((plan_g, out_g), (plan_r, out_r)):
+        g = torch.cuda.CUDAGraph()
+        l0 = ctx.launches
+        with torch.cuda.stream(cs):
+            with torch.cuda.graph(g, stream=cs):
+                plan.execute(t, x, out=out, stream=cs)
+        graph_launches += ctx.launches - l0
+        graphs.append(g)
+    torch.cuda.synchronize()
+    for _ in range(max(args.warmup, 3)):
+        for g in graphs:
+            g.replay()
     torch.cuda.synchronize()
     plan = ctx.last_plan()
 
-    # ---- timed region ----
-    ctx.profile(True)
-    ctx.profile_reset()
-    l0 = ctx.launches
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    # ---- timed region: graph replays, an event between the two estimators ----
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
         ev[0].record(stream)
-        for s in range(args.steps):
-            step()
-            ev[s + 1].record(stream)
+        for s_ in range(args.steps):
+            graphs[0].replay()
+            ev[2 * s_ + 1].record(stream)
+            graphs[1].replay()
+            ev[2 * s_ + 2].record(stream)
         torch.cuda.synchronize()
         barrier()
-    launches = ctx.launches - l0
-    prof = ctx.profile_report()
-    ctx.profile(False)
-    step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
+    launches = graph_launches * args.steps
+    step_ms = [ev[2 * s_].elapsed_time(ev[2 * s_ + 2]) for s_ in range(args.steps)]
+    g_ms = float(np.mean([ev[2 * s_].elapsed_time(ev[2 * s_ + 1]) for s_ in range(args.steps)]))
+    r_ms = float(np.mean([ev[2 * s_ + 1].elapsed_time(ev[2 * s_ + 2]) for s_ in range(args.steps)]))
     total_ms = ev[0].elapsed_time(ev[-1])
     total_ms = shard.max_over_ranks(total_ms, device=dev)
     units = 2.0 * B * K * args.steps * world
     value = units / (total_ms / 1e3)
-
     c32 = out_g["c"].clone()
     counts = out_r["count"].clone()
     rect_c = out_r["c"].clone()
+    if plan_g.status() != 0 or plan_r.status() != 0:
+        raise RuntimeError("a plan's device guard flagged the benchmark data")
 
-    # ---- plain FP64 GPU path on the same batch ----
+    # ---- the same step through one call for both estimators (one statistics pass),
+    # with the kernel profiler (shares, roofline) ----
+    def step():
+        api.corr_batch_multi(offs, t, x, lags, [G_OPT, R_OPT], ctx=ctx, stream=stream, outs=[out_g, out_r])
+
+    step()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_reset()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prof = ctx.profile_report()
+    ctx.profile(False)
+    one_shot_ms = p0.elapsed_time(p1) / args.steps
+
+    # ---- spec comparison: FP32 form vs the plain FP64 GPU path, Gaussian ----
     fp64 = None
     if not args.no_fp64:
-        step("fp64")
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step("fp64")
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        c64 = out_g["c"].clone()
-
-        def gauss_ms(prec):
-            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            g0.record(stream)
-            for _ in range(3):
-                api.corr_batch(offs, t, x, lags, kernel="gaussian", h=H, path="spectral", precision=prec,
-                               ctx=ctx, stream=stream, out=out_g)
-            g1.record(stream)
-            torch.cuda.synchronize()
-            return g0.elapsed_time(g1) / 3
-
-        g32, g64 = gauss_ms("fp32"), gauss_ms("fp64")
-        fp64 = {"value": 2.0 * B * K * world / (ms64 / 1e3), "unit": "series*lags/s", "ms_per_step": ms64,
-                "path": "FP64 spectral (Gaussian) + exact scan (rectangle)",
-                "max_abs_diff_fp32_vs_fp64": float((c32 - c64).abs().max().item()),
-                "speedup_fp32_form": (ms64 / (total_ms / args.steps)),
-                "gaussian_only_ms": {"fp32_form": g32, "fp64": g64, "speedup": g64 / g32}}
+        fp64 = fp64_plain_run(api, ctx, stream, w, offs, t, x, lags, out_g, c32, g_ms, world)
 
     # ---- end to end through the host-buffer C call ----
     e2e = None
@@ -579,7 +758,7 @@ def main():
                "count": torch.empty(B, K, dtype=torch.int64).pin_memory()}
 
         # both estimators of the step from one upload of the batch (ncf_corr_batch_host_multi)
-        hopts = [dict(kernel="gaussian", h=H, path="spectral", precision="fp32"), dict(kernel="rectangle", h=H)]
+        hopts = [dict(G_OPT), dict(R_OPT)]
 
         def hstep():
             api.corr_batch_host_multi(offs, th, xh, lh, hopts, ctx=ctx, stream=stream, outs=[og, orr])
@@ -598,6 +777,17 @@ def main():
         e2e = {"value": 2.0 * B * K * n_e2e * world / dt, "unit": "series*lags/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
 
+    mem = {"context_workspace_high_water_bytes": ctx.device_bytes,
+           "plan_bytes": {"gaussian_fp32_form": plan_g.device_bytes, "rectangle_exact_scan": plan_r.device_bytes},
+           "workspace_bound_bytes": {
+               "gaussian_fp32_form": api.workspace_bytes(int(offs[-1]), B, K, float(max(
+                   w.t[offs[b + 1] - 1] - w.t[offs[b]] for b in range(B))), float(np.max(np.abs(w.lags))), **G_OPT)[0],
+               "rectangle_exact_scan": api.workspace_bytes(int(offs[-1]), B, K, 0.0, float(np.max(np.abs(w.lags))),
+                                                           **R_OPT)[0]},
+           "inputs_bytes": int(w.t.nbytes + w.x.nbytes + w.lags.nbytes)}
+    plan_g.close()
+    plan_r.close()
+
     serve = None
     if not args.no_serve:
         serve = serve_run(api, local)
@@ -605,6 +795,8 @@ def main():
     regular = None if args.no_serve else regular_run(api, local)
     hanning = None if args.no_serve else hanning_run(api, local)
     paper = None if args.no_serve else paper_run(api, local)
+    single = None if args.no_serve else single_acf_run(api, local)
+    precision = None if args.no_serve else precision_run(api, local)
 
     if rank != 0:
         if world > 1:
@@ -630,7 +822,7 @@ def main():
                "sample": f"{len(series)} random series x {len(lag_idx)} of 256 lags, both kernels, "
                          f"FP64 windowed scan; {secs:.1f} s"}
 
-    # ---- roofline of the dominant kernel ----
+    # ---- roofline of the dominant kernel (profiled one-shot steps) ----
     hbm, tc_peak, src = peaks()
     n_pts = int(offs[-1])
     items = n_pts * K  # outer points x lags of the rectangle scan
@@ -642,12 +834,14 @@ def main():
     if name.startswith("rect_scan"):
         # integer ALU: 16 int32 operations per (outer point, lag) item (two
         # 64-bit bound adds, two 64-bit window compares, one 64-bit window
-        # difference, one 64x64->128-bit multiply-accumulate)
+        # difference, one 64x64->128-bit multiply-accumulate), against the
+        # measured integer rates for that mix (INT_OPS_PER_CLK_SM)
         ops = 16.0 * items / (nl / args.steps)
-        peak_ops = 148 * 128 * 2032e6
+        peak_ops = 148 * INT_OPS_PER_CLK_SM * 2032e6
         roof = {"bound": "alu", "achieved": ops / per_launch_s / 1e12, "peak": peak_ops / 1e12,
                 "unit": "Tint32op/s", "frac": ops / per_launch_s / peak_ops, "traffic": None,
-                "kernel": name, "peak_source": "148 SM x 128 INT32 lanes x 2.032 GHz"}
+                "kernel": name, "peak_source": "measured integer rates: IADD3 120, LOP3/SHF/IMAD 60 ops per clock "
+                                               "per SM; the item's 8 + 8 ops at 80 per clock, 148 SM x 2.032 GHz"}
     elif name == "spread_kernel":
         byts = (16.0 * n_pts + 8.0 * B * nf) / (nl / args.steps)
         roof = {"bound": "hbm", "achieved": byts / per_launch_s / 1e9, "peak": hbm, "unit": "GB/s",
@@ -673,13 +867,19 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "B": B, "K": K, "points": n_pts, "h": H,
-                   "grid": nf, "modes": M, "period_d": plan["period"],
+                   "grid": nf, "modes": M, "period_d": plan["period"], "graph": True,
                    "l2": f"inputs larger than L2 ({(w.t.nbytes + w.x.nbytes) / 1e9:.2f} GB per step)"},
+        "per_estimator": {
+            "gaussian_fp32_form": {"ms": g_ms, "value": B * K * world / (g_ms / 1e3), "unit": "series*lags/s"},
+            "rectangle_exact_scan": {"ms": r_ms, "value": B * K * world / (r_ms / 1e3), "unit": "series*lags/s"},
+            "one_call_ms_per_step": one_shot_ms,
+            "one_call": "ncf_corr_batch_multi: both estimators on one statistics pass, host analysis per call"},
         "gpu_launches": int(launches),
+        "device_memory": mem,
         "clocks": clk.summary(),
         "roofline": roof,
         "e2e": e2e,
-        "fp64_plain": fp64,
+        "north_star": fp64,
         "paper_timings": {
             "hardware": "MacBook Pro 2020, 2 GHz quad-core Intel Core i5, 16 GB LPDDR4X (the paper's benchmark machine)",
             "note": "context only: other hardware, single series, K = 366; not the target",
@@ -688,7 +888,7 @@ def main():
             "realspace_rectangle_s_per_point_per_lag": 1.34e-6 / 366,
             "regular_fft_n256000": {"gaussian_s": 0.07, "rectangle_s": 0.04},
             "this_run_s_per_point_per_lag": {
-                "gaussian_fp32_form": (fp64["gaussian_only_ms"]["fp32_form"] / 1e3 / (n_pts * K)) if fp64 else None,
+                "gaussian_fp32_form": g_ms / 1e3 / (n_pts * K),
                 "rectangle_exact_scan": share.get("rect_scan_pt_kernel", share.get("rect_scan_kernel", 0.0))
                 * (total_ms / args.steps) / 1e3 / (n_pts * K)}},
         "serving": serve,
@@ -696,6 +896,8 @@ def main():
         "regular_fft": regular,
         "hanning": hanning,
         "paper_nufft": paper,
+        "single_acf_fp64": single,
+        "precision_mjd_1e7": precision,
         "accuracy": acc,
         "cpu_baseline": cpu,
     }

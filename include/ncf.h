@@ -125,6 +125,11 @@ NCF_API const char *ncf_last_error(const ncf_ctx *ctx);
 NCF_API const char *ncf_status_string(ncf_status s);
 /* Number of kernels this context has launched so far. */
 NCF_API uint64_t ncf_launch_count(const ncf_ctx *ctx);
+/* High-water mark of the device memory the context's workspaces have held (bytes;
+ * workspaces grow on demand and are kept until ncf_destroy).  Plans and servers
+ * report their own memory (ncf_plan_device_bytes, the server's budget).  No
+ * counterpart in the paper: a serving metric. */
+NCF_API size_t ncf_device_bytes(const ncf_ctx *ctx);
 
 /*
  * Geometry of the most recent spectral call on this context: the common
@@ -195,13 +200,76 @@ NCF_API ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, cons
                                double *c_out, double *b_out, int64_t *count_out, void *stream);
 
 /*
+ * ncf_corr_batch with several option sets (estimators) on one batch whose
+ * arrays are already on the device: the per-series statistics (the prior
+ * standardisation step of Algorithms 2, 4, 9 and 10, which does not depend on
+ * the kernel) are computed and validated once, then each option set runs its
+ * own path on them.  Arguments as ncf_corr_batch, with opts[n_opts] and
+ * c_out[o], b_out[o], count_out[o] DEVICE buffers of [B x K] (b_out,
+ * count_out and any of their entries may be NULL).  Every result equals the one
+ * ncf_corr_batch gives for that option set.  Errors as ncf_corr_batch; the
+ * first failing option set ends the call.  n_opts < 1, a NULL opts or a NULL
+ * c_out[o] gives NCF_EINVAL.
+ */
+NCF_API ncf_status ncf_corr_batch_multi(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                                        const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                                        const double *lags, int64_t K, const ncf_options *opts, int n_opts,
+                                        double *const *c_out, double *const *b_out, int64_t *const *count_out,
+                                        void *stream);
+
+/*
+ * One very long series over several GPUs (or several passes of one GPU): the
+ * estimator's sums are additive over the outer points, N_k = sum_j y_j
+ * sum_i x_i b(s_j - t_i - tau_k) (Eq. kernel_estimator), so a series can be cut
+ * into contiguous ranges of its outer points s_j, each evaluated against the
+ * inner points t_i within reach of it (max|tau| plus the kernel's half-width),
+ * and the ranges' partial N_k, B_k and pair counts summed.  Both need the
+ * standardisation of the whole series (Appendix, "Prior standardization"),
+ * pooled from the ranges' own statistics.
+ *
+ * ncf_series_stats runs the statistics pass of ONE series (device t, x, n >= 1
+ * points) and returns, in *out (host): n, the mean, m2 = sum (x - mean)^2
+ * (population variance m2 / n), the first and last times, and validation flags
+ * (nonzero: 1 NaN or Inf present, 2 times decrease).  Pooling ranges a and b:
+ * n = n_a + n_b, mean = mean_a + (mean_b - mean_a) n_b / n,
+ * m2 = m2_a + m2_b + (mean_b - mean_a)^2 n_a n_b / n (Chan, Golub and LeVeque's
+ * pairwise update).  Synchronises `stream`.
+ *
+ * ncf_corr_pooled is ncf_corr with the standardisation taken from *pooled
+ * (the means, population standard deviations and total sizes of the whole
+ * series, pooled as above) instead of from the given points; the given points'
+ * own statistics pass still validates them (a range of constant values is
+ * allowed).  Only NORM_NONE (normalise after summing the ranges); NCF_EINVAL for
+ * means or std that are not finite and positive.  Results and errors otherwise
+ * as ncf_corr; b_out and count_out (the range's B_k and exact pair counts) sum
+ * over the ranges, and N_k = c_k max(B_k, 1e-16).
+ */
+typedef struct {
+    int64_t n;
+    double mean, m2, t_first, t_last;
+    int32_t flags, pad;
+} ncf_series_summary;
+typedef struct {
+    double mean_x, std_x;  /* pooled over every point of the x series */
+    double mean_y, std_y;  /* the y series of a CCF (ignored for an ACF) */
+    int64_t n_x, n_y;      /* total sizes of the series pooled over */
+} ncf_pooled_stats;
+NCF_API ncf_status ncf_series_stats(ncf_ctx *ctx, const double *t, const double *x, int64_t n,
+                                    ncf_series_summary *out, void *stream);
+NCF_API ncf_status ncf_corr_pooled(ncf_ctx *ctx, const double *t, const double *x, int64_t nx,
+                                   const double *s, const double *y, int64_t ny, const double *lags,
+                                   int64_t K, const ncf_options *opt, const ncf_pooled_stats *pooled,
+                                   double *c_out, double *b_out, int64_t *count_out, void *stream);
+
+/*
  * Several estimators of one batch from a single upload.  For example, the
  * Gaussian and the rectangle estimate of the same series (Eq. kernel_estimator
  * with Eq. Gaussian_kernel and Eq. rectangle_kernel).  It works as
  * ncf_corr_batch_host but takes n_opts option sets:
  *   - t, x (s, y) and lags are copied to the device once;
  *   - each chunk of series is evaluated with opts[0], ..., opts[n_opts - 1] in
- *     turn;
+ *     turn, on one statistics pass (the prior standardisation step of
+ *     Algorithms 2, 4, 9 and 10 does not depend on the kernel);
  *   - the results are written to the HOST buffers c_out[o], b_out[o] and
  *     count_out[o], each [B x K].
  * b_out and count_out may be NULL, and so may any of their entries.

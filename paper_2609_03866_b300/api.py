@@ -37,6 +37,17 @@ class ncf_options(ctypes.Structure):
                 ("tol", ctypes.c_double)]
 
 
+class ncf_series_summary(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("mean", ctypes.c_double), ("m2", ctypes.c_double),
+                ("t_first", ctypes.c_double), ("t_last", ctypes.c_double), ("flags", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
+class ncf_pooled_stats(ctypes.Structure):
+    _fields_ = [("mean_x", ctypes.c_double), ("std_x", ctypes.c_double), ("mean_y", ctypes.c_double),
+                ("std_y", ctypes.c_double), ("n_x", ctypes.c_int64), ("n_y", ctypes.c_int64)]
+
+
 class ncf_plan_info(ctypes.Structure):
     _fields_ = [("period", ctypes.c_double), ("modes", ctypes.c_int64), ("grid", ctypes.c_int64),
                 ("width", ctypes.c_int64), ("B", ctypes.c_int64), ("K", ctypes.c_int64)]
@@ -77,6 +88,8 @@ def lib():
             L.ncf_status_string.restype = ctypes.c_char_p
             L.ncf_launch_count.argtypes = [vp]
             L.ncf_launch_count.restype = ctypes.c_uint64
+            L.ncf_device_bytes.argtypes = [vp]
+            L.ncf_device_bytes.restype = ctypes.c_size_t
             L.ncf_last_plan.argtypes = [vp, ctypes.POINTER(ncf_plan_info)]
             L.ncf_last_plan.restype = ctypes.c_int
             L.ncf_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -174,6 +187,11 @@ class Context:
     @property
     def launches(self) -> int:
         return int(lib().ncf_launch_count(self._h))
+
+    @property
+    def device_bytes(self) -> int:
+        """High-water mark of the context's device workspaces (bytes)."""
+        return int(lib().ncf_device_bytes(self._h))
 
     def last_plan(self) -> dict:
         """Geometry of the most recent spectral call (period, modes, grid, width, B, K)."""
@@ -286,6 +304,59 @@ def corr(t, x, lags, kernel="gaussian", h=1.0, s=None, y=None, path="auto", prec
     rc = lib().ncf_corr(ctx.handle, _ptr(t), _ptr(x), t.numel(), _ptr(None if acf else s),
                         _ptr(None if acf else y), 0 if acf else s.numel(), _ptr(lags), K,
                         ctypes.byref(o), _ptr(c), _ptr(b), _ptr(cnt), _stream_handle(stream, dev))
+    ctx.check(rc)
+    return {"c": c, "b": b, "count": cnt}
+
+
+def series_stats(t, x, ctx: Context | None = None, stream=None) -> dict:
+    """Statistics pass of one series on the GPU (ncf_series_stats): n, mean, m2 =
+    sum (x - mean)^2, first and last time, validation flags."""
+    import torch
+    L = lib()
+    if not getattr(L, "_stats_types", False):
+        vp = ctypes.c_void_p
+        L.ncf_series_stats.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(ncf_series_summary), vp]
+        L.ncf_series_stats.restype = ctypes.c_int
+        L._stats_types = True
+    ctx = ctx or default_context()
+    dev = torch.device("cuda", ctx.device)
+    t, x = _dev(t, dev), _dev(x, dev)
+    out = ncf_series_summary()
+    ctx.check(L.ncf_series_stats(ctx.handle, _ptr(t), _ptr(x), t.numel(), ctypes.byref(out),
+                                 _stream_handle(stream, dev)))
+    return {f: getattr(out, f) for f, _ in ncf_series_summary._fields_ if f != "pad"}
+
+
+def corr_pooled(t, x, lags, pooled, kernel="gaussian", h=1.0, s=None, y=None, path="auto", precision="fp64",
+                trunc_R=0.0, tol=0.0, ctx: Context | None = None, stream=None):
+    """ncf_corr with the standardisation of a whole series pooled over its shards
+    (ncf_corr_pooled).  `pooled`: dict(mean_x, std_x, n_x[, mean_y, std_y, n_y]).
+    Returns dict(c, b, count) of device tensors in the order of `lags`."""
+    import torch
+    L = lib()
+    if not getattr(L, "_pooled_types", False):
+        vp = ctypes.c_void_p
+        L.ncf_corr_pooled.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, ctypes.c_int64,
+                                      ctypes.POINTER(ncf_options), ctypes.POINTER(ncf_pooled_stats), vp, vp, vp,
+                                      vp]
+        L.ncf_corr_pooled.restype = ctypes.c_int
+        L._pooled_types = True
+    ctx = ctx or default_context()
+    dev = torch.device("cuda", ctx.device)
+    t, x, lags = _dev(t, dev), _dev(x, dev), _dev(lags, dev)
+    acf = s is None
+    if not acf:
+        s, y = _dev(s, dev), _dev(y, dev)
+    K = lags.numel()
+    c = torch.empty(K, dtype=torch.float64, device=dev)
+    b = torch.empty(K, dtype=torch.float64, device=dev)
+    cnt = torch.empty(K, dtype=torch.int64, device=dev)
+    o = make_options(kernel, h, path, precision, "none", trunc_R, tol)
+    ps = ncf_pooled_stats(float(pooled["mean_x"]), float(pooled["std_x"]), float(pooled.get("mean_y", 0.0)),
+                          float(pooled.get("std_y", 1.0)), int(pooled["n_x"]), int(pooled.get("n_y", 0)))
+    rc = L.ncf_corr_pooled(ctx.handle, _ptr(t), _ptr(x), t.numel(), _ptr(None if acf else s),
+                           _ptr(None if acf else y), 0 if acf else s.numel(), _ptr(lags), K, ctypes.byref(o),
+                           ctypes.byref(ps), _ptr(c), _ptr(b), _ptr(cnt), _stream_handle(stream, dev))
     ctx.check(rc)
     return {"c": c, "b": b, "count": cnt}
 
@@ -519,6 +590,53 @@ def corr_batch_host_multi(offs, t, x, lags, options, offs_y=None, s=None, y=None
     dev = torch.device("cuda", ctx.device)
     rc = L.ncf_corr_batch_host_multi(ctx.handle, pox, _ptr(t), _ptr(x), poy, _ptr(s), _ptr(y), B, _ptr(lags), K,
                                      opts, n, cp, bp, np_, _stream_handle(stream, dev))
+    ctx.check(rc)
+    return outs
+
+
+def corr_batch_multi(offs, t, x, lags, options, offs_y=None, s=None, y=None, ctx: Context | None = None,
+                     stream=None, outs=None):
+    """Several estimators of one batch of device arrays on one statistics pass
+    (ncf_corr_batch_multi).  `options` is a list of dicts of corr_batch's keyword
+    options; returns one dict(c, b, count) of device tensors [B, K] per option
+    set, equal to corr_batch with that set."""
+    import torch
+    L = lib()
+    if not getattr(L, "_dmulti_types", False):
+        vp = ctypes.c_void_p
+        vpp = ctypes.POINTER(ctypes.c_void_p)
+        L.ncf_corr_batch_multi.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp, ctypes.c_int64,
+                                           ctypes.POINTER(ncf_options), ctypes.c_int, vpp, vpp, vpp, vp]
+        L.ncf_corr_batch_multi.restype = ctypes.c_int
+        L._dmulti_types = True
+    n = len(options)
+    if n < 1:
+        raise ValueError("options: at least one option set")
+    ctx = ctx or default_context()
+    dev = torch.device("cuda", ctx.device)
+    t, x, lags = _dev(t, dev), _dev(x, dev), _dev(lags, dev)
+    ox, pox = _host_offs(offs)
+    B = ox.size - 1
+    acf = s is None
+    oy, poy = (None, ctypes.c_void_p(0)) if acf else _host_offs(offs_y)
+    if not acf:
+        s, y = _dev(s, dev), _dev(y, dev)
+    K = lags.numel()
+    if outs is None:
+        outs = [{"c": torch.empty(B, K, dtype=torch.float64, device=dev),
+                 "b": torch.empty(B, K, dtype=torch.float64, device=dev),
+                 "count": torch.empty(B, K, dtype=torch.int64, device=dev)} for _ in range(n)]
+    elif len(outs) != n:
+        raise ValueError("outs: one dict of result buffers per option set")
+    for o in outs:
+        _check_out(o, (B, K), dev)
+    opts = (ncf_options * n)(*[make_options(**o) for o in options])
+    cp = (ctypes.c_void_p * n)(*[o["c"].data_ptr() for o in outs])
+    bp = (ctypes.c_void_p * n)(*[o["b"].data_ptr() if o.get("b") is not None else 0 for o in outs])
+    np_ = (ctypes.c_void_p * n)(*[o["count"].data_ptr() if o.get("count") is not None else 0 for o in outs])
+    rc = L.ncf_corr_batch_multi(ctx.handle, pox, _ptr(t), _ptr(x), poy, _ptr(None if acf else s),
+                                _ptr(None if acf else y), B, _ptr(lags), K, opts, n, cp, bp, np_,
+                                _stream_handle(stream, dev))
     ctx.check(rc)
     return outs
 

@@ -54,6 +54,7 @@ struct ncf_ctx {
     char *paper = nullptr;       // the paper's NUFFT variant (ncf_corr_paper)
     size_t paper_cap = 0;
     uint64_t launches = 0;
+    size_t dev_hwm = 0;          // largest device footprint of the workspaces so far
     cudaEvent_t staged = nullptr;  // recorded after staging copies issued past the read-back sync
     cudaStream_t copy_st = nullptr;  // host-buffer calls: uploads and read-backs beside the compute stream
     std::vector<cudaEvent_t> copy_ev;
@@ -116,6 +117,11 @@ ncf_status fail(ncf_ctx *ctx, ncf_status s, const char *fmt, ...) {
             return fail(ctx, NCF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
+// device bytes the context holds now (its workspaces only grow)
+size_t ctx_device_bytes(const ncf_ctx *ctx) {
+    return ctx->ws_cap + ctx->ws2_cap + ctx->hbuf_cap + ctx->boot_cap + ctx->paper_cap;
+}
+
 ncf_status grow(ncf_ctx *ctx, char **buf, size_t *cap, size_t need, cudaStream_t st) {
     if (need <= *cap) return NCF_OK;
     size_t ncap = std::max(need, *cap + *cap / 2);
@@ -131,6 +137,7 @@ ncf_status grow(ncf_ctx *ctx, char **buf, size_t *cap, size_t need, cudaStream_t
         return fail(ctx, NCF_ENOMEM, "cudaMalloc of %zu bytes failed", ncap);
     }
     *cap = ncap;
+    ctx->dev_hwm = std::max(ctx->dev_hwm, ctx_device_bytes(ctx));
     return NCF_OK;
 }
 
@@ -260,6 +267,7 @@ struct Eval {
     ncf_options opt{};
     int path = NCF_PATH_AUTO;
     bool den_only = false;  // windowed path: the pair sums alone (PairCount), no numerator
+    const ncf_pooled_stats *pooled = nullptr;  // statistics pooled over a series' shards (ncf_corr_pooled)
     Side X, Y;
     std::vector<double> lagv;
     double max_tau = 0.0, t_abs = 0.0;
@@ -413,6 +421,20 @@ ncf_status analyze(ncf_ctx *ctx, Eval &ev, const double *lags, cudaStream_t st) 
         auto *hy = reinterpret_cast<SeriesStats *>(down + al(B * sizeof(SeriesStats)));
         ev.Y.stats.assign(hy, hy + B);
     }
+    if (ev.pooled) {
+        // standardise with the statistics pooled over the shards; this shard's own
+        // pass still validates order and finiteness (a shard may be constant)
+        auto patch = [&](Side &sd, double mean, double sdv) -> ncf_status {
+            sd.stats[0].mean = mean;
+            sd.stats[0].inv_std = 1.0 / sdv;
+            sd.stats[0].flags &= ~STAT_DEGENERATE;
+            NCF_CUDA(cudaMemcpyAsync(sd.d_stats, sd.stats.data(), sizeof(SeriesStats), cudaMemcpyHostToDevice, st));
+            return NCF_OK;
+        };
+        if ((rc = patch(ev.X, ev.pooled->mean_x, ev.pooled->std_x))) return rc;
+        if (!ev.acf && (rc = patch(ev.Y, ev.pooled->mean_y, ev.pooled->std_y))) return rc;
+        NCF_CUDA(cudaStreamSynchronize(st));
+    }
     if ((rc = check_stats(ctx, ev.X, B, "x"))) return rc;
     if (!ev.acf && (rc = check_stats(ctx, ev.Y, B, "y"))) return rc;
     ev.lagv.assign(h_lags, h_lags + K);
@@ -506,7 +528,11 @@ ncf_status prepare(ncf_ctx *ctx, Eval &ev, char *mem, size_t cap, char *pinned, 
     ev.d_lags = d_lags;
     if (rect_scan(ev)) {
         Side &X = ev.X, &O = ev.outer();
-        ev.fs = choose_scales(ev.t_abs + ev.max_tau + ev.opt.h + 1.0, std::max(X.n_max, O.n_max));
+        // |x_std| <= sqrt(n) bounds the quantised values; pooled statistics come from
+        // the whole series, so its size bounds them
+        int64_t n_bound = std::max(X.n_max, O.n_max);
+        if (ev.pooled) n_bound = std::max({n_bound, ev.pooled->n_x, ev.pooled->n_y});
+        ev.fs = choose_scales(ev.t_abs + ev.max_tau + ev.opt.h + 1.0, n_bound);
         auto keys = [&](const Side &sd, int64_t *&T, int64_t *&Xq, int64_t *&P, int64_t *&C) {
             T = a2.take<int64_t>(sd.n_total);
             Xq = a2.take<int64_t>(sd.n_total);
@@ -786,7 +812,8 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
                                   const double *x, const int64_t *offs_y, const double *s,
                                   const double *y, int64_t B, const double *lags, int64_t K,
                                   const ncf_options *opt, double *c_out, double *b_out,
-                                  int64_t *count_out, cudaStream_t st, bool den_only = false) {
+                                  int64_t *count_out, cudaStream_t st, bool den_only = false,
+                                  const ncf_pooled_stats *pooled = nullptr) {
     LaunchScope scope(ctx);
     ctx->err.clear();
     // the pinned staging buffer may still feed a copy queued by the previous call
@@ -795,6 +822,7 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
     ncf_status rc = check_args(ctx, offs_x, t, x, offs_y, s, y, B, lags, K, opt, ev);
     if (rc) return rc;
     ev.den_only = den_only;
+    ev.pooled = pooled;
     if (!c_out) return fail(ctx, NCF_EINVAL, "c_out is NULL");
     ev.X.t = t; ev.X.v = x;
     if (!ev.acf) { ev.Y.t = s; ev.Y.v = y; }
@@ -810,6 +838,53 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
     NCF_CUDA(cudaEventRecord(ctx->staged, st));
     if (rect_scan(ev) && (rc = tune_rect(ctx, ev, st))) return rc;
     return launch(ctx, ev, /*stats_fresh=*/true, /*guard=*/false, c_out, b_out, count_out, st);
+}
+
+// Several option sets (estimators) on one batch: the statistics pass and its
+// read-back run once, then each option set prepares and launches its own path
+// on the same statistics.
+static ncf_status corr_batch_multi_impl(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                                        const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                                        const double *lags, int64_t K, const ncf_options *opts, int n_opts,
+                                        double *const *c_out, double *const *b_out, int64_t *const *count_out,
+                                        cudaStream_t st) {
+    LaunchScope scope(ctx);
+    ctx->err.clear();
+    if (!opts || n_opts < 1 || !c_out) return fail(ctx, NCF_EINVAL, "no option set or c_out is NULL");
+    if (ctx->staged) NCF_CUDA(cudaEventSynchronize(ctx->staged));
+    Eval ev;
+    ncf_status rc = check_args(ctx, offs_x, t, x, offs_y, s, y, B, lags, K, &opts[0], ev);
+    if (rc) return rc;
+    std::vector<int> paths(n_opts);
+    for (int o = 0; o < n_opts; ++o) {
+        if (!c_out[o]) return fail(ctx, NCF_EINVAL, "c_out of option set %d is NULL", o);
+        if ((rc = check_options(ctx, &opts[o], B, K, &paths[o]))) return rc;
+    }
+    ev.X.t = t; ev.X.v = x;
+    if (!ev.acf) { ev.Y.t = s; ev.Y.v = y; }
+    if ((rc = grow(ctx, &ctx->ws, &ctx->ws_cap, pre_bytes(ev), st))) return rc;
+    carve_pre(ev, ctx->ws);
+    if ((rc = analyze(ctx, ev, lags, st))) return rc;
+    for (int o = 0; o < n_opts; ++o) {
+        Eval eo = ev;  // the sides, their statistics and the lags, shared
+        eo.opt = opts[o];
+        eo.path = paths[o];
+        eo.lag0 = opts[o].norm == NCF_NORM_LAG0;
+        choose_path(eo);
+        size_t dev = 0, pin = 0;
+        if ((rc = main_bytes(ctx, eo, &dev, &pin))) return rc;
+        // the pinned staging may still feed the previous option set's uploads
+        if (o > 0 && ctx->staged) NCF_CUDA(cudaEventSynchronize(ctx->staged));
+        if ((rc = grow(ctx, &ctx->ws2, &ctx->ws2_cap, dev, st))) return rc;
+        if ((rc = grow_pinned(ctx, pin, st))) return rc;
+        if ((rc = prepare(ctx, eo, ctx->ws2, ctx->ws2_cap, ctx->pinned, ctx->pinned_cap, lags, st))) return rc;
+        NCF_CUDA(cudaEventRecord(ctx->staged, st));
+        if (rect_scan(eo) && (rc = tune_rect(ctx, eo, st))) return rc;
+        if ((rc = launch(ctx, eo, /*stats_fresh=*/true, /*guard=*/false, c_out[o], b_out ? b_out[o] : nullptr,
+                         count_out ? count_out[o] : nullptr, st)))
+            return rc;
+    }
+    return NCF_OK;
 }
 
 // frac(tau / L) 2^64 to about one unit: q = fl(tau / L), the exact remainder
@@ -1133,6 +1208,8 @@ const char *ncf_last_error(const ncf_ctx *ctx) { return ctx ? ctx->err.c_str() :
 
 uint64_t ncf_launch_count(const ncf_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+size_t ncf_device_bytes(const ncf_ctx *ctx) { return ctx ? std::max(ctx->dev_hwm, ncf::ctx_device_bytes(ctx)) : 0; }
+
 ncf_status ncf_corr(ncf_ctx *ctx, const double *t, const double *x, int64_t nx, const double *s,
                     const double *y, int64_t ny, const double *lags, int64_t K, const ncf_options *opt,
                     double *c_out, double *b_out, int64_t *count_out, void *stream) {
@@ -1143,6 +1220,63 @@ ncf_status ncf_corr(ncf_ctx *ctx, const double *t, const double *x, int64_t nx, 
     const bool acf = (s == nullptr && y == nullptr);
     return ncf::corr_batch_impl(ctx, ox, t, x, acf ? nullptr : oy, s, y, 1, lags, K, opt, c_out, b_out,
                                 count_out, (cudaStream_t)stream);
+}
+
+ncf_status ncf_corr_pooled(ncf_ctx *ctx, const double *t, const double *x, int64_t nx, const double *s,
+                           const double *y, int64_t ny, const double *lags, int64_t K, const ncf_options *opt,
+                           const ncf_pooled_stats *pooled, double *c_out, double *b_out, int64_t *count_out,
+                           void *stream) {
+    if (!ctx) return NCF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return NCF_ECUDA;
+    if (!pooled) return ncf::fail(ctx, NCF_EINVAL, "pooled statistics are NULL");
+    const bool acf = (s == nullptr && y == nullptr);
+    auto bad = [](double m, double sd, int64_t n) { return !std::isfinite(m) || !(sd > 0.0) || !std::isfinite(sd) || n < 2; };
+    if (bad(pooled->mean_x, pooled->std_x, pooled->n_x) || (!acf && bad(pooled->mean_y, pooled->std_y, pooled->n_y)))
+        return ncf::fail(ctx, NCF_EINVAL, "pooled statistics need finite means, std > 0 and n >= 2");
+    if (opt && opt->norm != NCF_NORM_NONE)
+        return ncf::fail(ctx, NCF_EUNSUPPORTED, "pooled statistics: NORM_NONE only (normalise after the reduction)");
+    const int64_t ox[2] = {0, nx};
+    const int64_t oy[2] = {0, ny};
+    return ncf::corr_batch_impl(ctx, ox, t, x, acf ? nullptr : oy, s, y, 1, lags, K, opt, c_out, b_out,
+                                count_out, (cudaStream_t)stream, false, pooled);
+}
+
+ncf_status ncf_series_stats(ncf_ctx *ctx, const double *t, const double *x, int64_t n, ncf_series_summary *out,
+                            void *stream) {
+    using namespace ncf;
+    if (!ctx || !t || !x || !out || n < 1) return NCF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return NCF_ECUDA;
+    LaunchScope scope(ctx);
+    ctx->err.clear();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ctx->staged) NCF_CUDA(cudaEventSynchronize(ctx->staged));
+    Eval ev;
+    const int64_t offs[2] = {0, n};
+    ev.B = 1;
+    plan_side(ev.X, offs, 1);
+    ev.X.t = t;
+    ev.X.v = x;
+    ncf_status rc;
+    if ((rc = grow(ctx, &ctx->ws, &ctx->ws_cap, pre_bytes(ev), st))) return rc;
+    carve_pre(ev, ctx->ws);
+    if ((rc = grow_pinned(ctx, 4096, st))) return rc;
+    int64_t *hp = reinterpret_cast<int64_t *>(ctx->pinned);
+    hp[0] = 0; hp[1] = n;
+    hp[2] = 0; hp[3] = ev.X.n_chunks;
+    NCF_CUDA(cudaMemcpyAsync(ev.X.d_offs, hp, 16, cudaMemcpyHostToDevice, st));
+    NCF_CUDA(cudaMemcpyAsync(ev.X.d_chunk_base, hp + 2, 16, cudaMemcpyHostToDevice, st));
+    launch_chunk_series(ev.X.d_chunk_base, 1, ev.X.d_cs, st);
+    run_stats(ev, st);
+    auto *hs = reinterpret_cast<SeriesStats *>(ctx->pinned + 256);
+    NCF_CUDA(cudaMemcpyAsync(hs, ev.X.d_stats, sizeof(SeriesStats), cudaMemcpyDeviceToHost, st));
+    NCF_CUDA(cudaStreamSynchronize(st));
+    out->n = n;
+    out->mean = hs->mean;
+    out->m2 = hs->inv_std > 0.0 ? (double)n / (hs->inv_std * hs->inv_std) : 0.0;
+    out->t_first = hs->t_first;
+    out->t_last = hs->t_last;
+    out->flags = hs->flags & ~STAT_DEGENERATE;
+    return NCF_OK;
 }
 
 ncf_status ncf_corr_paper(ncf_ctx *ctx, const double *t, const double *x, int64_t nx, const double *s,
@@ -1364,15 +1498,20 @@ static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *
             }
             if (cudaStreamWaitEvent(st, ev_in[c], 0) != cudaSuccess)
                 return fail(ctx, NCF_ECUDA, "%s: stream wait failed", who);
+            std::vector<double *> cc(n_opts), bb(n_opts);
+            std::vector<int64_t *> nn(n_opts);
             for (int o = 0; o < n_opts; ++o) {
-                rc = corr_batch_impl(ctx, ox.data(), dt + x0, dx + x0, acf ? nullptr : oy.data(),
-                                     acf ? nullptr : ds + y0, acf ? nullptr : dy + y0, nb, dl, K, &opts[o],
-                                     dc[o] + b0 * K, bo(o) ? db[o] + b0 * K : nullptr,
-                                     no(o) ? dn[o] + b0 * K : nullptr, st);
-                if (rc) {
-                    cudaStreamSynchronize(cs);
-                    return rc;
-                }
+                cc[o] = dc[o] + b0 * K;
+                bb[o] = bo(o) ? db[o] + b0 * K : nullptr;
+                nn[o] = no(o) ? dn[o] + b0 * K : nullptr;
+            }
+            // one statistics pass for every option set of the chunk
+            rc = corr_batch_multi_impl(ctx, ox.data(), dt + x0, dx + x0, acf ? nullptr : oy.data(),
+                                       acf ? nullptr : ds + y0, acf ? nullptr : dy + y0, nb, dl, K, opts, n_opts,
+                                       cc.data(), bb.data(), nn.data(), st);
+            if (rc) {
+                cudaStreamSynchronize(cs);
+                return rc;
             }
         }
         ok = cudaEventRecord(ev_out[c], st) == cudaSuccess;
@@ -1405,6 +1544,17 @@ ncf_status ncf_corr_batch_host(ncf_ctx *ctx, const int64_t *offs_x, const double
     if (cudaSetDevice(ctx->device) != cudaSuccess) return NCF_ECUDA;
     return ncf::host_batch(ctx, offs_x, t, x, offs_y, s, y, B, lags, K, opt, 1, &c_out, &b_out, &count_out,
                            (cudaStream_t)stream, "ncf_corr_batch_host");
+}
+
+ncf_status ncf_corr_batch_multi(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                                const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                                const double *lags, int64_t K, const ncf_options *opts, int n_opts,
+                                double *const *c_out, double *const *b_out, int64_t *const *count_out,
+                                void *stream) {
+    if (!ctx) return NCF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return NCF_ECUDA;
+    return ncf::corr_batch_multi_impl(ctx, offs_x, t, x, offs_y, s, y, B, lags, K, opts, n_opts, c_out, b_out,
+                                      count_out, (cudaStream_t)stream);
 }
 
 ncf_status ncf_corr_batch_host_multi(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,

@@ -358,11 +358,24 @@ constexpr unsigned kOffT = offsetof(PtSmem, sT);
 // two CTAs per SM: 228 KB of shared memory, 1 KB of it reserved per CTA
 static_assert(2 * (sizeof(PtSmem) + 1024) <= 228 * 1024, "two CTAs per SM");
 
-__device__ __forceinline__ int4 pt_ent(const unsigned char *S, unsigned off) {
-    return *reinterpret_cast<const int4 *>(S + kOffE + off);
+// Loads at 32-bit addresses of the shared window.  Indexing shared memory
+// through a generic byte pointer makes the compiler form 64-bit addresses (an
+// add with carry per access); the lag loop addresses its staged entries and
+// rank table this way instead.  volatile keeps them in program order, after the
+// barrier that publishes the staged data.
+__device__ __forceinline__ int4 lds_v4(uint32_t a) {
+    int4 v;
+    asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
 }
-__device__ __forceinline__ unsigned pt_bin(const unsigned char *S, int32_t v, int bsh) {
-    return (unsigned)*reinterpret_cast<const uint16_t *>(S + kOffT + 2u * (unsigned)(v >> bsh)) << 4;
+__device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
+    unsigned short v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+    return v;
+}
+// shared address of the rank-table entry of query v
+__device__ __forceinline__ uint32_t pt_bin_addr(uint32_t aT, int32_t v, int bsh) {
+    return aT + ((uint32_t)(v >> bsh) << 1);
 }
 
 // Bounds of lower_bound(Tx, ia, ib, v) from the planning samples samp[m] =
@@ -412,18 +425,34 @@ __device__ __noinline__ int2 pt_band(const int64_t *__restrict__ Tx, const doubl
 
 struct PtAcc { long long a00, a01, a02, a10, a11, a12; };
 
-__device__ __forceinline__ void pt_mac(PtAcc &A, const int4 &el, const int4 &eh, int32_t y0, int32_t y1) {
-    const int32_t d0 = eh.y - el.y, d1 = eh.z - el.z;
-    const int32_t d2 = (int32_t)((unsigned)(eh.w - el.w) << 10) >> 10;  // modulo 2^22, sign-extended
-    // 32 x 32 -> 64-bit multiply-adds in one instruction each
-#define NCF_MADW(acc, a, b) asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b))
-    NCF_MADW(A.a00, y0, d0);
-    NCF_MADW(A.a01, y0, d1);
-    NCF_MADW(A.a02, y0, d2);
-    NCF_MADW(A.a10, y1, d0);
-    NCF_MADW(A.a11, y1, d1);
-    NCF_MADW(A.a12, y1, d2);
-#undef NCF_MADW
+// sum_i a[i] b[i] over the points of a batch as one chain of 32 x 32 -> 64-bit
+// multiply-adds (each product below 2^52, the chain below 2^54), then one 64-bit
+// add into the accumulator: a chain lets the multiply-adds accumulate in place
+// instead of taking a 64-bit add each.
+__device__ __forceinline__ long long pt_dot(const int32_t (&a)[kPtBatch], const int32_t (&b)[kPtBatch]) {
+    long long t;
+    asm("mul.wide.s32 %0, %1, %2;" : "=l"(t) : "r"(a[0]), "r"(b[0]));
+#pragma unroll
+    for (int i = 1; i < kPtBatch; ++i) asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(t) : "r"(a[i]), "r"(b[i]));
+    return t;
+}
+
+// The six limb products y_a d_b of a batch's points into the accumulators.
+__device__ __forceinline__ void pt_mac_batch(PtAcc &A, const int32_t (&d0)[kPtBatch], const int32_t (&d1)[kPtBatch],
+                                             const int32_t (&d2)[kPtBatch], const int32_t (&y0)[kPtM],
+                                             const int32_t (&y1)[kPtM], int q0) {
+    int32_t ya[kPtBatch], yb[kPtBatch];
+#pragma unroll
+    for (int i = 0; i < kPtBatch; ++i) {
+        ya[i] = y0[q0 + i];
+        yb[i] = y1[q0 + i];
+    }
+    A.a00 += pt_dot(ya, d0);
+    A.a01 += pt_dot(ya, d1);
+    A.a02 += pt_dot(ya, d2);
+    A.a10 += pt_dot(yb, d0);
+    A.a11 += pt_dot(yb, d1);
+    A.a12 += pt_dot(yb, d2);
 }
 
 // a 2^e added to the 128-bit two's-complement value (lo, hi), 0 < e < 64
@@ -468,11 +497,14 @@ struct PtLagArgs {
 };
 
 // One lag over this lane's outer points of the segment [pa, pb) (the whole
-// full tile when kFull).  Points are handled kPtBatch at a time: the bin and
-// entry loads of a batch are issued together, then the short walks, one test
-// for the (rare) band, and the numerators.
+// full tile when kFull).  Points are handled kPtBatch at a time: the rank-table
+// and entry loads of a batch are issued together; an edge whose bin holds keys
+// below its query steps forward in a warp-uniform loop that is rarely entered
+// (about 0.25 keys per query on the light-curve batch), and so is the band
+// test's FP64 fix-up; then the counts and the numerators.  Edge positions are
+// shared-window byte addresses of staged entries (16 bytes each).
 template <bool kFull>
-__device__ __forceinline__ void pt_lag(const unsigned char *S, const int32_t (&sc)[kPtM],
+__device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (&sc)[kPtM],
                                        const int32_t (&y0)[kPtM], const int32_t (&y1)[kPtM], int pbase,
                                        int32_t sca, int4 L, const PtLagArgs &g, unsigned &c, PtAcc &A) {
 #pragma unroll
@@ -491,49 +523,70 @@ __device__ __forceinline__ void pt_lag(const unsigned char *S, const int32_t (&s
             for (int i = 0; i < kPtBatch; ++i) any |= ok[i];
             if (!__any_sync(0xffffffffu, any)) continue;
         }
-        unsigned ol[kPtBatch], oh[kPtBatch];
+        uint32_t ol[kPtBatch], oh[kPtBatch];
         int4 el[kPtBatch], eh[kPtBatch];
 #pragma unroll
         for (int i = 0; i < kPtBatch; ++i) {
-            ol[i] = pt_bin(S, s[i] + L.x, g.bsh);
-            oh[i] = pt_bin(S, s[i] + L.z, g.bsh);
+            ol[i] = lds_u16(pt_bin_addr(aT, s[i] + L.x, g.bsh));
+            oh[i] = lds_u16(pt_bin_addr(aT, s[i] + L.z, g.bsh));
         }
 #pragma unroll
         for (int i = 0; i < kPtBatch; ++i) {
-            el[i] = pt_ent(S, ol[i]);
-            eh[i] = pt_ent(S, oh[i]);
+            ol[i] = aE + (ol[i] << 4);
+            oh[i] = aE + (oh[i] << 4);
+            el[i] = lds_v4(ol[i]);
+            eh[i] = lds_v4(oh[i]);
+        }
+        bool step = false;
+#pragma unroll
+        for (int i = 0; i < kPtBatch; ++i) step |= (el[i].x < s[i] + L.x) | (eh[i].x < s[i] + L.z);
+        while (__any_sync(0xffffffffu, step)) {
+            step = false;
+#pragma unroll
+            for (int i = 0; i < kPtBatch; ++i) {
+                if (el[i].x < s[i] + L.x) {
+                    ol[i] += 16u;
+                    el[i] = lds_v4(ol[i]);
+                }
+                if (eh[i].x < s[i] + L.z) {
+                    oh[i] += 16u;
+                    eh[i] = lds_v4(oh[i]);
+                }
+                step |= (el[i].x < s[i] + L.x) | (eh[i].x < s[i] + L.z);
+            }
         }
         bool band = false;
 #pragma unroll
-        for (int i = 0; i < kPtBatch; ++i) {
-            const int32_t vl = s[i] + L.x, vh = s[i] + L.z;
-            while (el[i].x < vl) el[i] = pt_ent(S, ol[i] += 16u);
-            while (eh[i].x < vh) eh[i] = pt_ent(S, oh[i] += 16u);
-            band |= ok[i] && ((el[i].x < s[i] + L.y) || (eh[i].x < s[i] + L.w));
-        }
-        if (band) {
+        for (int i = 0; i < kPtBatch; ++i) band |= ok[i] & ((el[i].x < s[i] + L.y) | (eh[i].x < s[i] + L.w));
+        if (__any_sync(0xffffffffu, band)) {
 #pragma unroll
             for (int i = 0; i < kPtBatch; ++i) {
                 const bool fl = el[i].x < s[i] + L.y, fh = eh[i].x < s[i] + L.w;
                 if (ok[i] && (fl || fh)) {
                     const int2 r = pt_band(g.Tx, g.tx, g.Sy, g.sy, g.dls, g.dus, g.slags,
                                            g.j0 + pbase + kPtStride * (q0 + i), g.k, g.eps, g.h, g.eta, g.ia_s, g.lim,
-                                           (int)(ol[i] >> 4), (int)(oh[i] >> 4), fl, fh);
-                    ol[i] = 16u * (unsigned)r.x;
-                    oh[i] = 16u * (unsigned)r.y;
-                    el[i] = pt_ent(S, ol[i]);
-                    eh[i] = pt_ent(S, oh[i]);
+                                           (int)((ol[i] - aE) >> 4), (int)((oh[i] - aE) >> 4), fl, fh);
+                    ol[i] = aE + 16u * (unsigned)r.x;
+                    oh[i] = aE + 16u * (unsigned)r.y;
+                    el[i] = lds_v4(ol[i]);
+                    eh[i] = lds_v4(oh[i]);
                 }
             }
         }
         // off the band, oh >= ol: the upper query is not below the lower one
+        int32_t d0[kPtBatch], d1[kPtBatch], d2[kPtBatch];
 #pragma unroll
         for (int i = 0; i < kPtBatch; ++i) {
-            if (kFull || ok[i]) {
-                c += oh[i] - ol[i];
-                pt_mac(A, el[i], eh[i], y0[q0 + i], y1[q0 + i]);
-            }
+            const bool use = kFull || ok[i];
+            c += use ? oh[i] - ol[i] : 0u;
+            // limbs of prefix sums rebased to the sub-group's first entry: |P| < 2^61,
+            // so the top limbs (P >> 42) differ by less than 2^20 and every
+            // difference is exact
+            d0[i] = use ? eh[i].y - el[i].y : 0;
+            d1[i] = use ? eh[i].z - el[i].z : 0;
+            d2[i] = use ? eh[i].w - el[i].w : 0;
         }
+        pt_mac_batch(A, d0, d1, d2, y0, y1, q0);
     }
 }
 
@@ -550,7 +603,8 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                     unsigned long long *__restrict__ num128) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PtSmem &sm = *reinterpret_cast<PtSmem *>(smem_raw);
-    const unsigned char *S = smem_raw;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    const uint32_t aE = sbase + kOffE, aT = sbase + kOffT;
     const int64_t tI = blockIdx.x / G;
     const int g = (int)(blockIdx.x - tI * G);
     const ScanTile tile = tiles[tI];
@@ -735,6 +789,10 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                                  : "memory");
                 }
                 asm volatile("cp.async.wait_all;" ::: "memory");
+                // prefix sums rebased to the first entry's: |P[ia + i] - P[ia]| is a sum
+                // of |X| within one series, below n 2^p + n/2 < 2^61 (sum |x_std| <= n for
+                // ddof 0 and p <= 61 - 1.5 log2 n), so the three limbs never wrap
+                const int64_t P0 = P[sb.ia];
                 for (int i = tid; i <= max(nK, 0); i += blockDim.x) {
                     const longlong2 raw = *reinterpret_cast<const longlong2 *>(&sm.sE[i]);
                     int32_t key = kSentinel;
@@ -742,7 +800,7 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                         const int64_t v = ((raw.x - base) >> sh) - vmin;
                         key = (int32_t)max(min(v, (int64_t)(1 << 30)), (int64_t)-1);
                     }
-                    const int64_t pv = raw.y;
+                    const int64_t pv = (int64_t)((unsigned long long)raw.y - (unsigned long long)P0);
                     sm.sE[i] = make_int4(key, (int32_t)(pv & 0x1fffff), (int32_t)((pv >> 21) & 0x1fffff),
                                          (int32_t)(pv >> 42));
                 }
@@ -791,9 +849,9 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                     unsigned int c = 0;
                     PtAcc A{0, 0, 0, 0, 0, 0};
                     if (full)
-                        pt_lag<true>(S, sc, y0, y1, pbase, sca, L, ga, c, A);
+                        pt_lag<true>(aE, aT, sc, y0, y1, pbase, sca, L, ga, c, A);
                     else
-                        pt_lag<false>(S, sc, y0, y1, pbase, sca, L, ga, c, A);
+                        pt_lag<false>(aE, aT, sc, y0, y1, pbase, sca, L, ga, c, A);
                     c = __reduce_add_sync(0xffffffffu, c >> 4);
                     U128 acc = pt_combine(A);
 #pragma unroll

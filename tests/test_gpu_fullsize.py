@@ -40,3 +40,16 @@ def test_light_curves_4096_x_256_sampled_against_the_oracle(batch):
         assert np.max(np.abs(r["c"][b, ks] - ref_r["c"])) < 1e-10, b
         ref_g = oracle.corr(w.t[sl], w.x[sl], w.lags[ks], "gaussian", H, method="windowed", trunc_R=8.0)
         assert np.max(np.abs(g["c"][b, ks] - ref_g["c"])) < 1e-5, b
+
+
+def test_light_curves_4096_x_256_every_fp32_value_within_1e5_of_the_fp64_path(batch):
+    """Every one of the 4096 x 256 values of the batched FP32 form against the FP64
+    spectral path on the same batch, which the oracle pins within 1e-10 (the
+    sampled test above and the spectral parity tests)."""
+    w = batch
+    f32 = api.corr_batch(w.offs, w.t, w.x, w.lags, kernel="gaussian", h=H, path="spectral", precision="fp32")
+    f64 = api.corr_batch(w.offs, w.t, w.x, w.lags, kernel="gaussian", h=H, path="spectral", precision="fp64")
+    d = (f32["c"] - f64["c"]).abs()
+    assert d.numel() == 4096 * 256
+    assert float(d.max()) < 1e-5, float(d.max())
+    assert float((f32["b"] / f64["b"] - 1).abs().max()) < 1e-5

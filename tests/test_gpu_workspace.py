@@ -85,5 +85,5 @@ def test_server_admits_by_the_bound():
     fits = api.Server(device=0, mem_budget_bytes=need, slots=1)
     r = fits.wait(fits.submit(w.t, w.x, w.lags, **opt))
     ref = api.corr(w.t, w.x, w.lags, **opt)["c"].cpu().numpy()
-    assert np.max(np.abs(r["c"] - ref)) < 1e-12
+    assert np.max(np.abs(r["c"] - ref)) < 1e-6   # FP32 form: the same up to summation order
     fits.close()

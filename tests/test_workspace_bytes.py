@@ -20,6 +20,9 @@ def test_light_curve_batch_footprints_are_positive_and_path_dependent():
     assert rect > 24 * LC["n_x"]
     # the FP32 spectral path keeps B grids of >= 4 L / h complex FP32 cells
     assert g32 > LC["B"] * 4 * (LC["span"] / LC["h"]) * 8
+    # a CCF spreads two series: more
+    ccf, _ = ws(**dict(LC, n_y=LC["n_x"]), kernel="gaussian", precision="fp32")
+    assert ccf > g32
 
 
 def test_monotone_in_sizes_and_span():
