@@ -8,12 +8,13 @@ rotation signal with OU amplitude, flicker noise, heteroscedastic errors,
 nightly cadence with seasonal and weather gaps; shared 256-lag grid on
 [0, 200] d; Gaussian kernel h = 0.5 d and rectangle half-width 0.5 d.
 
-A step is the whole hot path over the batch: the Gaussian ACFs through the
-batched FP32 form (statistics, spreading, FFT, spectra, mode-to-lag
+A step is the whole hot path over the batch: one statistics pass, the Gaussian
+ACFs through the batched FP32 form (spreading, FFT, spectra, mode-to-lag
 contraction on tensor cores) and the rectangle ACFs through the exact
-pair-count scan, each with its statistics pass and normalisation.  Each is a
-plan (analysis done once) whose launches are captured in a CUDA graph; a step
-replays both graphs.  Series-lags per step = 2 * 4096 * 256 (one per estimator).
+pair-count scan, each with its normalisation.  Both estimators are one plan
+(analysis done once, ncf_plan_create_multi) whose launches are captured in a
+CUDA graph; a step replays it.  Series-lags per step = 2 * 4096 * 256 (one per
+estimator).
 
 One JSON line is printed (rank 0): the device-timed throughput (`value`) and
 each estimator's own rate; the same metric end to end through the host-buffer
@@ -53,7 +54,7 @@ WORKLOAD = "light_curves: 4096 series, n log-uniform [200, 2e5], 256 lags on [0,
 # lags), dram__bytes_read.sum + dram__bytes_write.sum from one single-pass ncu capture of
 # this command.  Reported as the roofline's traffic only for that workload; update or
 # remove an entry whenever its kernel changes.
-MEASURED_TRAFFIC = {("rect_scan_pt_kernel", 4096): 3.02e9 + 31.02e6}
+MEASURED_TRAFFIC = {("rect_scan_pt_kernel", 4096): 3.02e9 + 31.15e6}
 
 
 # Integer rates of this GPU measured by a probe of independent instruction chains
@@ -671,48 +672,48 @@ def main():
     G_OPT = dict(kernel="gaussian", h=H, path="spectral", precision="fp32")
     R_OPT = dict(kernel="rectangle", h=H)
 
-    # ---- the step: one plan per estimator, its launches captured in a CUDA graph ----
-    plan_g = api.Plan(offs, t, x, lags, **G_OPT, ctx=ctx, stream=stream)
-    plan_r = api.Plan(offs, t, x, lags, **R_OPT, ctx=ctx, stream=stream)
-    for _ in range(max(args.warmup, 3)):
-        plan_g.execute(t, x, out=out_g, stream=stream)
-        plan_r.execute(t, x, out=out_r, stream=stream)
-    torch.cuda.synchronize()
-    graphs, graph_launches = [], 0
-    cs = torch.cuda.Stream(dev)
-    cs.wait_stream(stream)
-    for plan, out in ((plan_g, out_g), (plan_r, out_r)):
+    # ---- the step: one plan of both estimators (one statistics pass), its launches
+    # captured in a CUDA graph; each estimator also as a plan of its own ----
+    def capture(fn):
         g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream(dev)
+        cs.wait_stream(stream)
         l0 = ctx.launches
         with torch.cuda.stream(cs):
             with torch.cuda.graph(g, stream=cs):
-                plan.execute(t, x, out=out, stream=cs)
-        graph_launches += ctx.launches - l0
-        graphs.append(g)
-    torch.cuda.synchronize()
+                fn(cs)
+        torch.cuda.synchronize()
+        return g, ctx.launches - l0
+
+    plan_m = api.MultiPlan(offs, t, x, lags, [G_OPT, R_OPT], ctx=ctx, stream=stream)
+    plan_g = api.Plan(offs, t, x, lags, **G_OPT, ctx=ctx, stream=stream)
+    plan_r = api.Plan(offs, t, x, lags, **R_OPT, ctx=ctx, stream=stream)
     for _ in range(max(args.warmup, 3)):
-        for g in graphs:
-            g.replay()
+        plan_m.execute(t, x, outs=[out_g, out_r], stream=stream)
+    plan_g.execute(t, x, out=out_g, stream=stream)
+    plan_r.execute(t, x, out=out_r, stream=stream)
+    torch.cuda.synchronize()
+    g_step, graph_launches = capture(lambda cs: plan_m.execute(t, x, outs=[out_g, out_r], stream=cs))
+    g_gauss, _ = capture(lambda cs: plan_g.execute(t, x, out=out_g, stream=cs))
+    g_rect, _ = capture(lambda cs: plan_r.execute(t, x, out=out_r, stream=cs))
+    for _ in range(max(args.warmup, 3)):
+        g_step.replay()
     torch.cuda.synchronize()
     plan = ctx.last_plan()
 
-    # ---- timed region: graph replays, an event between the two estimators ----
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
+    # ---- timed region: graph replays of the step ----
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
         ev[0].record(stream)
         for s_ in range(args.steps):
-            graphs[0].replay()
-            ev[2 * s_ + 1].record(stream)
-            graphs[1].replay()
-            ev[2 * s_ + 2].record(stream)
+            g_step.replay()
+            ev[s_ + 1].record(stream)
         torch.cuda.synchronize()
         barrier()
     launches = graph_launches * args.steps
-    step_ms = [ev[2 * s_].elapsed_time(ev[2 * s_ + 2]) for s_ in range(args.steps)]
-    g_ms = float(np.mean([ev[2 * s_].elapsed_time(ev[2 * s_ + 1]) for s_ in range(args.steps)]))
-    r_ms = float(np.mean([ev[2 * s_ + 1].elapsed_time(ev[2 * s_ + 2]) for s_ in range(args.steps)]))
+    step_ms = [ev[s_].elapsed_time(ev[s_ + 1]) for s_ in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     total_ms = shard.max_over_ranks(total_ms, device=dev)
     units = 2.0 * B * K * args.steps * world
@@ -720,6 +721,22 @@ def main():
     c32 = out_g["c"].clone()
     counts = out_r["count"].clone()
     rect_c = out_r["c"].clone()
+    if plan_m.status() != 0:
+        raise RuntimeError("a plan's device guard flagged the benchmark data")
+
+    # ---- each estimator alone (its own plan and graph, its own statistics pass) ----
+    def graph_ms(g, reps=3):
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    g_ms, r_ms = graph_ms(g_gauss), graph_ms(g_rect)
     if plan_g.status() != 0 or plan_r.status() != 0:
         raise RuntimeError("a plan's device guard flagged the benchmark data")
 
@@ -778,13 +795,15 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
 
     mem = {"context_workspace_high_water_bytes": ctx.device_bytes,
-           "plan_bytes": {"gaussian_fp32_form": plan_g.device_bytes, "rectangle_exact_scan": plan_r.device_bytes},
+           "plan_bytes": {"both_estimators": plan_m.device_bytes, "gaussian_fp32_form": plan_g.device_bytes,
+                          "rectangle_exact_scan": plan_r.device_bytes},
            "workspace_bound_bytes": {
                "gaussian_fp32_form": api.workspace_bytes(int(offs[-1]), B, K, float(max(
                    w.t[offs[b + 1] - 1] - w.t[offs[b]] for b in range(B))), float(np.max(np.abs(w.lags))), **G_OPT)[0],
                "rectangle_exact_scan": api.workspace_bytes(int(offs[-1]), B, K, 0.0, float(np.max(np.abs(w.lags))),
                                                            **R_OPT)[0]},
            "inputs_bytes": int(w.t.nbytes + w.x.nbytes + w.lags.nbytes)}
+    plan_m.close()
     plan_g.close()
     plan_r.close()
 
@@ -870,6 +889,7 @@ def main():
                    "grid": nf, "modes": M, "period_d": plan["period"], "graph": True,
                    "l2": f"inputs larger than L2 ({(w.t.nbytes + w.x.nbytes) / 1e9:.2f} GB per step)"},
         "per_estimator": {
+            "note": "each estimator alone: its own plan and graph, statistics pass included",
             "gaussian_fp32_form": {"ms": g_ms, "value": B * K * world / (g_ms / 1e3), "unit": "series*lags/s"},
             "rectangle_exact_scan": {"ms": r_ms, "value": B * K * world / (r_ms / 1e3), "unit": "series*lags/s"},
             "one_call_ms_per_step": one_shot_ms,

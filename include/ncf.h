@@ -426,6 +426,25 @@ NCF_API ncf_status ncf_plan_execute(ncf_plan *plan, const double *t, const doubl
                                     const double *y, double *c_out, double *b_out, int64_t *count_out,
                                     void *stream);
 NCF_API ncf_status ncf_plan_status(ncf_plan *plan, void *stream, int32_t *flags);
+/*
+ * A plan of several option sets (estimators) on the same data: ncf_plan_create
+ * with opts[n_opts].  ncf_plan_execute_multi runs the statistics pass once
+ * (the prior standardisation step of Algorithms 2, 4, 9 and 10 does not depend
+ * on the kernel) and then every option set's kernels, writing c_out[o], b_out[o]
+ * and count_out[o] (DEVICE [B x K]; b_out, count_out and their entries may be
+ * NULL).  Like ncf_plan_execute it neither allocates nor synchronises, so it can
+ * be captured in a CUDA graph; one status word covers every set.
+ * ncf_plan_execute on such a plan runs the first option set only;
+ * ncf_plan_option_sets returns n_opts.
+ */
+NCF_API ncf_status ncf_plan_create_multi(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                                         const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                                         const double *lags, int64_t K, const ncf_options *opts, int n_opts,
+                                         void *stream, ncf_plan **out);
+NCF_API ncf_status ncf_plan_execute_multi(ncf_plan *plan, const double *t, const double *x, const double *s,
+                                          const double *y, double *const *c_out, double *const *b_out,
+                                          int64_t *const *count_out, void *stream);
+NCF_API int ncf_plan_option_sets(const ncf_plan *plan);
 NCF_API size_t ncf_plan_device_bytes(const ncf_plan *plan);
 
 /*

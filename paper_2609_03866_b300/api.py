@@ -717,6 +717,92 @@ class Plan:
             pass
 
 
+class MultiPlan:
+    """A plan of several estimators on the same batch (ncf_plan_create_multi): one
+    statistics pass per `execute`, then every option set's kernels; no host
+    synchronisation or allocation in `execute`, so it can be captured in a CUDA
+    graph.  `options`: a list of dicts of corr_batch's keyword options."""
+
+    def __init__(self, offs, t, x, lags, options, offs_y=None, s=None, y=None, ctx: Context | None = None,
+                 stream=None):
+        import torch
+        L = lib()
+        if not getattr(L, "_mplan_types", False):
+            vp = ctypes.c_void_p
+            vpp = ctypes.POINTER(ctypes.c_void_p)
+            L.ncf_plan_create_multi.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp, ctypes.c_int64,
+                                                ctypes.POINTER(ncf_options), ctypes.c_int, vp,
+                                                ctypes.POINTER(vp)]
+            L.ncf_plan_create_multi.restype = ctypes.c_int
+            L.ncf_plan_execute_multi.argtypes = [vp, vp, vp, vp, vp, vpp, vpp, vpp, vp]
+            L.ncf_plan_execute_multi.restype = ctypes.c_int
+            L.ncf_plan_option_sets.argtypes = [vp]
+            L.ncf_plan_option_sets.restype = ctypes.c_int
+            L._mplan_types = True
+        self.ctx = ctx or default_context()
+        dev = torch.device("cuda", self.ctx.device)
+        t, x, lags = _dev(t, dev), _dev(x, dev), _dev(lags, dev)
+        ox, pox = _host_offs(offs)
+        self.B, self.K, self.acf = ox.size - 1, lags.numel(), s is None
+        oy, poy = (None, ctypes.c_void_p(0)) if self.acf else _host_offs(offs_y)
+        if not self.acf:
+            s, y = _dev(s, dev), _dev(y, dev)
+        self.n_x, self.n_y = t.numel(), (0 if self.acf else s.numel())
+        self.n = len(options)
+        opts = (ncf_options * self.n)(*[make_options(**o) for o in options])
+        self._h = ctypes.c_void_p()
+        rc = L.ncf_plan_create_multi(self.ctx.handle, pox, _ptr(t), _ptr(x), poy, _ptr(None if self.acf else s),
+                                     _ptr(None if self.acf else y), self.B, _ptr(lags), self.K, opts, self.n,
+                                     _stream_handle(stream, dev), ctypes.byref(self._h))
+        self.ctx.check(rc)
+        self.device = dev
+
+    @property
+    def device_bytes(self) -> int:
+        return int(lib().ncf_plan_device_bytes(self._h))
+
+    def execute(self, t, x, s=None, y=None, outs=None, stream=None):
+        import torch
+        _check_device_input("t", t, self.n_x, self.device)
+        _check_device_input("x", x, self.n_x, self.device)
+        if not self.acf:
+            _check_device_input("s", s, self.n_y, self.device)
+            _check_device_input("y", y, self.n_y, self.device)
+        if outs is None:
+            outs = [{"c": torch.empty(self.B, self.K, dtype=torch.float64, device=self.device),
+                     "b": torch.empty(self.B, self.K, dtype=torch.float64, device=self.device),
+                     "count": torch.empty(self.B, self.K, dtype=torch.int64, device=self.device)}
+                    for _ in range(self.n)]
+        elif len(outs) != self.n:
+            raise ValueError("outs: one dict of result buffers per option set")
+        for o in outs:
+            _check_out(o, (self.B, self.K), self.device)
+        cp = (ctypes.c_void_p * self.n)(*[o["c"].data_ptr() for o in outs])
+        bp = (ctypes.c_void_p * self.n)(*[o["b"].data_ptr() if o.get("b") is not None else 0 for o in outs])
+        np_ = (ctypes.c_void_p * self.n)(*[o["count"].data_ptr() if o.get("count") is not None else 0
+                                           for o in outs])
+        rc = lib().ncf_plan_execute_multi(self._h, _ptr(t), _ptr(x), _ptr(s), _ptr(y), cp, bp, np_,
+                                          _stream_handle(stream, self.device))
+        self.ctx.check(rc)
+        return outs
+
+    def status(self, stream=None) -> int:
+        f = ctypes.c_int32()
+        lib().ncf_plan_status(self._h, _stream_handle(stream, self.device), ctypes.byref(f))
+        return int(f.value)
+
+    def close(self):
+        if self._h:
+            lib().ncf_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class ncf_request(ctypes.Structure):
     _fields_ = [("t", ctypes.c_void_p), ("x", ctypes.c_void_p), ("nx", ctypes.c_int64),
                 ("s", ctypes.c_void_p), ("y", ctypes.c_void_p), ("ny", ctypes.c_int64),

@@ -626,13 +626,14 @@ ncf_status prepare(ncf_ctx *ctx, Eval &ev, char *mem, size_t cap, char *pinned, 
 // The per-data kernels of an evaluation; `stats_fresh` skips the statistics
 // pass when `analyze` has just run it on the same data.
 ncf_status launch(ncf_ctx *ctx, Eval &ev, bool stats_fresh, bool guard, double *c_out, double *b_out,
-                  int64_t *count_out, cudaStream_t st) {
+                  int64_t *count_out, cudaStream_t st, bool first = true) {
     const int64_t B = ev.B, K = ev.K;
     std::string msg;
     ncf_status rc;
-    NCF_CUDA(cudaMemsetAsync(ev.status, 0, sizeof(int), st));
+    // the status word and the statistics belong to the first option set of an evaluation
+    if (first) NCF_CUDA(cudaMemsetAsync(ev.status, 0, sizeof(int), st));
     if (!stats_fresh) run_stats(ev, st);
-    if (guard) launch_stats_guard(ev.X.d_stats, ev.acf ? nullptr : ev.Y.d_stats, B, ev.status, st);
+    if (guard && first) launch_stats_guard(ev.X.d_stats, ev.acf ? nullptr : ev.Y.d_stats, B, ev.status, st);
     Side &X = ev.X, &O = ev.outer();
     if (rect_scan(ev)) {
         launch_keys_prefix(X.t, X.v, X.d_offs, X.d_chunk_base, X.d_cs, X.n_chunks, kPrepChunk, X.d_stats, ev.fs,
@@ -1081,9 +1082,13 @@ static ncf_status corr_paper_impl(ncf_ctx *ctx, const double *t, const double *x
 struct ncf_plan {
     ncf_ctx *ctx = nullptr;  // used by execute/status (the context must outlive those calls)
     int device = 0;          // destroy needs no context
-    ncf::Eval ev;
+    ncf::Eval ev;            // the first option set; it owns the statistics
     char *pre = nullptr, *main = nullptr;
     size_t pre_cap = 0, main_cap = 0;
+    // further option sets on the same data and statistics (ncf_plan_create_multi)
+    std::vector<ncf::Eval> more;
+    std::vector<char *> more_main;
+    std::vector<size_t> more_cap;
 };
 
 // ----------------------------------------------------------------------------
@@ -1568,16 +1573,17 @@ ncf_status ncf_corr_batch_host_multi(ncf_ctx *ctx, const int64_t *offs_x, const 
                            (cudaStream_t)stream, "ncf_corr_batch_host_multi");
 }
 
-ncf_status ncf_plan_create(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
-                           const int64_t *offs_y, const double *s, const double *y, int64_t B,
-                           const double *lags, int64_t K, const ncf_options *opt, void *stream,
-                           ncf_plan **out) {
+ncf_status ncf_plan_create_multi(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                                 const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                                 const double *lags, int64_t K, const ncf_options *opts, int n_opts, void *stream,
+                                 ncf_plan **out) {
     using namespace ncf;
     if (!ctx || !out) return NCF_EINVAL;
     *out = nullptr;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return NCF_ECUDA;
     LaunchScope scope(ctx);
     ctx->err.clear();
+    if (!opts || n_opts < 1) return fail(ctx, NCF_EINVAL, "no option set");
     cudaStream_t st = (cudaStream_t)stream;
     if (ctx->staged) NCF_CUDA(cudaEventSynchronize(ctx->staged));
     ncf_plan *p = new ncf_plan();
@@ -1587,11 +1593,15 @@ ncf_status ncf_plan_create(ncf_ctx *ctx, const int64_t *offs_x, const double *t,
     auto bail = [&](ncf_status rc) {
         if (p->pre) cudaFree(p->pre);
         if (p->main) cudaFree(p->main);
+        for (char *m : p->more_main) if (m) cudaFree(m);
         delete p;
         return rc;
     };
-    ncf_status rc = check_args(ctx, offs_x, t, x, offs_y, s, y, B, lags, K, opt, ev);
+    ncf_status rc = check_args(ctx, offs_x, t, x, offs_y, s, y, B, lags, K, &opts[0], ev);
     if (rc) return bail(rc);
+    std::vector<int> paths(n_opts);
+    for (int o = 0; o < n_opts; ++o)
+        if ((rc = check_options(ctx, &opts[o], B, K, &paths[o]))) return bail(rc);
     ev.X.t = t; ev.X.v = x;
     if (!ev.acf) { ev.Y.t = s; ev.Y.v = y; }
     p->pre_cap = pre_bytes(ev);
@@ -1601,20 +1611,47 @@ ncf_status ncf_plan_create(ncf_ctx *ctx, const int64_t *offs_x, const double *t,
     }
     carve_pre(ev, p->pre);
     if ((rc = analyze(ctx, ev, lags, st))) return bail(rc);
-    choose_path(ev);
-    size_t dev = 0, pin = 0;
-    if ((rc = main_bytes(ctx, ev, &dev, &pin))) return bail(rc);
-    p->main_cap = dev;
-    if (cudaMalloc(&p->main, dev) != cudaSuccess) {
-        cudaGetLastError();
-        return bail(fail(ctx, NCF_ENOMEM, "cudaMalloc of %zu bytes failed", dev));
+    // option sets 1.. share the sides, their statistics and the lags of set 0
+    for (int o = 1; o < n_opts; ++o) {
+        Eval eo = ev;
+        eo.opt = opts[o];
+        eo.path = paths[o];
+        eo.lag0 = opts[o].norm == NCF_NORM_LAG0;
+        p->more.push_back(eo);
+        p->more_main.push_back(nullptr);
+        p->more_cap.push_back(0);
     }
-    if ((rc = grow_pinned(ctx, pin, st))) return bail(rc);
-    if ((rc = prepare(ctx, ev, p->main, dev, ctx->pinned, ctx->pinned_cap, lags, st))) return bail(rc);
-    if (rect_scan(ev) && (rc = tune_rect(ctx, ev, st))) return bail(rc);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(ctx, NCF_ECUDA, "plan set-up failed"));
+    for (int o = 0; o < n_opts; ++o) {
+        Eval &eo = o == 0 ? ev : p->more[o - 1];
+        char *&mem = o == 0 ? p->main : p->more_main[o - 1];
+        size_t &cap = o == 0 ? p->main_cap : p->more_cap[o - 1];
+        choose_path(eo);
+        size_t dev = 0, pin = 0;
+        if ((rc = main_bytes(ctx, eo, &dev, &pin))) return bail(rc);
+        cap = dev;
+        if (cudaMalloc(&mem, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(ctx, NCF_ENOMEM, "cudaMalloc of %zu bytes failed", dev));
+        }
+        if ((rc = grow_pinned(ctx, pin, st))) return bail(rc);
+        if ((rc = prepare(ctx, eo, mem, dev, ctx->pinned, ctx->pinned_cap, lags, st))) return bail(rc);
+        if (rect_scan(eo) && (rc = tune_rect(ctx, eo, st))) return bail(rc);
+        // the pinned staging is reused by the next option set's tables
+        if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(ctx, NCF_ECUDA, "plan set-up failed"));
+    }
     *out = p;
     return NCF_OK;
+}
+
+ncf_status ncf_plan_create(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                           const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                           const double *lags, int64_t K, const ncf_options *opt, void *stream,
+                           ncf_plan **out) {
+    if (!opt) {
+        if (ctx) ctx->err = "options are NULL";
+        return NCF_EINVAL;
+    }
+    return ncf_plan_create_multi(ctx, offs_x, t, x, offs_y, s, y, B, lags, K, opt, 1, stream, out);
 }
 
 ncf_status ncf_plan_execute(ncf_plan *plan, const double *t, const double *x, const double *s,
@@ -1630,6 +1667,32 @@ ncf_status ncf_plan_execute(ncf_plan *plan, const double *t, const double *x, co
     if (!ev.acf) { ev.Y.t = s; ev.Y.v = y; }
     return launch(ctx, ev, /*stats_fresh=*/false, /*guard=*/true, c_out, b_out, count_out, (cudaStream_t)stream);
 }
+
+ncf_status ncf_plan_execute_multi(ncf_plan *plan, const double *t, const double *x, const double *s,
+                                  const double *y, double *const *c_out, double *const *b_out,
+                                  int64_t *const *count_out, void *stream) {
+    using namespace ncf;
+    if (!plan || !t || !x || !c_out) return NCF_EINVAL;
+    ncf_ctx *ctx = plan->ctx;
+    const int n = 1 + (int)plan->more.size();
+    for (int o = 0; o < n; ++o)
+        if (!c_out[o]) return fail(ctx, NCF_EINVAL, "c_out of option set %d is NULL", o);
+    if (!plan->ev.acf && (!s || !y)) return fail(ctx, NCF_EINVAL, "this plan is a CCF: s and y are needed");
+    LaunchScope scope(ctx);
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int o = 0; o < n; ++o) {
+        Eval &ev = o == 0 ? plan->ev : plan->more[o - 1];
+        ev.X.t = t; ev.X.v = x;
+        if (!ev.acf) { ev.Y.t = s; ev.Y.v = y; }
+        // one statistics pass (set 0) for every option set
+        ncf_status rc = launch(ctx, ev, /*stats_fresh=*/o > 0, /*guard=*/true, c_out[o], b_out ? b_out[o] : nullptr,
+                               count_out ? count_out[o] : nullptr, st, /*first=*/o == 0);
+        if (rc) return rc;
+    }
+    return NCF_OK;
+}
+
+int ncf_plan_option_sets(const ncf_plan *plan) { return plan ? 1 + (int)plan->more.size() : 0; }
 
 ncf_status ncf_plan_status(ncf_plan *plan, void *stream, int32_t *flags) {
     if (!plan || !flags) return NCF_EINVAL;
@@ -1647,7 +1710,12 @@ ncf_status ncf_plan_status(ncf_plan *plan, void *stream, int32_t *flags) {
     return NCF_OK;
 }
 
-size_t ncf_plan_device_bytes(const ncf_plan *plan) { return plan ? plan->pre_cap + plan->main_cap : 0; }
+size_t ncf_plan_device_bytes(const ncf_plan *plan) {
+    if (!plan) return 0;
+    size_t b = plan->pre_cap + plan->main_cap;
+    for (size_t c : plan->more_cap) b += c;
+    return b;
+}
 
 ncf_status ncf_workspace_bytes(ncf_ctx *ctx, int64_t n_x, int64_t n_y, int64_t B, int64_t K, double span,
                                double max_abs_lag, const ncf_options *opt, size_t *device_bytes,
@@ -1709,6 +1777,7 @@ void ncf_plan_destroy(ncf_plan *plan) {
     cudaDeviceSynchronize();
     if (plan->pre) cudaFree(plan->pre);
     if (plan->main) cudaFree(plan->main);
+    for (char *m : plan->more_main) if (m) cudaFree(m);
     delete plan;
 }
 

@@ -529,6 +529,124 @@ __global__ void spectrum_kernel(const typename CT<R>::V *__restrict__ Gx,
 
 
 // ---------------------------------------------------------------------------
+// FFT and spectrum of one series' grid in shared memory (FP32 ACFs on grids of
+// up to 2^14 cells): one CTA per series reads its spread grid from HBM once,
+// transforms it in place in shared memory and writes only the weighted power
+// spectra -- instead of lg / 3 global Stockham passes that each read and write
+// the whole batch, and a spectrum pass that reads it once more.
+//   load      the grid into shared memory, padded by one cell per 32 so that the
+//             late passes, whose lanes step across blocks, fall on distinct bank
+//             pairs;
+//   fft       in-place decimation-in-frequency passes of radix 8 (then 4 or 2):
+//             for a block of length Lb, butterfly j takes the R cells at stride
+//             Lb / R, applies the R-point DFT and the twiddles w_Lb^(j r), read
+//             as the product of two 128-entry tables in shared memory; the
+//             transform ends at digit-reversed positions;
+//   spectrum  modes m and n_f - m read from their digit-reversed positions,
+//             Hermitian unpack, wgt_m |X_m|^2 and wgt_m |W_m|^2 into the A rows
+//             (zero beyond the kept modes), as spectrum_kernel.
+// ---------------------------------------------------------------------------
+constexpr int kSmemFftThreads = 512;
+constexpr int kSmemFftMaxLg = 14;
+constexpr int kSmemFftTw = 128;  // entries of each twiddle table
+
+__host__ __device__ __forceinline__ int sfft_pad(int i) { return i + (i >> 5); }
+inline size_t sfft_smem_bytes(int lg) {
+    return (size_t)sfft_pad(1 << lg) * sizeof(float2) + 2 * kSmemFftTw * sizeof(float2);
+}
+
+// position of frequency k after the in-place passes (radix 8 while >= 3 bits
+// remain, then 4 or 2): its mixed-radix digits, first pass's digit least
+// significant, placed at the passes' strides
+__device__ __forceinline__ int sfft_pos(int k, int lg) {
+    int pos = 0;
+    for (int Llg = lg; Llg > 0;) {
+        const int rlg = Llg >= 3 ? 3 : Llg;
+        pos += (k & ((1 << rlg) - 1)) << (Llg - rlg);
+        k >>= rlg;
+        Llg -= rlg;
+    }
+    return pos;
+}
+
+// exp(+2 pi i q / n_f) = T1[q >> 7] T2[q & 127]
+__device__ __forceinline__ float2 sfft_tw(const float2 *T1, const float2 *T2, int q) {
+    return cmul(T1[q >> 7], T2[q & (kSmemFftTw - 1)]);
+}
+
+template <int R>
+__device__ __forceinline__ void sfft_pass(float2 *g, int lg, int Llg, const float2 *T1, const float2 *T2) {
+    constexpr int rlg = R == 8 ? 3 : (R == 4 ? 2 : 1);
+    const int slg = Llg - rlg;   // log2 of the butterfly stride Lb / R
+    const int blg = lg - Llg;    // log2 of the number of blocks (= n_f / Lb)
+    const int nbf = 1 << (lg - rlg);
+    for (int t = threadIdx.x; t < nbf; t += kSmemFftThreads) {
+        int j, blk;
+        if (slg >= 5) {          // lanes along j: consecutive cells
+            j = t & ((1 << slg) - 1);
+            blk = t >> slg;
+        } else {                 // lanes along blocks: padded cells on distinct bank pairs
+            blk = t & ((1 << blg) - 1);
+            j = t >> blg;
+        }
+        const int base = (blk << Llg) + j;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = g[sfft_pad(base + (r << slg))];
+        dft<R>(v);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], sfft_tw(T1, T2, (j * r) << blg));
+#pragma unroll
+        for (int r = 0; r < R; ++r) g[sfft_pad(base + (r << slg))] = v[r];
+    }
+}
+
+__global__ void __launch_bounds__(kSmemFftThreads)
+fft_spectrum_smem_kernel(const float2 *__restrict__ grids, int lg, int64_t M, int64_t Mp,
+                         const float2 *__restrict__ tw, const float *__restrict__ wgt, float *__restrict__ Anum,
+                         float *__restrict__ Aden) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nf = 1 << lg, nfm = nf - 1;
+    float2 *g = reinterpret_cast<float2 *>(smem_raw);
+    float2 *T1 = g + sfft_pad(nf), *T2 = T1 + kSmemFftTw;
+    const int64_t b = blockIdx.x;
+    const float4 *src = reinterpret_cast<const float4 *>(grids + b * (int64_t)nf);  // two cells per load
+    for (int i = threadIdx.x; i < nf / 2; i += kSmemFftThreads) {
+        const float4 v = src[i];
+        g[sfft_pad(2 * i)] = make_float2(v.x, v.y);
+        g[sfft_pad(2 * i + 1)] = make_float2(v.z, v.w);
+    }
+    for (int i = threadIdx.x; i < kSmemFftTw; i += kSmemFftThreads) {
+        T1[i] = (i << 7) < nf ? tw[i << 7] : make_float2(1.0f, 0.0f);
+        T2[i] = i < nf ? tw[i] : make_float2(1.0f, 0.0f);
+    }
+    for (int Llg = lg; Llg > 0;) {
+        const int rlg = Llg >= 3 ? 3 : Llg;
+        __syncthreads();
+        if (rlg == 3) sfft_pass<8>(g, lg, Llg, T1, T2);
+        else if (rlg == 2) sfft_pass<4>(g, lg, Llg, T1, T2);
+        else sfft_pass<2>(g, lg, Llg, T1, T2);
+        Llg -= rlg;
+    }
+    __syncthreads();
+    float *an = Anum + b * Mp, *ad = Aden + b * Mp;
+    for (int m = threadIdx.x; m < Mp; m += kSmemFftThreads) {
+        float vn = 0.0f, vd = 0.0f;
+        if (m < M) {
+            const float2 a = g[sfft_pad(sfft_pos(m, lg))];
+            const float2 c = g[sfft_pad(sfft_pos((nf - m) & nfm, lg))];
+            const float Xr = (a.x + c.x) * 0.5f, Xi = (a.y - c.y) * 0.5f;
+            const float Wr = (a.y + c.y) * 0.5f, Wi = (c.x - a.x) * 0.5f;
+            vn = wgt[m] * (Xr * Xr + Xi * Xi);
+            vd = wgt[m] * (Wr * Wr + Wi * Wi);
+        }
+        an[m] = vn;
+        ad[m] = vd;
+    }
+}
+
+
+// ---------------------------------------------------------------------------
 // contraction: acc[c][b][k] += sum_{m in chunk} A_c[b][m] E[m][k], c = num, den
 // ---------------------------------------------------------------------------
 constexpr int kBM = 32, kBN = 64, kBK = 32, kChunk = 512;
@@ -733,6 +851,40 @@ void prepare_typed(const SpectralPrepared &p, char *ws, const double *h_tc,
                lag_table_kernel<R><<<grid, 128, 0, st>>>(bf.d_phi, p.Mp, p.Kp, p.K1, ccf, bf.E));
 }
 
+// Contraction of the A rows with the lag table, then the normalisation.
+template <typename R>
+ncf_status contract_and_finish(const SpectralArgs &a, const SpectralPrepared &p, const Bufs<R> &bf, int *status,
+                               cudaStream_t st, std::string *msg) {
+    const int64_t B = p.B;
+    const bool ccf = !p.acf;
+    cudaMemsetAsync(bf.acc_num, 0, B * p.Kp * 8, st);
+    cudaMemsetAsync(bf.acc_den, 0, B * p.Kp * 8, st);
+    if constexpr (std::is_same<R, float>::value) {
+        // FP32 form: tensor cores (TF32 split products, FP64 chunk sums)
+        launch_contract_tc(bf.Anum, bf.Aden, bf.E, B, p.M2, p.Kp, bf.acc_num, bf.acc_den, status, st);
+    } else {
+        dim3 grid((unsigned)((p.Kp + kBN - 1) / kBN), (unsigned)((B + kBM - 1) / kBM),
+                  (unsigned)((p.M2 + kChunk - 1) / kChunk));
+        NCF_LAUNCH("contract_kernel", st,
+                   contract_kernel<R><<<grid, 256, 0, st>>>(bf.Anum, bf.Aden, bf.E, B, p.M2, p.Kp, bf.acc_num,
+                                                            bf.acc_den));
+    }
+    const int mode = p.lag0 ? (ccf ? 2 : 1) : 0;
+    NCF_LAUNCH("finish_spectral_kernel", st,
+               finish_spectral_kernel<<<(unsigned)((B * p.K + 255) / 256), 256, 0, st>>>(
+                   bf.acc_num, bf.acc_den, B, p.K, p.Kp, mode, bf.lag0, status,
+                   std::is_same<R, float>::value ? reinterpret_cast<const float *>(bf.Anum) : nullptr,
+                   std::is_same<R, float>::value ? reinterpret_cast<const float *>(bf.Aden) : nullptr, p.M2,
+                   a.c_out, a.b_out, a.count_out));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *msg = std::string("spectral path launch failed: ") + cudaGetErrorString(e);
+        return NCF_ECUDA;
+    }
+    return NCF_OK;
+}
+
+
 template <typename R>
 ncf_status launch_typed(const SpectralArgs &a, const SpectralPrepared &p, char *ws, int *status,
                         cudaStream_t st, std::string *msg) {
@@ -792,6 +944,21 @@ ncf_status launch_typed(const SpectralArgs &a, const SpectralPrepared &p, char *
         }
         return in;
     };
+    if constexpr (std::is_same<R, float>::value) {
+        if (!ccf && p.lg <= kSmemFftMaxLg && p.lg >= 7) {
+            // ACF on a grid that fits shared memory: FFT and spectrum per series there
+            const size_t smem = sfft_smem_bytes(p.lg);
+            static std::atomic<unsigned long long> sfft_done{0};
+            once_per_device(sfft_done,
+                            [&] { return set_smem_limit(fft_spectrum_smem_kernel, sfft_smem_bytes(kSmemFftMaxLg)); });
+            NCF_LAUNCH("fft_spectrum_smem_kernel", st,
+                       fft_spectrum_smem_kernel<<<(unsigned)B, kSmemFftThreads, smem, st>>>(
+                           reinterpret_cast<const float2 *>(bf.grid_x), p.lg, p.M, p.Mp,
+                           reinterpret_cast<const float2 *>(bf.tw), reinterpret_cast<const float *>(bf.wgt),
+                           reinterpret_cast<float *>(bf.Anum), reinterpret_cast<float *>(bf.Aden)));
+            return contract_and_finish(a, p, bf, status, st, msg);
+        }
+    }
     V *Gx = fft(bf.grid_x);
     if (Gx == bf.scratch && ccf) {
         // keep x's transform out of the scratch buffer before y's passes
@@ -808,31 +975,7 @@ ncf_status launch_typed(const SpectralArgs &a, const SpectralPrepared &p, char *
                    spectrum_kernel<R><<<grid, 256, 0, st>>>(Gx, Gy, p.nf, p.M, p.Mp, B, bf.wgt, bf.Anum,
                                                             bf.Aden, lag0_ccf ? bf.lag0 : nullptr));
     }
-    cudaMemsetAsync(bf.acc_num, 0, B * p.Kp * 8, st);
-    cudaMemsetAsync(bf.acc_den, 0, B * p.Kp * 8, st);
-    if constexpr (std::is_same<R, float>::value) {
-        // FP32 form: tensor cores (TF32 split products, FP64 chunk sums)
-        launch_contract_tc(bf.Anum, bf.Aden, bf.E, B, p.M2, p.Kp, bf.acc_num, bf.acc_den, status, st);
-    } else {
-        dim3 grid((unsigned)((p.Kp + kBN - 1) / kBN), (unsigned)((B + kBM - 1) / kBM),
-                  (unsigned)((p.M2 + kChunk - 1) / kChunk));
-        NCF_LAUNCH("contract_kernel", st,
-                   contract_kernel<R><<<grid, 256, 0, st>>>(bf.Anum, bf.Aden, bf.E, B, p.M2, p.Kp, bf.acc_num,
-                                                            bf.acc_den));
-    }
-    const int mode = p.lag0 ? (ccf ? 2 : 1) : 0;
-    NCF_LAUNCH("finish_spectral_kernel", st,
-               finish_spectral_kernel<<<(unsigned)((B * p.K + 255) / 256), 256, 0, st>>>(
-                   bf.acc_num, bf.acc_den, B, p.K, p.Kp, mode, bf.lag0, status,
-                   std::is_same<R, float>::value ? reinterpret_cast<const float *>(bf.Anum) : nullptr,
-                   std::is_same<R, float>::value ? reinterpret_cast<const float *>(bf.Aden) : nullptr, p.M2,
-                   a.c_out, a.b_out, a.count_out));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        *msg = std::string("spectral path launch failed: ") + cudaGetErrorString(e);
-        return NCF_ECUDA;
-    }
-    return NCF_OK;
+    return contract_and_finish(a, p, bf, status, st, msg);
 }
 
 // Checks, on the device, that every series of an executed plan still fits the
