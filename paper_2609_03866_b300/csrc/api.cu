@@ -866,16 +866,28 @@ static ncf_status corr_batch_multi_impl(ncf_ctx *ctx, const int64_t *offs_x, con
     if ((rc = grow(ctx, &ctx->ws, &ctx->ws_cap, pre_bytes(ev), st))) return rc;
     carve_pre(ev, ctx->ws);
     if ((rc = analyze(ctx, ev, lags, st))) return rc;
+    // The host prepares each option set after the statistics read-back while the
+    // GPU runs what is already queued: the long real-space scans go first, so the
+    // spectral sets' host preparation hides behind them.
+    std::vector<Eval> evs(n_opts, ev);  // the sides, their statistics and the lags, shared
+    std::vector<int> order(n_opts);
     for (int o = 0; o < n_opts; ++o) {
-        Eval eo = ev;  // the sides, their statistics and the lags, shared
-        eo.opt = opts[o];
-        eo.path = paths[o];
-        eo.lag0 = opts[o].norm == NCF_NORM_LAG0;
-        choose_path(eo);
+        evs[o].opt = opts[o];
+        evs[o].path = paths[o];
+        evs[o].lag0 = opts[o].norm == NCF_NORM_LAG0;
+        choose_path(evs[o]);
+        order[o] = o;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (evs[a].path == NCF_PATH_SPECTRAL) < (evs[b].path == NCF_PATH_SPECTRAL);
+    });
+    for (int q = 0; q < n_opts; ++q) {
+        const int o = order[q];
+        Eval &eo = evs[o];
         size_t dev = 0, pin = 0;
         if ((rc = main_bytes(ctx, eo, &dev, &pin))) return rc;
         // the pinned staging may still feed the previous option set's uploads
-        if (o > 0 && ctx->staged) NCF_CUDA(cudaEventSynchronize(ctx->staged));
+        if (q > 0 && ctx->staged) NCF_CUDA(cudaEventSynchronize(ctx->staged));
         if ((rc = grow(ctx, &ctx->ws2, &ctx->ws2_cap, dev, st))) return rc;
         if ((rc = grow_pinned(ctx, pin, st))) return rc;
         if ((rc = prepare(ctx, eo, ctx->ws2, ctx->ws2_cap, ctx->pinned, ctx->pinned_cap, lags, st))) return rc;
