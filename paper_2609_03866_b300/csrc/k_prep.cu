@@ -114,15 +114,25 @@ __global__ void stats_finish_kernel(const double *__restrict__ t, const double *
                                     const int64_t *__restrict__ chunk_base, int64_t B,
                                     const ChunkPartial *__restrict__ part,
                                     SeriesStats *__restrict__ stats) {
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per series: lane l sums chunks l, l + 32, ..., then a butterfly over
+    // the lanes (a fixed order: the same sums on every run)
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (b >= B) return;
     double s1 = 0.0, s2 = 0.0;
     int flags = 0;
-    for (int64_t g = chunk_base[b]; g < chunk_base[b + 1]; ++g) {
+    for (int64_t g = chunk_base[b] + lane; g < chunk_base[b + 1]; g += 32) {
         s1 += part[g].s1;
         s2 += part[g].s2;
         flags |= part[g].flags;
     }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        flags |= __shfl_xor_sync(0xffffffffu, flags, o);
+    }
+    if (lane != 0) return;
     const int64_t a0 = offs[b], a1 = offs[b + 1];
     const double n = (double)(a1 - a0);
     const double m1 = s1 / n;
@@ -297,7 +307,7 @@ void launch_stats_finish(const double *t, const double *x, const int64_t *offs,
                          const int64_t *chunk_base, int64_t B, const ChunkPartial *part,
                          SeriesStats *stats, cudaStream_t st) {
     NCF_LAUNCH("stats_finish_kernel", st,
-    stats_finish_kernel<<<(unsigned)((B + 127) / 128), 128, 0, st>>>(t, x, offs, chunk_base, B, part, stats));
+    stats_finish_kernel<<<(unsigned)((B * 32 + 127) / 128), 128, 0, st>>>(t, x, offs, chunk_base, B, part, stats));
 }
 
 void launch_keys_prefix(const double *t, const double *x, const int64_t *offs,

@@ -180,19 +180,39 @@ inline unsigned twiddle_blocks(int n) { return (unsigned)((n / kTwRun + 255) / 2
 // formed exactly in 64-bit fixed point: Phi_k = frac(tau_k / L) 2^64, and
 // m Phi_k mod 2^64 is an exact integer product.
 template <typename R>
+__device__ __forceinline__ void lag_sincos(unsigned long long ph, R &c, R &s);
+// FP64 table: sin and cos of 2 pi ph 2^-64 from the 53 leading bits
+template <>
+__device__ __forceinline__ void lag_sincos<double>(unsigned long long ph, double &c, double &s) {
+    const double p = (double)(ph >> 11) * 0x1.0p-53;  // [0, 1)
+    sincospi(2.0 * p, &s, &c);
+}
+// FP32 table, FP32 arithmetic only: the phase splits exactly into a = the leading
+// 24 bits and b < 2^-24 (the next 24 bits); sin and cos of 2 pi a by the FP32
+// function, then one first-order step to a + b (the dropped term is below
+// (2 pi 2^-24)^2 / 2 < 1e-13).  Within a few FP32 ulps, which is what the table is
+// stored in (an FP64 sincospi per entry cost 13 ms for 2.8e8 entries).
+template <>
+__device__ __forceinline__ void lag_sincos<float>(unsigned long long ph, float &c, float &s) {
+    const float a = (float)(unsigned)(ph >> 40) * 0x1.0p-24f;                          // exact
+    const float b = (float)(unsigned)((ph >> 16) & 0xFFFFFFu) * 0x1.0p-48f;            // exact, < 2^-24
+    float sa, ca;
+    sincospif(2.0f * a, &sa, &ca);
+    const float d = 6.28318530717958647692f * b;
+    c = fmaf(-d, sa, ca);
+    s = fmaf(d, ca, sa);
+}
+
+template <typename R>
 __global__ void lag_table_kernel(const unsigned long long *__restrict__ Phi, int64_t Mp, int64_t Kp,
                                  int64_t K1, bool with_sin, R *__restrict__ E) {
     const int64_t k = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     const int64_t m = blockIdx.x;
     if (k >= Kp) return;
-    double c = 0.0, s = 0.0;
-    if (k < K1) {
-        const unsigned long long ph = (unsigned long long)m * Phi[k];
-        const double p = (double)(ph >> 11) * 0x1.0p-53;  // [0, 1)
-        sincospi(2.0 * p, &s, &c);
-    }
-    E[m * Kp + k] = (R)c;
-    if (with_sin) E[(Mp + m) * Kp + k] = (R)s;
+    R c = (R)0, s = (R)0;
+    if (k < K1) lag_sincos<R>((unsigned long long)m * Phi[k], c, s);
+    E[m * Kp + k] = c;
+    if (with_sin) E[(Mp + m) * Kp + k] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -773,6 +793,11 @@ void make_plan(const SpectralArgs &a, double max_span, SpectralPrepared &p) {
     p.Kp = (p.K1 + 3) / 4 * 4;
     p.M2 = a.acf ? p.Mp : 2 * p.Mp;
     p.fp32 = a.fp32;
+    // One FP64 series: the mode sums at the lags directly (exact 64-bit phases, 6
+    // FP64 operations per mode and lag) instead of a [modes x lags] table whose
+    // entries each cost an FP64 sincospi and are read once.  A batch shares the
+    // table across its series and keeps it.
+    p.direct = !a.fp32 && a.B == 1;
     p.kernel = a.kernel;
     p.acf = a.acf;
     p.lag0 = a.lag0;
@@ -787,6 +812,7 @@ struct Bufs {
     typename CT<R>::V *grid_x, *grid_y, *scratch, *tw;
     double *wgt64;
     R *wgt, *Anum, *Aden, *E;
+    double2 *Apk;  // direct mode sums: the rows as complex spectra
     double *acc_num, *acc_den, *lag0, *d_tc;
     unsigned long long *d_phi;
     double *d_gx, *d_gphi;
@@ -809,7 +835,8 @@ Bufs<R> carve(const SpectralPrepared &p, char *ws) {
     b.wgt = take<R>(ws, used, p.Mp);
     b.Anum = take<R>(ws, used, B * p.M2);
     b.Aden = take<R>(ws, used, B * p.M2);
-    b.E = take<R>(ws, used, p.M2 * p.Kp);
+    b.E = take<R>(ws, used, p.direct ? 0 : p.M2 * p.Kp);
+    b.Apk = take<double2>(ws, used, p.direct ? 2 * p.Mp : 0);
     b.acc_num = take<double>(ws, used, B * p.Kp);
     b.acc_den = take<double>(ws, used, B * p.Kp);
     b.lag0 = take<double>(ws, used, 4 * B);
@@ -846,9 +873,21 @@ void prepare_typed(const SpectralPrepared &p, char *ws, const double *h_tc,
     if (std::is_same<R, double>::value)
         cudaMemcpyAsync(bf.wgt, bf.wgt64, p.Mp * 8, cudaMemcpyDeviceToDevice, st);
     NCF_LAUNCH("twiddle_kernel", st, twiddle_kernel<V><<<twiddle_blocks(p.nf), 256, 0, st>>>(bf.tw, p.nf));
-    dim3 grid((unsigned)p.Mp, (unsigned)((p.Kp + 127) / 128));
-    NCF_LAUNCH("lag_table_kernel", st,
-               lag_table_kernel<R><<<grid, 128, 0, st>>>(bf.d_phi, p.Mp, p.Kp, p.K1, ccf, bf.E));
+    if (!p.direct) {
+        dim3 grid((unsigned)p.Mp, (unsigned)((p.Kp + 127) / 128));
+        NCF_LAUNCH("lag_table_kernel", st,
+                   lag_table_kernel<R><<<grid, 128, 0, st>>>(bf.d_phi, p.Mp, p.Kp, p.K1, ccf, bf.E));
+    }
+}
+
+// The FP64 spectra rows of one series as complex values (cos row, sin row; an
+// ACF's sin row is zero) for the direct mode sums.
+__global__ void pack_rows_kernel(const double *__restrict__ num, const double *__restrict__ den, int64_t Mp,
+                                 bool ccf, double2 *__restrict__ out) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Mp) return;
+    out[m] = make_double2(num[m], ccf ? num[Mp + m] : 0.0);
+    out[Mp + m] = make_double2(den[m], ccf ? den[Mp + m] : 0.0);
 }
 
 // Contraction of the A rows with the lag table, then the normalisation.
@@ -862,6 +901,14 @@ ncf_status contract_and_finish(const SpectralArgs &a, const SpectralPrepared &p,
     if constexpr (std::is_same<R, float>::value) {
         // FP32 form: tensor cores (TF32 split products, FP64 chunk sums)
         launch_contract_tc(bf.Anum, bf.Aden, bf.E, B, p.M2, p.Kp, bf.acc_num, bf.acc_den, status, st);
+    } else if (p.direct) {
+        // N_k = sum_m Re(A_m exp(-2 pi i m tau_k / L)), A_m = (cos row, sin row) of
+        // the spectra, at the K + 1 lags (with the appended zero lag)
+        NCF_LAUNCH("pack_rows_kernel", st,
+                   pack_rows_kernel<<<(unsigned)((p.Mp + 255) / 256), 256, 0, st>>>(
+                       reinterpret_cast<const double *>(bf.Anum), reinterpret_cast<const double *>(bf.Aden), p.Mp,
+                       ccf, bf.Apk));
+        paper_eval(bf.Apk, p.Mp - 1, bf.d_phi, p.K1, bf.acc_num, st, bf.Apk + p.Mp, bf.acc_den);
     } else {
         dim3 grid((unsigned)((p.Kp + kBN - 1) / kBN), (unsigned)((B + kBM - 1) / kBM),
                   (unsigned)((p.M2 + kChunk - 1) / kChunk));

@@ -40,6 +40,7 @@ struct SpectralPrepared {
     int64_t M = 0, Mp = 0, K1 = 0, Kp = 0, M2 = 0, B = 0, K = 0;
     int nf = 0, lg = 0, W = 8, nq = 64;
     bool fp32 = false, acf = true, lag0 = false;
+    bool direct = false;  // one FP64 series: mode sums at the lags, no lag table
     int kernel = 0;
     std::vector<double> tc, gx, gphi, poly;
     std::vector<unsigned long long> phi;
