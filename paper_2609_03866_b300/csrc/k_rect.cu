@@ -321,11 +321,11 @@ rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
 // ---------------------------------------------------------------------------
 constexpr int kPtWarps = 8;
 constexpr int kPtM = kRectTile / (kPtWarps * 32);  // outer points per lane
+constexpr int kPtBatch = 4;                         // points of a lane handled together (load ILP)
 // Lane l of warp w owns points (q kPtWarps + w) 32 + l, q < kPtM: each warp's
 // groups of 32 consecutive points are spread over the whole tile, so dense and
 // sparse stretches of a tile fall evenly on the warps.
-constexpr int kPtStride = kPtWarps * 32;
-constexpr int kPtBatch = 4;                         // points of a lane handled together (load ILP)
+__device__ __forceinline__ constexpr int pt_off(int q) { return q * (kPtWarps * 32); }
 constexpr int kPtCap = 5300;                        // staged entries per sub-group
 constexpr int kPtSamples = 1024;                    // planning samples of a lag group's key range
 constexpr int kPtExact = 16;                        // sample stride up to which the bounds stay coarse
@@ -499,9 +499,10 @@ struct PtLagArgs {
 // One lag over this lane's outer points of the segment [pa, pb) (the whole
 // full tile when kFull).  Points are handled kPtBatch at a time: the rank-table
 // and entry loads of a batch are issued together; an edge whose bin holds keys
-// below its query steps forward in a warp-uniform loop that is rarely entered
-// (about 0.25 keys per query on the light-curve batch), and so is the band
-// test's FP64 fix-up; then the counts and the numerators.  Edge positions are
+// below its query steps forward in a warp-uniform loop per batch slot (about
+// 0.25 keys per query on the light-curve batch, but over a warp's 32 lanes the
+// loop runs to the largest count), then the rarely entered band test's FP64
+// fix-up, then the counts and the numerators.  Edge positions are
 // shared-window byte addresses of staged entries (16 bytes each).
 template <bool kFull>
 __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (&sc)[kPtM],
@@ -513,7 +514,7 @@ __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (
         bool ok[kPtBatch];
 #pragma unroll
         for (int i = 0; i < kPtBatch; ++i) {
-            const int pt = pbase + kPtStride * (q0 + i);
+            const int pt = pbase + pt_off(q0 + i);
             ok[i] = kFull || (pt >= g.pa && pt < g.pb);
             s[i] = ok[i] ? sc[q0 + i] : sca;  // a point outside the segment queries in range, counts nothing
         }
@@ -537,13 +538,14 @@ __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (
             el[i] = lds_v4(ol[i]);
             eh[i] = lds_v4(oh[i]);
         }
-        bool step = false;
+        // one warp-uniform walk per batch slot rather than one over the whole
+        // batch: a slot's 32 points are consecutive, so their edges lie in one
+        // short stretch of time, and a slot whose stretch falls between clusters
+        // of keys skips the walk however long its neighbours' walks are
 #pragma unroll
-        for (int i = 0; i < kPtBatch; ++i) step |= (el[i].x < s[i] + L.x) | (eh[i].x < s[i] + L.z);
-        while (__any_sync(0xffffffffu, step)) {
-            step = false;
-#pragma unroll
-            for (int i = 0; i < kPtBatch; ++i) {
+        for (int i = 0; i < kPtBatch; ++i) {
+            bool step = (el[i].x < s[i] + L.x) | (eh[i].x < s[i] + L.z);
+            while (__any_sync(0xffffffffu, step)) {
                 if (el[i].x < s[i] + L.x) {
                     ol[i] += 16u;
                     el[i] = lds_v4(ol[i]);
@@ -552,7 +554,7 @@ __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (
                     oh[i] += 16u;
                     eh[i] = lds_v4(oh[i]);
                 }
-                step |= (el[i].x < s[i] + L.x) | (eh[i].x < s[i] + L.z);
+                step = (el[i].x < s[i] + L.x) | (eh[i].x < s[i] + L.z);
             }
         }
         bool band = false;
@@ -564,7 +566,7 @@ __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (
                 const bool fl = el[i].x < s[i] + L.y, fh = eh[i].x < s[i] + L.w;
                 if (ok[i] && (fl || fh)) {
                     const int2 r = pt_band(g.Tx, g.tx, g.Sy, g.sy, g.dls, g.dus, g.slags,
-                                           g.j0 + pbase + kPtStride * (q0 + i), g.k, g.eps, g.h, g.eta, g.ia_s, g.lim,
+                                           g.j0 + pbase + pt_off(q0 + i), g.k, g.eps, g.h, g.eta, g.ia_s, g.lim,
                                            (int)((ol[i] - aE) >> 4), (int)((oh[i] - aE) >> 4), fl, fh);
                     ol[i] = aE + 16u * (unsigned)r.x;
                     oh[i] = aE + 16u * (unsigned)r.y;
@@ -629,7 +631,7 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
     const int pbase = warp * 32 + lane;
 #pragma unroll
     for (int q = 0; q < kPtM; ++q) {
-        const int pt = pbase + kPtStride * q;
+        const int pt = pbase + pt_off(q);
         const int64_t Y = pt < tn ? Yq[tile.j0 + pt] : 0;
         sc[q] = pt < tn ? (int32_t)((Sy[tile.j0 + pt] - S0) >> sh) : 0;
         y0[q] = (int32_t)(Y & 0x7fffffffll);
@@ -870,7 +872,7 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                     unsigned int c = 0;
                     U128 acc{0ull, 0ull};
                     for (int q = 0; q < kPtM; ++q) {
-                        const int pt = pbase + kPtStride * q;
+                        const int pt = pbase + pt_off(q);
                         if (pt < pa || pt >= pb) continue;
                         const int64_t j = tile.j0 + pt;
                         const int64_t Lf = Sy[j] + dl, Uf = Sy[j] + du;
