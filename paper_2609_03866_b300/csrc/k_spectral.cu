@@ -813,6 +813,7 @@ struct Bufs {
     double *wgt64;
     R *wgt, *Anum, *Aden, *E;
     double2 *Apk;  // direct mode sums: the rows as complex spectra
+    unsigned char *At, *Et;  // FP32 form: operand tiles of the tensor-core contraction
     double *acc_num, *acc_den, *lag0, *d_tc;
     unsigned long long *d_phi;
     double *d_gx, *d_gphi;
@@ -837,6 +838,9 @@ Bufs<R> carve(const SpectralPrepared &p, char *ws) {
     b.Aden = take<R>(ws, used, B * p.M2);
     b.E = take<R>(ws, used, p.direct ? 0 : p.M2 * p.Kp);
     b.Apk = take<double2>(ws, used, p.direct ? 2 * p.Mp : 0);
+    const bool tc = std::is_same<R, float>::value && !p.direct;
+    b.At = take<unsigned char>(ws, used, tc ? tc_a_tiles_bytes(B, p.M2) : 0);
+    b.Et = take<unsigned char>(ws, used, tc ? tc_e_tiles_bytes(p.M2, p.Kp) : 0);
     b.acc_num = take<double>(ws, used, B * p.Kp);
     b.acc_den = take<double>(ws, used, B * p.Kp);
     b.lag0 = take<double>(ws, used, 4 * B);
@@ -877,6 +881,8 @@ void prepare_typed(const SpectralPrepared &p, char *ws, const double *h_tc,
         dim3 grid((unsigned)p.Mp, (unsigned)((p.Kp + 127) / 128));
         NCF_LAUNCH("lag_table_kernel", st,
                    lag_table_kernel<R><<<grid, 128, 0, st>>>(bf.d_phi, p.Mp, p.Kp, p.K1, ccf, bf.E));
+        if constexpr (std::is_same<R, float>::value)
+            launch_tc_pack_e(reinterpret_cast<const float *>(bf.E), p.M2, p.Kp, bf.Et, st);
     }
 }
 
@@ -900,7 +906,8 @@ ncf_status contract_and_finish(const SpectralArgs &a, const SpectralPrepared &p,
     cudaMemsetAsync(bf.acc_den, 0, B * p.Kp * 8, st);
     if constexpr (std::is_same<R, float>::value) {
         // FP32 form: tensor cores (TF32 split products, FP64 chunk sums)
-        launch_contract_tc(bf.Anum, bf.Aden, bf.E, B, p.M2, p.Kp, bf.acc_num, bf.acc_den, status, st);
+        launch_tc_pack_a(bf.Anum, bf.Aden, B, p.M2, bf.At, st);
+        launch_contract_tc(bf.At, bf.Et, B, p.M2, p.Kp, a.sm_count, bf.acc_num, bf.acc_den, status, st);
     } else if (p.direct) {
         // N_k = sum_m Re(A_m exp(-2 pi i m tau_k / L)), A_m = (cos row, sin row) of
         // the spectra, at the K + 1 lags (with the appended zero lag)

@@ -61,11 +61,18 @@ void spectral_guard(const SpectralArgs &a, const SpectralPrepared &p, char *ws, 
                     cudaStream_t st);
 
 // Tensor-core contraction of the FP32 form (k_tc.cu): acc_c += A_c E over all
-// modes, TF32 split products, FP32 TMEM accumulation per 128-mode chunk, FP64
-// partial sums.  *status becomes nonzero if a bounded wait gave up.
+// modes, TF32 split products, FP32 TMEM accumulation per chunk of modes, FP64
+// partial sums.  The operands are first packed into split, swizzled tiles
+// (launch_tc_pack_a per execution, launch_tc_pack_e when the lag table is
+// made).  *status becomes nonzero if a bounded wait gave up.
 bool contract_tc_supported(int64_t M2);
-void launch_contract_tc(const float *Anum, const float *Aden, const float *E, int64_t B, int64_t M2,
-                        int64_t Kp, double *acc_num, double *acc_den, int *status, cudaStream_t st);
+size_t tc_a_tiles_bytes(int64_t B, int64_t M2);
+size_t tc_e_tiles_bytes(int64_t M2, int64_t Kp);
+void launch_tc_pack_a(const float *Anum, const float *Aden, int64_t B, int64_t M2, unsigned char *At,
+                      cudaStream_t st);
+void launch_tc_pack_e(const float *E, int64_t M2, int64_t Kp, unsigned char *Et, cudaStream_t st);
+void launch_contract_tc(const unsigned char *At, const unsigned char *Et, int64_t B, int64_t M2, int64_t Kp,
+                        int sm_count, double *acc_num, double *acc_den, int *status, cudaStream_t st);
 
 // FP64 forward FFT passes shared with the regular-grid path (k_spectral.cu).
 void fft_twiddles_f64(double2 *tw, int lg, cudaStream_t st);
