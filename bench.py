@@ -700,6 +700,7 @@ def main():
         g_step.replay()
     torch.cuda.synchronize()
     plan = ctx.last_plan()
+    tuned = ctx.last_tuning()
 
     # ---- timed region: graph replays of the step ----
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -887,6 +888,14 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "B": B, "K": K, "points": n_pts, "h": H,
                    "grid": nf, "modes": M, "period_d": plan["period"], "graph": True,
+                   "tuned": {"rect_scan": ["lags on lanes, runs of 16", "lags on lanes, runs of 32",
+                                           "lags on lanes, runs of 64",
+                                           "outer points on lanes"][tuned["rect_variant"]]
+                             if tuned["rect_variant"] >= 0 else None,
+                             "fft": {0: "shared-memory FFT fused with the spectrum", 1: "global Stockham passes"}
+                             .get(tuned["fft_variant"]),
+                             "contraction": {0: "tensor cores (tcgen05, split TF32)", 1: "FP32 pipe"}
+                             .get(tuned["contract_variant"])},
                    "l2": f"inputs larger than L2 ({(w.t.nbytes + w.x.nbytes) / 1e9:.2f} GB per step)"},
         "per_estimator": {
             "note": "each estimator alone: its own plan and graph, statistics pass included",

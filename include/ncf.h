@@ -144,6 +144,26 @@ typedef struct {
 NCF_API ncf_status ncf_last_plan(const ncf_ctx *ctx, ncf_plan_info *out);
 
 /*
+ * The autotuner's choices for the most recent evaluation of each kind on this
+ * context (-1: none made yet).  rect_variant: the exact rectangle scan's design
+ * (0, 1, 2: lags on lanes with runs of 16, 32, 64 outer points; 3: outer points
+ * on lanes).  For the FP32 spectral form: fft_variant 0 = the FFT of an ACF grid
+ * of 2^7..2^14 cells in shared memory, fused with its spectrum, 1 = global
+ * Stockham passes (the only choice for larger grids and for CCFs);
+ * contract_variant 0 = mode-to-lag contraction on tensor cores, 1 = on the FP32
+ * pipe.  Each choice is the fastest of its candidates when first timed for a
+ * problem bucket (device, sizes in powers of two, ACF/CCF), and is kept for the
+ * process; NCF_RECT_VARIANT and NCF_SPEC_VARIANT (bit 0 fft, bit 1 contraction)
+ * in the environment pin them.  The estimators' results agree between variants:
+ * bit for bit on the rectangle scan, within the FP32 form's error otherwise.
+ * No counterpart in the paper (an implementation choice).
+ */
+typedef struct {
+    int32_t rect_variant, fft_variant, contract_variant, reserved;
+} ncf_tuning;
+NCF_API ncf_status ncf_last_tuning(const ncf_ctx *ctx, ncf_tuning *out);
+
+/*
  * Kernel profiler.  While enabled, every kernel the context launches is
  * bracketed by two CUDA events recorded on its launch stream.
  * ncf_profile_report synchronises on the recorded events, folds them into

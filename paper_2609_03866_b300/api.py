@@ -53,6 +53,11 @@ class ncf_plan_info(ctypes.Structure):
                 ("width", ctypes.c_int64), ("B", ctypes.c_int64), ("K", ctypes.c_int64)]
 
 
+class ncf_tuning(ctypes.Structure):
+    _fields_ = [("rect_variant", ctypes.c_int32), ("fft_variant", ctypes.c_int32),
+                ("contract_variant", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class NcfError(RuntimeError):
     def __init__(self, status: int, name: str, message: str):
         super().__init__(f"{name}: {message}")
@@ -92,6 +97,8 @@ def lib():
             L.ncf_device_bytes.restype = ctypes.c_size_t
             L.ncf_last_plan.argtypes = [vp, ctypes.POINTER(ncf_plan_info)]
             L.ncf_last_plan.restype = ctypes.c_int
+            L.ncf_last_tuning.argtypes = [vp, ctypes.POINTER(ncf_tuning)]
+            L.ncf_last_tuning.restype = ctypes.c_int
             L.ncf_profile_enable.argtypes = [vp, ctypes.c_int]
             L.ncf_profile_enable.restype = ctypes.c_int
             L.ncf_profile_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
@@ -198,6 +205,13 @@ class Context:
         info = ncf_plan_info()
         self.check(lib().ncf_last_plan(self._h, ctypes.byref(info)))
         return {f: getattr(info, f) for f, _ in ncf_plan_info._fields_}
+
+    def last_tuning(self) -> dict:
+        """The autotuner's latest choices (ncf_last_tuning): rect_variant,
+        fft_variant, contract_variant; -1 where none was made yet."""
+        info = ncf_tuning()
+        self.check(lib().ncf_last_tuning(self._h, ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in ncf_tuning._fields_ if f != "reserved"}
 
     def profile(self, on: bool = True):
         """Bracket every kernel launch of this context with CUDA events."""

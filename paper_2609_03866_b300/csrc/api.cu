@@ -60,6 +60,7 @@ struct ncf_ctx {
     std::vector<cudaEvent_t> copy_ev;
     NcfProfiler prof;
     ncf_plan_info plan{0.0, 0, 0, 0, 0, 0};
+    ncf_tuning tuning{-1, -1, -1, 0};
     std::string err;
 };
 
@@ -755,6 +756,7 @@ ncf_status tune_rect(ncf_ctx *ctx, Eval &ev, cudaStream_t st) {
         const int v = std::atoi(pin);
         if (v >= 0 && v < kRectVariants) {
             ev.r_main.variant = ev.r_x.variant = ev.r_y.variant = v;
+            ctx->tuning.rect_variant = v;
             return NCF_OK;
         }
     }
@@ -764,6 +766,7 @@ ncf_status tune_rect(ncf_ctx *ctx, Eval &ev, cudaStream_t st) {
         auto it = g_tune_rect.find(key);
         if (it != g_tune_rect.end()) {
             ev.r_main.variant = ev.r_x.variant = ev.r_y.variant = it->second;
+            ctx->tuning.rect_variant = it->second;
             return NCF_OK;
         }
     }
@@ -801,6 +804,95 @@ ncf_status tune_rect(ncf_ctx *ctx, Eval &ev, cudaStream_t st) {
         g_tune_rect[key] = best;
     }
     ev.r_main.variant = ev.r_x.variant = ev.r_y.variant = best;
+    ctx->tuning.rect_variant = best;
+    return NCF_OK;
+}
+
+
+// Autotuned FP32 spectral shapes per (device, problem bucket): the FFT of an ACF
+// grid that fits shared memory (there, fused with its spectrum, or as global
+// passes) and the mode-to-lag contraction (tensor cores or the FP32 pipe).  The
+// candidates agree within the FP32 form's error, not bit for bit; the one kept
+// is the fastest on the first batch of its bucket, and the caller's evaluation
+// then runs with it.
+std::map<std::pair<int, uint64_t>, int> g_tune_spec;
+constexpr int kSpecVariants = 4;  // bit 0: global-pass FFT; bit 1: FP32-pipe contraction
+
+uint64_t spec_tune_key(const Eval &ev) {
+    auto lg = [](double v) { return (uint64_t)std::max(0.0, std::floor(std::log2(std::max(v, 1.0)))); };
+    return lg((double)ev.B) | ((uint64_t)ev.sp.lg << 8) | (lg((double)ev.K) << 16) | ((uint64_t)ev.acf << 24) |
+           ((uint64_t)ev.sp.kernel << 25);
+}
+
+void set_spec_variant(ncf_ctx *ctx, Eval &ev, int v) {
+    ev.sp.fft_variant = v & 1;
+    ev.sp.contract_variant = (v >> 1) & 1;
+    // the shared-memory FFT applies to ACF grids of 2^7..2^14 cells only
+    const bool fft_choice = ev.acf && ev.sp.lg >= 7 && ev.sp.lg <= 14;
+    ctx->tuning.fft_variant = fft_choice ? ev.sp.fft_variant : 1;
+    ctx->tuning.contract_variant = ev.sp.contract_variant;
+}
+
+ncf_status tune_spectral(ncf_ctx *ctx, Eval &ev, cudaStream_t st) {
+    if (rect_scan(ev) || ev.path == NCF_PATH_WINDOWED || !ev.sp.fp32 || ev.sp.direct) return NCF_OK;
+    // NCF_SPEC_VARIANT=0..3 pins the shapes (tests, measurements) and skips the timing
+    if (const char *pin = std::getenv("NCF_SPEC_VARIANT")) {
+        const int v = std::atoi(pin);
+        if (v >= 0 && v < kSpecVariants) {
+            set_spec_variant(ctx, ev, v);
+            return NCF_OK;
+        }
+    }
+    const std::pair<int, uint64_t> key{ctx->device, spec_tune_key(ev)};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_spec.find(key);
+        if (it != g_tune_spec.end()) {
+            set_spec_variant(ctx, ev, it->second);
+            return NCF_OK;
+        }
+    }
+    // the FFT choice exists only where the shared-memory FFT applies
+    const bool fft_choice = ev.acf && ev.sp.lg >= 7 && ev.sp.lg <= 14;
+    std::vector<int> cands;
+    for (int v = 0; v < kSpecVariants; ++v)
+        if (fft_choice || !(v & 1)) cands.push_back(v);
+    // scratch outputs: the timing runs write results that the evaluation proper overwrites
+    const int64_t BK = ev.B * ev.K;
+    double *scratch = nullptr;
+    NCF_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&scratch), (size_t)BK * 24, st));
+    SpectralArgs sa = spectral_args(ev, scratch, scratch + BK, reinterpret_cast<int64_t *>(scratch + 2 * BK));
+    std::vector<cudaEvent_t> e(cands.size() + 1);
+    for (auto &x : e) NCF_CUDA(cudaEventCreate(&x));
+    std::string msg;
+    ncf_status rc = NCF_OK;
+    NCF_CUDA(cudaEventRecord(e[0], st));
+    for (size_t i = 0; i < cands.size() && !rc; ++i) {
+        set_spec_variant(ctx, ev, cands[i]);
+        rc = spectral_launch(sa, ev.sp, ev.spec_ws, ev.status, st, &msg);
+        cudaEventRecord(e[i + 1], st);
+    }
+    int best = 0;
+    if (!rc) {
+        NCF_CUDA(cudaEventSynchronize(e.back()));
+        float best_ms = 1e30f;
+        for (size_t i = 0; i < cands.size(); ++i) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e[i], e[i + 1]);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cands[i];
+            }
+        }
+    }
+    for (auto &x : e) cudaEventDestroy(x);
+    cudaFreeAsync(scratch, st);
+    if (rc) return fail(ctx, rc, "%s", msg.c_str());
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_spec[key] = best;
+    }
+    set_spec_variant(ctx, ev, best);
     return NCF_OK;
 }
 
@@ -838,6 +930,7 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
     if ((rc = prepare(ctx, ev, ctx->ws2, ctx->ws2_cap, ctx->pinned, ctx->pinned_cap, lags, st))) return rc;
     NCF_CUDA(cudaEventRecord(ctx->staged, st));
     if (rect_scan(ev) && (rc = tune_rect(ctx, ev, st))) return rc;
+    if ((rc = tune_spectral(ctx, ev, st))) return rc;
     return launch(ctx, ev, /*stats_fresh=*/true, /*guard=*/false, c_out, b_out, count_out, st);
 }
 
@@ -893,6 +986,7 @@ static ncf_status corr_batch_multi_impl(ncf_ctx *ctx, const int64_t *offs_x, con
         if ((rc = prepare(ctx, eo, ctx->ws2, ctx->ws2_cap, ctx->pinned, ctx->pinned_cap, lags, st))) return rc;
         NCF_CUDA(cudaEventRecord(ctx->staged, st));
         if (rect_scan(eo) && (rc = tune_rect(ctx, eo, st))) return rc;
+        if ((rc = tune_spectral(ctx, eo, st))) return rc;
         if ((rc = launch(ctx, eo, /*stats_fresh=*/true, /*guard=*/false, c_out[o], b_out ? b_out[o] : nullptr,
                          count_out ? count_out[o] : nullptr, st)))
             return rc;
@@ -1175,6 +1269,12 @@ void ncf_destroy(ncf_ctx *ctx) {
 ncf_status ncf_last_plan(const ncf_ctx *ctx, ncf_plan_info *out) {
     if (!ctx || !out) return NCF_EINVAL;
     *out = ctx->plan;
+    return NCF_OK;
+}
+
+ncf_status ncf_last_tuning(const ncf_ctx *ctx, ncf_tuning *out) {
+    if (!ctx || !out) return NCF_EINVAL;
+    *out = ctx->tuning;
     return NCF_OK;
 }
 
@@ -1648,6 +1748,7 @@ ncf_status ncf_plan_create_multi(ncf_ctx *ctx, const int64_t *offs_x, const doub
         if ((rc = grow_pinned(ctx, pin, st))) return bail(rc);
         if ((rc = prepare(ctx, eo, mem, dev, ctx->pinned, ctx->pinned_cap, lags, st))) return bail(rc);
         if (rect_scan(eo) && (rc = tune_rect(ctx, eo, st))) return bail(rc);
+        if ((rc = tune_spectral(ctx, eo, st))) return bail(rc);
         // the pinned staging is reused by the next option set's tables
         if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(ctx, NCF_ECUDA, "plan set-up failed"));
     }

@@ -904,9 +904,10 @@ ncf_status contract_and_finish(const SpectralArgs &a, const SpectralPrepared &p,
     const bool ccf = !p.acf;
     cudaMemsetAsync(bf.acc_num, 0, B * p.Kp * 8, st);
     cudaMemsetAsync(bf.acc_den, 0, B * p.Kp * 8, st);
-    if constexpr (std::is_same<R, float>::value) {
+    if (std::is_same<R, float>::value && p.contract_variant == 0) {
         // FP32 form: tensor cores (TF32 split products, FP64 chunk sums)
-        launch_tc_pack_a(bf.Anum, bf.Aden, B, p.M2, bf.At, st);
+        launch_tc_pack_a(reinterpret_cast<const float *>(bf.Anum), reinterpret_cast<const float *>(bf.Aden), B,
+                         p.M2, bf.At, st);
         launch_contract_tc(bf.At, bf.Et, B, p.M2, p.Kp, a.sm_count, bf.acc_num, bf.acc_den, status, st);
     } else if (p.direct) {
         // N_k = sum_m Re(A_m exp(-2 pi i m tau_k / L)), A_m = (cos row, sin row) of
@@ -924,11 +925,13 @@ ncf_status contract_and_finish(const SpectralArgs &a, const SpectralPrepared &p,
                                                             bf.acc_den));
     }
     const int mode = p.lag0 ? (ccf ? 2 : 1) : 0;
+    // the tensor-core contraction leaves out the m = 0 term, which the finish adds in FP64
+    const bool m0_apart = std::is_same<R, float>::value && p.contract_variant == 0;
     NCF_LAUNCH("finish_spectral_kernel", st,
                finish_spectral_kernel<<<(unsigned)((B * p.K + 255) / 256), 256, 0, st>>>(
                    bf.acc_num, bf.acc_den, B, p.K, p.Kp, mode, bf.lag0, status,
-                   std::is_same<R, float>::value ? reinterpret_cast<const float *>(bf.Anum) : nullptr,
-                   std::is_same<R, float>::value ? reinterpret_cast<const float *>(bf.Aden) : nullptr, p.M2,
+                   m0_apart ? reinterpret_cast<const float *>(bf.Anum) : nullptr,
+                   m0_apart ? reinterpret_cast<const float *>(bf.Aden) : nullptr, p.M2,
                    a.c_out, a.b_out, a.count_out));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -999,7 +1002,7 @@ ncf_status launch_typed(const SpectralArgs &a, const SpectralPrepared &p, char *
         return in;
     };
     if constexpr (std::is_same<R, float>::value) {
-        if (!ccf && p.lg <= kSmemFftMaxLg && p.lg >= 7) {
+        if (!ccf && p.lg <= kSmemFftMaxLg && p.lg >= 7 && p.fft_variant == 0) {
             // ACF on a grid that fits shared memory: FFT and spectrum per series there
             const size_t smem = sfft_smem_bytes(p.lg);
             static std::atomic<unsigned long long> sfft_done{0};

@@ -41,6 +41,10 @@ struct SpectralPrepared {
     int nf = 0, lg = 0, W = 8, nq = 64;
     bool fp32 = false, acf = true, lag0 = false;
     bool direct = false;  // one FP64 series: mode sums at the lags, no lag table
+    // FP32 shapes chosen by the autotuner: FFT of an ACF grid of 2^7..2^14 cells in
+    // shared memory fused with its spectrum (0) or as global passes (1); the
+    // contraction on tensor cores (0) or on the FP32 pipe (1)
+    int fft_variant = 0, contract_variant = 0;
     int kernel = 0;
     std::vector<double> tc, gx, gphi, poly;
     std::vector<unsigned long long> phi;
