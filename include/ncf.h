@@ -135,11 +135,16 @@ NCF_API size_t ncf_device_bytes(const ncf_ctx *ctx);
  * Geometry of the most recent spectral call on this context: the common
  * period L of the Fourier series, the number of modes kept (m = 0 .. modes-1),
  * the oversampled grid size n_f, the spreading kernel width (cells), and the
- * batch size B and lag count K it served.  All zero before any spectral call.
+ * batch size B and lag count K it served.  A batch whose series need grids of
+ * very different sizes is split into `buckets` of series sharing a grid size,
+ * each on its own period and grid (per-series grid sizing; Algorithm 1 applied
+ * to each bucket's spans); period, modes and grid then describe the largest
+ * bucket, and buckets = 1 means one grid for the batch.  All zero before any
+ * spectral call.
  */
 typedef struct {
     double period;
-    int64_t modes, grid, width, B, K;
+    int64_t modes, grid, width, B, K, buckets;
 } ncf_plan_info;
 NCF_API ncf_status ncf_last_plan(const ncf_ctx *ctx, ncf_plan_info *out);
 

@@ -50,7 +50,8 @@ class ncf_pooled_stats(ctypes.Structure):
 
 class ncf_plan_info(ctypes.Structure):
     _fields_ = [("period", ctypes.c_double), ("modes", ctypes.c_int64), ("grid", ctypes.c_int64),
-                ("width", ctypes.c_int64), ("B", ctypes.c_int64), ("K", ctypes.c_int64)]
+                ("width", ctypes.c_int64), ("B", ctypes.c_int64), ("K", ctypes.c_int64),
+                ("buckets", ctypes.c_int64)]
 
 
 class ncf_tuning(ctypes.Structure):

@@ -59,7 +59,7 @@ struct ncf_ctx {
     cudaStream_t copy_st = nullptr;  // host-buffer calls: uploads and read-backs beside the compute stream
     std::vector<cudaEvent_t> copy_ev;
     NcfProfiler prof;
-    ncf_plan_info plan{0.0, 0, 0, 0, 0, 0};
+    ncf_plan_info plan{0.0, 0, 0, 0, 0, 0, 0};
     ncf_tuning tuning{-1, -1, -1, 0};
     std::string err;
 };
@@ -620,7 +620,8 @@ ncf_status prepare(ncf_ctx *ctx, Eval &ev, char *mem, size_t cap, char *pinned, 
     }
     ev.spec_ws = mem + a2.used;  // the spectral workspace starts here (256-aligned)
     spectral_prepare(ev.sp, ev.spec_ws, pinned, st);
-    ctx->plan = ncf_plan_info{ev.sp.L, ev.sp.M, ev.sp.nf, ev.sp.W, B, K};
+    ctx->plan = ncf_plan_info{ev.sp.L, ev.sp.M, ev.sp.nf, ev.sp.W, B, K,
+                              std::max<int64_t>(1, (int64_t)ev.sp.buckets.size())};
     return NCF_OK;
 }
 
@@ -1876,6 +1877,9 @@ ncf_status ncf_workspace_bytes(ncf_ctx *ctx, int64_t n_x, int64_t n_y, int64_t B
         ev.path = pth;
         size_t d = 0, p = 0;
         if ((rc = main_bytes(ctx, ev, &d, &p))) return rc;
+        // a spectral batch of mixed spans may be split into grid-size buckets:
+        // no more device memory than one grid, a little more host staging
+        if (pth == NCF_PATH_SPECTRAL) p += spectral_bucket_pinned_allowance(B, K, n_x, acf ? 0 : n_y, !acf);
         dev = std::max(dev, d);
         pin = std::max(pin, p);
     }

@@ -302,7 +302,8 @@ template <> struct PointPhase<double> {
 template <typename R, int W>
 __global__ void __launch_bounds__(kSpreadThreads)
 spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
-              const int64_t *__restrict__ offs, const int64_t *__restrict__ chunk_base,
+              const int64_t *__restrict__ offs, const int64_t *__restrict__ offs_end,
+              const int64_t *__restrict__ chunk_base,
               const int32_t *__restrict__ cs,
               const SeriesStats *__restrict__ st, const double *__restrict__ tc, double a_scale,
               int nf, const EsPoly<R, W, PolyDeg<W>::D> poly, typename CT<R>::V *__restrict__ grids) {
@@ -315,7 +316,7 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
     int *sl = reinterpret_cast<int *>(sx + kStagePad);
     const int64_t g = blockIdx.x;
     const int64_t b = cs[g];
-    const int64_t a0 = offs[b], a1 = offs[b + 1];
+    const int64_t a0 = offs[b], a1 = offs_end[b];
     const int64_t start = a0 + (g - chunk_base[b]) * (int64_t)kPrepChunk;
     const int n = (int)(min(start + (int64_t)kPrepChunk, a1) - start);
     const double c_off = -tc[b] * a_scale - 0.5 * W + nf;
@@ -731,17 +732,18 @@ __global__ void finish_spectral_kernel(const double *__restrict__ acc_num,
                                        int64_t Kp, int lag0_mode, const double *__restrict__ lag0,
                                        const int *__restrict__ status, const float *__restrict__ dc_num,
                                        const float *__restrict__ dc_den, int64_t row,
-                                       double *__restrict__ c, double *__restrict__ bo,
-                                       int64_t *__restrict__ cnt) {
+                                       const int64_t *__restrict__ row_map, double *__restrict__ c,
+                                       double *__restrict__ bo, int64_t *__restrict__ cnt) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * K) return;
+    const int64_t b = i / K, k = i - b * K;
+    const int64_t o = (row_map ? row_map[b] : b) * K + k;  // output element (a bucket's series keep their rows)
     if (*status != 0) {  // a bounded device wait gave up: no valid result
-        c[i] = __longlong_as_double(0x7ff8000000000000ll);
-        if (bo) bo[i] = c[i];
-        if (cnt) cnt[i] = -1;
+        c[o] = __longlong_as_double(0x7ff8000000000000ll);
+        if (bo) bo[o] = c[o];
+        if (cnt) cnt[o] = -1;
         return;
     }
-    const int64_t b = i / K, k = i - b * K;
     // m = 0 terms kept out of the tensor-core sums (cos 0 = 1, sin 0 = 0)
     const double n0 = dc_num ? (double)dc_num[b * row] : 0.0, d0 = dc_den ? (double)dc_den[b * row] : 0.0;
     const double N = acc_num[b * Kp + k] + n0, D = acc_den[b * Kp + k] + d0;
@@ -753,9 +755,9 @@ __global__ void finish_spectral_kernel(const double *__restrict__ acc_num,
         const double sy = lag0[4 * b + 2] / fmax(lag0[4 * b + 3], 1e-16);
         ci /= sqrt(sx * sy);
     }
-    c[i] = ci;
-    if (bo) bo[i] = D;
-    if (cnt) cnt[i] = 0;
+    c[o] = ci;
+    if (bo) bo[o] = D;
+    if (cnt) cnt[o] = 0;
 }
 
 template <typename T>
@@ -931,7 +933,7 @@ ncf_status contract_and_finish(const SpectralArgs &a, const SpectralPrepared &p,
                finish_spectral_kernel<<<(unsigned)((B * p.K + 255) / 256), 256, 0, st>>>(
                    bf.acc_num, bf.acc_den, B, p.K, p.Kp, mode, bf.lag0, status,
                    m0_apart ? reinterpret_cast<const float *>(bf.Anum) : nullptr,
-                   m0_apart ? reinterpret_cast<const float *>(bf.Aden) : nullptr, p.M2,
+                   m0_apart ? reinterpret_cast<const float *>(bf.Aden) : nullptr, p.M2, a.row_map,
                    a.c_out, a.b_out, a.count_out));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -964,15 +966,16 @@ ncf_status launch_typed(const SpectralArgs &a, const SpectralPrepared &p, char *
     }
     auto spread = [&](const SpecSide &sd, V *grid) {
         cudaMemsetAsync(grid, 0, B * (size_t)p.nf * sizeof(V), st);
+        const int64_t *offs_end = sd.d_offs_end ? sd.d_offs_end : sd.d_offs + 1;
         if (p.W == 8)
             NCF_LAUNCH("spread_kernel", st,
                        spread_kernel<R, 8><<<(unsigned)sd.n_chunks, kSpreadThreads, smem, st>>>(
-                           sd.t, sd.v, sd.d_offs, sd.d_chunk_base, sd.d_cs, sd.d_stats, bf.d_tc, a_scale,
+                           sd.t, sd.v, sd.d_offs, offs_end, sd.d_chunk_base, sd.d_cs, sd.d_stats, bf.d_tc, a_scale,
                            p.nf, poly8, grid));
         else
             NCF_LAUNCH("spread_kernel", st,
                        spread_kernel<R, 16><<<(unsigned)sd.n_chunks, kSpreadThreads, smem, st>>>(
-                           sd.t, sd.v, sd.d_offs, sd.d_chunk_base, sd.d_cs, sd.d_stats, bf.d_tc, a_scale,
+                           sd.t, sd.v, sd.d_offs, offs_end, sd.d_chunk_base, sd.d_cs, sd.d_stats, bf.d_tc, a_scale,
                            p.nf, poly16, grid));
     };
     spread(a.x, bf.grid_x);
@@ -1257,7 +1260,8 @@ void paper_modes_run(const PaperModes &pm, const SpecSide &x, const SpecSide *y,
         cudaMemsetAsync(grid, 0, (size_t)pm.nf * sizeof(double2), st);
         NCF_LAUNCH("spread_kernel", st,
                    spread_kernel<double, 16><<<(unsigned)sd.n_chunks, kSpreadThreads, smem, st>>>(
-                       sd.t, sd.v, sd.d_offs, sd.d_chunk_base, sd.d_cs, sd.d_stats, bf.d_tc, a_scale, pm.nf,
+                       sd.t, sd.v, sd.d_offs, sd.d_offs + 1, sd.d_chunk_base, sd.d_cs, sd.d_stats, bf.d_tc,
+                       a_scale, pm.nf,
                        poly, grid));
     };
     spread(x, bf.grid_x);
@@ -1295,8 +1299,226 @@ void paper_type2(const PaperModes &pm, bool ccf, char *ws, const double2 *A, con
                    G, pm.lg, phi, K, poly, c)));
 }
 
+// ---------------------------------------------------------------------------
+// Per-series grid sizing: a batch whose series need grids of very different
+// sizes (spans) is split into buckets of series needing the same grid size;
+// each bucket runs the whole path on its own period, grid and lag table.  A
+// bucket names its series by index (their points stay where they are: the
+// spreading reads each series' own [start, end) range), its statistics are
+// gathered from the batch's at every launch, and its results go to the series'
+// own output rows.
+// ---------------------------------------------------------------------------
+struct SpectralBucket {
+    std::vector<int64_t> idx;             // series of the batch, ascending
+    std::vector<SeriesStats> hsx, hsy;    // their host statistics (planning)
+    SpectralPrepared p;                   // the bucket's own plan
+    size_t ws_off = 0, pin_off = 0;       // its workspace and staging
+    size_t tab_off = 0, tab_pin_off = 0;  // its index tables (device, staging)
+    std::vector<char> tab_img;            // host image of the index tables
+    int64_t nx_total = 0, nx_max = 0, nx_chunks = 0, ny_total = 0, ny_max = 0, ny_chunks = 0;
+};
+
+struct BucketTabs {
+    size_t row, xlo, xend, xcb, csx, sx, ylo, yend, ycb, csy, sy, bytes;
+};
+BucketTabs bucket_tabs(const SpectralBucket &bk, bool ccf) {
+    BucketTabs t{};
+    size_t u = 0;
+    const size_t Bk = bk.idx.size();
+    auto take = [&](size_t n) {
+        const size_t o = u;
+        u += al(n);
+        return o;
+    };
+    t.row = take(Bk * 8);
+    t.xlo = take(Bk * 8);
+    t.xend = take(Bk * 8);
+    t.xcb = take((Bk + 1) * 8);
+    t.csx = take((size_t)bk.nx_chunks * 4);
+    t.sx = take(Bk * sizeof(SeriesStats));
+    if (ccf) {
+        t.ylo = take(Bk * 8);
+        t.yend = take(Bk * 8);
+        t.ycb = take((Bk + 1) * 8);
+        t.csy = take((size_t)bk.ny_chunks * 4);
+        t.sy = take(Bk * sizeof(SeriesStats));
+    }
+    t.bytes = u;
+    return t;
+}
+
+__global__ void gather_stats_kernel(const SeriesStats *__restrict__ src, const int64_t *__restrict__ idx, int64_t n,
+                                    SeriesStats *__restrict__ dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[idx[i]];
+}
+
+// The bucket's arguments: the batch's points, the bucket's index tables and
+// gathered statistics, output rows through the row map.
+SpectralArgs bucket_args(const SpectralArgs &a, const SpectralBucket &bk, char *ws, cudaStream_t st) {
+    const bool ccf = !a.acf;
+    const BucketTabs t = bucket_tabs(bk, ccf);
+    char *tb = ws + bk.tab_off;
+    const int64_t Bk = (int64_t)bk.idx.size();
+    const int64_t *row = reinterpret_cast<const int64_t *>(tb + t.row);
+    SeriesStats *sx = reinterpret_cast<SeriesStats *>(tb + t.sx);
+    NCF_LAUNCH("gather_stats_kernel", st,
+               gather_stats_kernel<<<(unsigned)((Bk + 255) / 256), 256, 0, st>>>(a.x.d_stats, row, Bk, sx));
+    SpectralArgs ab = a;
+    ab.B = Bk;
+    ab.row_map = row;
+    ab.no_buckets = true;
+    ab.x = {a.x.t, a.x.v, reinterpret_cast<const int64_t *>(tb + t.xlo), sx, nullptr, bk.hsx.data(), bk.nx_total,
+            bk.nx_max, reinterpret_cast<const int64_t *>(tb + t.xcb), bk.nx_chunks,
+            reinterpret_cast<const int32_t *>(tb + t.csx), reinterpret_cast<const int64_t *>(tb + t.xend)};
+    if (ccf) {
+        SeriesStats *sy = reinterpret_cast<SeriesStats *>(tb + t.sy);
+        NCF_LAUNCH("gather_stats_kernel", st,
+                   gather_stats_kernel<<<(unsigned)((Bk + 255) / 256), 256, 0, st>>>(a.y.d_stats, row, Bk, sy));
+        ab.y = {a.y.t, a.y.v, reinterpret_cast<const int64_t *>(tb + t.ylo), sy, nullptr, bk.hsy.data(),
+                bk.ny_total, bk.ny_max, reinterpret_cast<const int64_t *>(tb + t.ycb), bk.ny_chunks,
+                reinterpret_cast<const int32_t *>(tb + t.csy), reinterpret_cast<const int64_t *>(tb + t.yend)};
+    }
+    return ab;
+}
+
+// Buckets by grid size when the per-series grids would hold at most 3/4 of the
+// cells of one common grid and the buckets' device memory is no more than one
+// grid's (NCF_SPEC_BUCKETS=0 keeps one grid).  Their host staging (each
+// bucket's tables) is bounded by spectral_bucket_pinned_allowance.  Returns
+// false when the batch keeps one grid.
+bool plan_buckets(const SpectralArgs &a, SpectralPrepared &out, size_t *ws_bytes, size_t *pinned_bytes,
+                  std::string *msg, ncf_status *rc) {
+    *rc = NCF_OK;
+    const int64_t B = a.B;
+    const bool ccf = !a.acf;
+    if (a.no_buckets || B < 2 || !a.x.h_offs || (ccf && !a.y.h_offs)) return false;
+    if (const char *e = std::getenv("NCF_SPEC_BUCKETS"))
+        if (std::atoi(e) == 0) return false;
+    std::vector<int> lgs(B);
+    int lg_max = 0;
+    for (int64_t b = 0; b < B; ++b) {
+        double lo = a.x.h_stats[b].t_first, hi = a.x.h_stats[b].t_last;
+        if (ccf) {
+            lo = std::min(lo, a.y.h_stats[b].t_first);
+            hi = std::max(hi, a.y.h_stats[b].t_last);
+        }
+        SpectralPrepared q;
+        make_plan(a, hi - lo, q);
+        lgs[b] = q.lg;
+        lg_max = std::max(lg_max, q.lg);
+    }
+    double cells_sum = 0.0;
+    std::vector<int> levels;
+    for (int64_t b = 0; b < B; ++b) {
+        cells_sum += std::ldexp(1.0, lgs[b]);
+        if (std::find(levels.begin(), levels.end(), lgs[b]) == levels.end()) levels.push_back(lgs[b]);
+    }
+    if (levels.size() < 2 || cells_sum > 0.75 * (double)B * std::ldexp(1.0, lg_max)) return false;
+    std::sort(levels.begin(), levels.end());
+    size_t ws = 0, pin = 0;
+    out.buckets.clear();
+    for (int lv : levels) {
+        auto bk = std::make_shared<SpectralBucket>();
+        for (int64_t b = 0; b < B; ++b)
+            if (lgs[b] == lv) bk->idx.push_back(b);
+        const int64_t Bk = (int64_t)bk->idx.size();
+        for (int64_t j = 0; j < Bk; ++j) {
+            bk->hsx.push_back(a.x.h_stats[bk->idx[j]]);
+            if (ccf) bk->hsy.push_back(a.y.h_stats[bk->idx[j]]);
+        }
+        SpectralArgs ak = a;
+        ak.B = Bk;
+        ak.no_buckets = true;
+        ak.x.h_stats = bk->hsx.data();
+        if (ccf) ak.y.h_stats = bk->hsy.data();
+        size_t wk = 0, pk = 0;
+        if ((*rc = spectral_plan(ak, &bk->p, &wk, &pk, msg))) return true;
+        bk->ws_off = ws;
+        ws += al(wk);
+        bk->pin_off = pin;
+        pin += al(pk);
+        // index tables: row map, [start, end) of each series, chunk tables
+        auto side = [&](const int64_t *offs, int64_t &total, int64_t &nmax, int64_t &nchunks,
+                        std::vector<int64_t> &lo, std::vector<int64_t> &end, std::vector<int64_t> &cb,
+                        std::vector<int32_t> &cs) {
+            cb.push_back(0);
+            for (int64_t j = 0; j < Bk; ++j) {
+                const int64_t b = bk->idx[j], n = offs[b + 1] - offs[b];
+                lo.push_back(offs[b]);
+                end.push_back(offs[b + 1]);
+                total += n;
+                nmax = std::max(nmax, n);
+                const int64_t c = (n + kPrepChunk - 1) / kPrepChunk;
+                for (int64_t q = 0; q < c; ++q) cs.push_back((int32_t)j);
+                cb.push_back(cb.back() + c);
+            }
+            nchunks = cb.back();
+        };
+        std::vector<int64_t> xlo, xend, xcb, ylo, yend, ycb;
+        std::vector<int32_t> csx, csy;
+        side(a.x.h_offs, bk->nx_total, bk->nx_max, bk->nx_chunks, xlo, xend, xcb, csx);
+        if (ccf) side(a.y.h_offs, bk->ny_total, bk->ny_max, bk->ny_chunks, ylo, yend, ycb, csy);
+        const BucketTabs t = bucket_tabs(*bk, ccf);
+        bk->tab_img.assign(t.bytes, 0);
+        auto put = [&](size_t off, const void *src, size_t bytes) {
+            if (bytes) std::memcpy(bk->tab_img.data() + off, src, bytes);
+        };
+        put(t.row, bk->idx.data(), Bk * 8);
+        put(t.xlo, xlo.data(), Bk * 8);
+        put(t.xend, xend.data(), Bk * 8);
+        put(t.xcb, xcb.data(), (Bk + 1) * 8);
+        put(t.csx, csx.data(), csx.size() * 4);
+        if (ccf) {
+            put(t.ylo, ylo.data(), Bk * 8);
+            put(t.yend, yend.data(), Bk * 8);
+            put(t.ycb, ycb.data(), (Bk + 1) * 8);
+            put(t.csy, csy.data(), csy.size() * 4);
+        }
+        bk->tab_off = ws;
+        ws += al(t.bytes);
+        bk->tab_pin_off = pin;
+        pin += al(t.bytes);
+        out.buckets.push_back(bk);
+    }
+    // split only where it also needs no more memory than one grid, so that a
+    // size-only bound (ncf_workspace_bytes) holds for either plan
+    {
+        SpectralArgs a1 = a;
+        a1.no_buckets = true;
+        SpectralPrepared one;
+        size_t w1 = 0, p1 = 0;
+        if ((*rc = spectral_plan(a1, &one, &w1, &p1, msg))) return true;
+        if (ws + 256 > w1) {
+            out.buckets.clear();
+            return false;
+        }
+    }
+    // the evaluation's geometry fields describe its largest grid
+    const SpectralPrepared &big = out.buckets.back()->p;
+    auto buckets = std::move(out.buckets);
+    out = big;
+    out.tc.clear();
+    out.phi.clear();
+    out.B = B;
+    out.direct = false;
+    out.buckets = std::move(buckets);
+    *ws_bytes = ws + 256;
+    *pinned_bytes = pin;
+    return true;
+}
+
 ncf_status spectral_plan(const SpectralArgs &a, SpectralPrepared *sp, size_t *ws_bytes,
                          size_t *pinned_bytes, std::string *msg) {
+    {
+        SpectralPrepared bp;
+        ncf_status rc = NCF_OK;
+        if (plan_buckets(a, bp, ws_bytes, pinned_bytes, msg, &rc)) {
+            if (rc) return rc;
+            *sp = std::move(bp);
+            return NCF_OK;
+        }
+    }
     const int64_t B = a.B;
     const bool ccf = !a.acf;
     // per-series centre t_c and the common period L (Algorithm 1 with an
@@ -1337,19 +1559,56 @@ ncf_status spectral_plan(const SpectralArgs &a, SpectralPrepared *sp, size_t *ws
     return NCF_OK;
 }
 
+// Host staging a split plan may need beyond one grid's: per bucket (at most
+// one per grid size, 2^1 .. 2^28 cells) its lag phases, quadrature tables and
+// index tables, each region aligned.
+size_t spectral_bucket_pinned_allowance(int64_t B, int64_t K, int64_t n_x, int64_t n_y, bool ccf) {
+    const size_t levels = 28;
+    const size_t per = al((size_t)(K + 4) * 8) + 2 * al(128 * 8) + 12 * 256;
+    auto side = [&](int64_t n) {
+        return 3 * al((size_t)B * 8) + al((size_t)(B + 1) * 8) + al((size_t)(n / kPrepChunk + B) * 4) +
+               al((size_t)B * sizeof(SeriesStats));
+    };
+    return levels * per + al((size_t)B * 8) + side(n_x) + (ccf ? side(n_y) : 0);
+}
+
 void spectral_prepare(const SpectralPrepared &p, char *ws, char *pinned, cudaStream_t st) {
+    if (!p.buckets.empty()) {
+        for (const auto &bk : p.buckets) {
+            spectral_prepare(bk->p, ws + bk->ws_off, pinned + bk->pin_off, st);
+            std::memcpy(pinned + bk->tab_pin_off, bk->tab_img.data(), bk->tab_img.size());
+            cudaMemcpyAsync(ws + bk->tab_off, pinned + bk->tab_pin_off, bk->tab_img.size(), cudaMemcpyHostToDevice,
+                            st);
+        }
+        return;
+    }
     if (p.fp32) prepare_typed<float>(p, ws, p.tc.data(), p.phi.data(), p.gx, p.gphi, pinned, st);
     else prepare_typed<double>(p, ws, p.tc.data(), p.phi.data(), p.gx, p.gphi, pinned, st);
 }
 
 ncf_status spectral_launch(const SpectralArgs &a, const SpectralPrepared &p, char *ws, int *status,
                            cudaStream_t st, std::string *msg) {
+    if (!p.buckets.empty()) {
+        for (const auto &bk : p.buckets) {
+            const SpectralArgs ab = bucket_args(a, *bk, ws, st);
+            bk->p.fft_variant = p.fft_variant;  // the shapes tuned for the evaluation
+            bk->p.contract_variant = p.contract_variant;
+            ncf_status rc = bk->p.fp32 ? launch_typed<float>(ab, bk->p, ws + bk->ws_off, status, st, msg)
+                                       : launch_typed<double>(ab, bk->p, ws + bk->ws_off, status, st, msg);
+            if (rc) return rc;
+        }
+        return NCF_OK;
+    }
     if (p.fp32) return launch_typed<float>(a, p, ws, status, st, msg);
     return launch_typed<double>(a, p, ws, status, st, msg);
 }
 
 void spectral_guard(const SpectralArgs &a, const SpectralPrepared &p, char *ws, int *status,
                     cudaStream_t st) {
+    if (!p.buckets.empty()) {
+        for (const auto &bk : p.buckets) spectral_guard(bucket_args(a, *bk, ws, st), bk->p, ws + bk->ws_off, status, st);
+        return;
+    }
     const double *d_tc = p.fp32 ? carve<float>(p, ws).d_tc : carve<double>(p, ws).d_tc;
     const double max_span = (p.L - p.max_tau - p.R_alias * p.h) * (1.0 + 1e-12);
     NCF_LAUNCH("spectral_guard_kernel", st,

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "common.cuh"
@@ -18,6 +19,7 @@ struct SpecSide {
     const int64_t *d_chunk_base = nullptr;    // device chunk table of the statistics pass
     int64_t n_chunks = 0;
     const int32_t *d_cs = nullptr;            // series of each chunk
+    const int64_t *d_offs_end = nullptr;      // device end offsets [B] (NULL: d_offs + 1)
 };
 
 struct SpectralArgs {
@@ -30,11 +32,18 @@ struct SpectralArgs {
     SpecSide x, y;
     double *c_out = nullptr, *b_out = nullptr;
     int64_t *count_out = nullptr;
+    const int64_t *row_map = nullptr;  // device [B]: output row of series b (NULL: b)
     int sm_count = 148;
+    bool no_buckets = false;           // plan one common grid (a bucket's own plan)
 };
 
+struct SpectralBucket;
+
 // Geometry and host tables of a spectral evaluation (spectral_plan), kept by
-// one-shot calls and by ncf_plan objects alike.
+// one-shot calls and by ncf_plan objects alike.  A batch whose series need grids
+// of very different sizes is split into buckets of series sharing a grid size,
+// each with its own plan (period, grid, lag table, workspace); the geometry
+// fields then describe the largest bucket.
 struct SpectralPrepared {
     double L = 0, beta = 0, R_alias = 0, h = 0, max_tau = 0;
     int64_t M = 0, Mp = 0, K1 = 0, Kp = 0, M2 = 0, B = 0, K = 0;
@@ -48,11 +57,14 @@ struct SpectralPrepared {
     int kernel = 0;
     std::vector<double> tc, gx, gphi, poly;
     std::vector<unsigned long long> phi;
+    std::vector<std::shared_ptr<SpectralBucket>> buckets;  // empty: one grid for the batch
 };
 
 // Host-side planning: geometry, tables, workspace sizes (device, pinned staging).
 ncf_status spectral_plan(const SpectralArgs &a, SpectralPrepared *sp, size_t *ws_bytes,
                          size_t *pinned_bytes, std::string *msg);
+// Host staging a plan split into grid-size buckets may need beyond one grid's.
+size_t spectral_bucket_pinned_allowance(int64_t B, int64_t K, int64_t n_x, int64_t n_y, bool ccf);
 // Uploads the host tables and builds the device tables (mode weights,
 // twiddles, lag table) in `ws`.
 void spectral_prepare(const SpectralPrepared &p, char *ws, char *pinned, cudaStream_t st);
