@@ -250,6 +250,29 @@ def regular_run(api, device, n=256_000, K=366, h=1.0):
     return out
 
 
+def spectral_k1024_run(api, device, B=1024, K=1024, h=0.5, reps=3):
+    """The FP32 form on 1024 light curves x 1024 lags (the serving config's
+    largest lag grid), Gaussian h = 0.5: a profiling workload for the
+    contraction (9 lag tiles) and the spreading.  Per-kernel times from the
+    context's profiler on the last of `reps` calls."""
+    import torch
+    from paper_2609_03866_b300 import synth
+    w = synth.light_curves(B=B, K=K)
+    dev = torch.device("cuda", device)
+    t, x, lags = (torch.as_tensor(a, device=dev) for a in (w.t, w.x, w.lags))
+    ctx = api.Context(device)
+    for i in range(reps):
+        if i == reps - 1:
+            ctx.profile_reset()
+            ctx.profile(True)
+        api.corr_batch(w.offs, t, x, lags, kernel="gaussian", h=h, path="spectral", precision="fp32", ctx=ctx)
+    torch.cuda.synchronize()
+    rep = ctx.profile_report()
+    ctx.close()
+    return {"workload": f"{B} light curves ({w.t.size} points) x {K} lags on [0, 200] d, Gaussian h = {h}, FP32 form",
+            "kernels_ms": {k: v[1] for k, v in sorted(rep.items(), key=lambda kv: -kv[1][1])}}
+
+
 def mixed_spans_run(api, device, B=4096, K=128, h=0.5, seed=29):
     """Per-series grid sizing: 4096 series whose spans are log-uniform in
     [20, 1460] d (uniform times, n log-uniform in [200, 2e4], a sinusoid plus
@@ -692,7 +715,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the serving, bootstrap, regular-grid, Hanning and paper-NUFFT legs")
     ap.add_argument("--batch", type=int, default=B_SERIES, help="series per rank (profiling runs)")
-    ap.add_argument("--only", choices=["paper", "hanning"], default=None,
+    ap.add_argument("--only", choices=["paper", "hanning", "spectral-k1024", "mixed-spans"], default=None,
                     help="run one side leg alone and print its JSON (profiling runs)")
     args = ap.parse_args()
 
@@ -712,6 +735,12 @@ def main():
         return
     if args.only == "hanning":
         print(json.dumps({"hanning": hanning_run(api, local)}))
+        return
+    if args.only == "spectral-k1024":
+        print(json.dumps({"spectral_k1024": spectral_k1024_run(api, local)}))
+        return
+    if args.only == "mixed-spans":
+        print(json.dumps({"per_series_grids": mixed_spans_run(api, local)}))
         return
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
