@@ -170,6 +170,35 @@ void launch_finish_gauss(const double *num, const double *den, const unsigned lo
                          int64_t B, int64_t K, const double *scale, const int *status, double *c,
                          double *b, int64_t *count, cudaStream_t st);
 
+
+#ifdef __CUDACC__
+// v as an unevaluated sum hi + lo of two floats (about 48 significant bits),
+// from the bit pattern when the exponent allows, else by conversion.  The
+// conversion path is out of line: inlined, the compiler predicates it into the
+// common path, and its FP64 conversions then occupy the (slow) FP64 pipe for
+// every value.
+static __device__ __noinline__ float2 split_df_slow(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+__device__ __forceinline__ void split_df(double v, float &hi, float &lo) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((u >> 52) & 0x7FF);
+    if (e >= 949 && e <= 1150) {
+        const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+        const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+        hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29));
+        const float scale = __uint_as_float((unsigned)(e - 948) << 23);  // 2^(e - 1075)
+        const float r = (float)(unsigned)(m & 0x1FFFFFFFull) * scale;
+        lo = sign ? -r : r;
+    } else {
+        const float2 f = split_df_slow(v);
+        hi = f.x;
+        lo = f.y;
+    }
+}
+#endif
+
 }  // namespace ncf
 
 namespace ncf {

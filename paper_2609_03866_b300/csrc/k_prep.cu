@@ -2,11 +2,13 @@
 // exact integer prefix sums.
 //
 // Standardisation (Appendix, "Prior standardization"; step 1 of Algorithms
-// 2, 4, 9, 10): mean and population variance (ddof 0) in FP64.  The pass is
-// chunked -- one CTA per `chunk` points of one series -- so a single series
-// of 1e7 points spreads over the whole GPU; sums are shifted by the series'
-// first value (x - x_ref) so that the one-pass variance S2/n - (S1/n)^2 does
-// not cancel, and partials are combined in a fixed order (deterministic).
+// 2, 4, 9, 10): mean and population variance (ddof 0).  The pass is chunked --
+// one CTA per `chunk` points of one series -- so a single series of 1e7 points
+// spreads over the whole GPU; sums are shifted by the series' first value
+// (d = x - x_ref, one FP64 subtraction) so that the one-pass variance
+// S2/n - (S1/n)^2 does not cancel.  Each thread sums its 16 points' d and d^2
+// in double-float (about 47 bits; the FP64 pipe would bound the pass), the
+// partials are combined in FP64 in a fixed order (deterministic).
 //
 // The exact rectangle scan works on fixed-point images of the inputs:
 //   T_i = floor(t_i * 2^q)  -- monotone, so comparisons against window bounds
@@ -56,6 +58,30 @@ __device__ __forceinline__ long long fixed_floor(double v, int q) {
     return neg ? -(long long)(mag + (rem ? 1 : 0)) : (long long)mag;
 }
 
+// Double-float arithmetic (an unevaluated sum h + l of two floats, about 47
+// significant bits): the statistics pass accumulates each thread's points this
+// way on the FP32 pipe, which runs many times the FP64 rate here.
+struct DF {
+    float h, l;
+};
+// sum of two double-float values (two-sum of the high parts, low parts added)
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = a.h + b.h;
+    const float v = s - a.h;
+    float e = (a.h - (s - v)) + (b.h - v);
+    e += a.l + b.l;
+    const float h = s + e;
+    return DF{h, e - (h - s)};
+}
+// square of a double-float value (exact product of the high parts by FMA)
+__device__ __forceinline__ DF df_sqr(DF a) {
+    const float p = a.h * a.h;
+    float e = fmaf(a.h, a.h, -p);
+    e = fmaf(2.0f * a.h, a.l, e);
+    const float h = p + e;
+    return DF{h, e - (h - p)};
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
@@ -71,28 +97,39 @@ stats_chunks_kernel(const double *__restrict__ t, const double *__restrict__ x,
     const int64_t start = a0 + (g - chunk_base[b]) * (int64_t)chunk;
     const int64_t end = min(start + (int64_t)chunk, a1);
     const double xref = x[a0];
-    double s1 = 0.0, s2 = 0.0;
+    DF f1{0.0f, 0.0f}, f2{0.0f, 0.0f};  // this thread's sums of d and d^2
     int flags = 0;
+    constexpr int kPer = kPrepChunk / kThreads;
+    const int lane = threadIdx.x & 31;
+    // order-preserving integer image of a time
+    auto okey = [](double v) {
+        const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+        return (long long)(u ^ ((u >> 63) ? 0x7FFFFFFFFFFFFFFFull : 0ull));
+    };
 #pragma unroll 4
-    for (int r = 0; r < kPrepChunk / kThreads; ++r) {
+    for (int r = 0; r < kPer; ++r) {
         const int64_t i = start + threadIdx.x + (int64_t)r * kThreads;
-        if (i < end) {
-            const double xi = x[i], ti = t[i];
+        const bool in = i < end;
+        const double xi = in ? x[i] : xref, ti = in ? t[i] : 0.0;
+        // the point before i is lane - 1's point of the same round (lane 0: a load)
+        const double tprev_l = __shfl_up_sync(0xffffffffu, ti, 1);
+        if (in) {
             const unsigned long long ux = (unsigned long long)__double_as_longlong(xi);
             const unsigned long long ut = (unsigned long long)__double_as_longlong(ti);
             if (((ux >> 52) & 0x7FF) == 0x7FF || ((ut >> 52) & 0x7FF) == 0x7FF) flags |= STAT_NONFINITE;
             if (i > a0) {
-                // order-preserving integer images of the two times
-                const long long kt = (long long)(ut ^ ((ut >> 63) ? 0x7FFFFFFFFFFFFFFFull : 0ull));
-                const unsigned long long up = (unsigned long long)__double_as_longlong(t[i - 1]);
-                const long long kp = (long long)(up ^ ((up >> 63) ? 0x7FFFFFFFFFFFFFFFull : 0ull));
-                if (kp > kt) flags |= STAT_UNSORTED;
+                const double tprev = lane ? tprev_l : t[i - 1];
+                if (okey(tprev) > okey(ti)) flags |= STAT_UNSORTED;
             }
-            const double d = xi - xref;
-            s1 += d;
-            s2 = fma(d, d, s2);
+            // one FP64 subtraction (as rounded as before), then double-float sums
+            float dh, dl;
+            split_df(xi - xref, dh, dl);
+            const DF d{dh, dl};
+            f1 = df_add(f1, d);
+            f2 = df_add(f2, df_sqr(d));
         }
     }
+    double s1 = (double)f1.h + (double)f1.l, s2 = (double)f2.h + (double)f2.l;
     __shared__ double sh1[kThreads / 32], sh2[kThreads / 32];
     __shared__ int shf[kThreads / 32];
     s1 = warp_sum(s1);
@@ -154,6 +191,7 @@ __global__ void stats_finish_kernel(const double *__restrict__ t, const double *
 }
 
 constexpr int kItems = 16;  // elements per thread in the keys/prefix kernels
+static_assert(kThreads * kItems == kPrepChunk, "one chunk per CTA of the prefix pass");
 
 __global__ void __launch_bounds__(kThreads)
 keys_chunks_kernel(const double *__restrict__ t, const double *__restrict__ x,
@@ -230,13 +268,21 @@ prefix_apply_kernel(const int64_t *__restrict__ offs, const int64_t *__restrict_
     const int64_t a0 = offs[b], a1 = offs[b + 1];
     const int64_t start = a0 + (g - chunk_base[b]) * (int64_t)chunk;
     const int64_t end = min(start + (int64_t)chunk, a1);
-    const int64_t my0 = start + (int64_t)threadIdx.x * kItems;
+    // the chunk goes through shared memory so that global loads and stores are
+    // coalesced (lane-consecutive) while each thread scans 16 consecutive values;
+    // one pad slot per 16 keeps the per-thread reads free of bank conflicts
+    __shared__ unsigned long long sx[kPrepChunk + kPrepChunk / kItems];
+    auto pad = [](int i) { return i + i / kItems; };
+    const int n = (int)(end - start);
+    for (int i = threadIdx.x; i < kPrepChunk; i += kThreads)
+        sx[pad(i)] = i < n ? (unsigned long long)Xq[start + i] : 0ull;
+    __syncthreads();
+    const int my0 = threadIdx.x * kItems;
     unsigned long long loc[kItems];
     unsigned long long s = 0;
 #pragma unroll
     for (int q = 0; q < kItems; ++q) {
-        const int64_t i = my0 + q;
-        loc[q] = (i < end) ? (unsigned long long)Xq[i] : 0ull;
+        loc[q] = sx[pad(my0 + q)];
         s += loc[q];
     }
     // block exclusive scan of the per-thread sums
@@ -253,11 +299,12 @@ prefix_apply_kernel(const int64_t *__restrict__ offs, const int64_t *__restrict_
     for (int q = 0; q < w; ++q) wpre += wsum[q];
     unsigned long long run = chunk_pref[g] + wpre + inc - s;
 #pragma unroll
-    for (int q = 0; q < kItems; ++q) {
-        const int64_t i = my0 + q;
-        if (i < end) P[i] = (int64_t)run;
+    for (int q = 0; q < kItems; ++q) {  // each thread rewrites the slots it alone read
+        sx[pad(my0 + q)] = run;
         run += loc[q];
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kThreads) P[start + i] = (int64_t)sx[pad(i)];
     if (g == (int64_t)gridDim.x - 1 && threadIdx.x == 0) P[n_total] = (int64_t)*total;
 }
 

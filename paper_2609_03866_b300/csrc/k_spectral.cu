@@ -246,23 +246,6 @@ __device__ __forceinline__ void split_ceil(double g, int &l0, float &f0) {
     f0 = __uint_as_float(0x3F800000u | (unsigned)((0ull - fr) >> 41)) - 1.0f;
 }
 
-// v as an unevaluated sum hi + lo of two floats (about 48 significant bits),
-// from the bit pattern when the exponent allows, else by conversion.
-__device__ __forceinline__ void split_df(double v, float &hi, float &lo) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-    const int e = (int)((u >> 52) & 0x7FF);
-    if (e >= 949 && e <= 1150) {
-        const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
-        const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
-        hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29));
-        const float scale = __uint_as_float((unsigned)(e - 948) << 23);  // 2^(e - 1075)
-        const float r = (float)(unsigned)(m & 0x1FFFFFFFull) * scale;
-        lo = sign ? -r : r;
-    } else {
-        hi = (float)v;
-        lo = (float)(v - (double)hi);
-    }
-}
 
 template <typename R> struct PointPhase;
 template <> struct PointPhase<float> {
