@@ -56,7 +56,8 @@ struct ncf_ctx {
     uint64_t launches = 0;
     size_t dev_hwm = 0;          // largest device footprint of the workspaces so far
     cudaEvent_t staged = nullptr;  // recorded after staging copies issued past the read-back sync
-    cudaStream_t copy_st = nullptr;  // host-buffer calls: uploads and read-backs beside the compute stream
+    cudaStream_t copy_st = nullptr;  // host-buffer calls: uploads beside the compute stream
+    cudaStream_t back_st = nullptr;  // and read-backs, on a stream of their own
     std::vector<cudaEvent_t> copy_ev;
     NcfProfiler prof;
     ncf_plan_info plan{0.0, 0, 0, 0, 0, 0, 0};
@@ -151,7 +152,8 @@ ncf_status grow_pinned(ncf_ctx *ctx, size_t need, cudaStream_t st) {
         ctx->pinned = nullptr;
         ctx->pinned_cap = 0;
     }
-    if (cudaHostAlloc(&ctx->pinned, ncap, cudaHostAllocDefault) != cudaSuccess) {
+    // device-mapped: small staging copies are done by a kernel (copy_pinned)
+    if (cudaHostAlloc(&ctx->pinned, ncap, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
         cudaGetLastError();
         ctx->pinned = nullptr;
         return fail(ctx, NCF_ENOMEM, "cudaHostAlloc of %zu bytes failed", ncap);
@@ -394,7 +396,7 @@ ncf_status analyze(ncf_ctx *ctx, Eval &ev, const double *lags, cudaStream_t st) 
     char *hp = ctx->pinned;
     auto upload = [&](void *dst, const void *src, size_t bytes) -> ncf_status {
         std::memcpy(hp, src, bytes);
-        NCF_CUDA(cudaMemcpyAsync(dst, hp, bytes, cudaMemcpyHostToDevice, st));
+        copy_pinned(dst, hp, bytes, st);
         hp += al(bytes);
         return NCF_OK;
     };
@@ -408,12 +410,10 @@ ncf_status analyze(ncf_ctx *ctx, Eval &ev, const double *lags, cudaStream_t st) 
     if (!ev.acf) launch_chunk_series(ev.Y.d_chunk_base, B, ev.Y.d_cs, st);
     run_stats(ev, st);
     char *down = ctx->pinned + up_bytes;
-    NCF_CUDA(cudaMemcpyAsync(down, ev.X.d_stats, B * sizeof(SeriesStats), cudaMemcpyDeviceToHost, st));
-    if (!ev.acf)
-        NCF_CUDA(cudaMemcpyAsync(down + al(B * sizeof(SeriesStats)), ev.Y.d_stats, B * sizeof(SeriesStats),
-                                 cudaMemcpyDeviceToHost, st));
+    copy_pinned(down, ev.X.d_stats, B * sizeof(SeriesStats), st);
+    if (!ev.acf) copy_pinned(down + al(B * sizeof(SeriesStats)), ev.Y.d_stats, B * sizeof(SeriesStats), st);
     double *h_lags = reinterpret_cast<double *>(down + 2 * al(B * sizeof(SeriesStats)));
-    NCF_CUDA(cudaMemcpyAsync(h_lags, lags, K * 8, cudaMemcpyDeviceToHost, st));
+    copy_pinned(h_lags, lags, K * 8, st);
     NCF_CUDA(cudaStreamSynchronize(st));
     NCF_CUDA(cudaGetLastError());
     auto *hs = reinterpret_cast<SeriesStats *>(down);
@@ -601,7 +601,7 @@ ncf_status prepare(ncf_ctx *ctx, Eval &ev, char *mem, size_t cap, char *pinned, 
         ev.scale = a2.take<double>(B);
         size_t off = 0;
         std::memcpy(pinned + off, t1.data(), t1.size() * sizeof(ScanTile));
-        NCF_CUDA(cudaMemcpyAsync(ev.g_tiles, pinned + off, t1.size() * sizeof(ScanTile), cudaMemcpyHostToDevice, st));
+        copy_pinned(ev.g_tiles, pinned + off, t1.size() * sizeof(ScanTile), st);
         off += al(t1.size() * sizeof(ScanTile));
         if (ev.lag0 && !ev.acf) {
             std::vector<ScanTile> t2 = make_tiles(ev.X.offs, B, tj);
@@ -609,8 +609,7 @@ ncf_status prepare(ncf_ctx *ctx, Eval &ev, char *mem, size_t cap, char *pinned, 
             ev.g_xtiles = a2.take<ScanTile>(ev.g_nxtiles);
             if (!ev.g_xtiles) return fail(ctx, NCF_ENOMEM, "internal: workspace estimate too small");
             std::memcpy(pinned + off, t2.data(), t2.size() * sizeof(ScanTile));
-            NCF_CUDA(cudaMemcpyAsync(ev.g_xtiles, pinned + off, t2.size() * sizeof(ScanTile), cudaMemcpyHostToDevice,
-                                     st));
+            copy_pinned(ev.g_xtiles, pinned + off, t2.size() * sizeof(ScanTile), st);
         } else {
             ev.g_xtiles = ev.g_tiles;
             ev.g_nxtiles = ev.g_ntiles;
@@ -1124,7 +1123,7 @@ static ncf_status corr_paper_impl(ncf_ctx *ctx, const double *t, const double *x
     size_t off = 0;
     auto up = [&](void *dst, const void *src, size_t bytes) -> ncf_status {
         std::memcpy(ctx->pinned + off, src, bytes);
-        NCF_CUDA(cudaMemcpyAsync(dst, ctx->pinned + off, bytes, cudaMemcpyHostToDevice, st));
+        copy_pinned(dst, ctx->pinned + off, bytes, st);
         off += al(bytes);
         return NCF_OK;
     };
@@ -1261,6 +1260,7 @@ void ncf_destroy(ncf_ctx *ctx) {
     if (ctx->staged) cudaEventDestroy(ctx->staged);
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
     if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
+    if (ctx->back_st) cudaStreamDestroy(ctx->back_st);
     for (cudaEvent_t e : ctx->copy_ev) cudaEventDestroy(e);
     if (ctx->boot) cudaFree(ctx->boot);
     if (ctx->paper) cudaFree(ctx->paper);
@@ -1559,13 +1559,16 @@ static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *
     }
     auto bo = [&](int o) { return b_out ? b_out[o] : nullptr; };
     auto no = [&](int o) { return count_out ? count_out[o] : nullptr; };
-    // Large batches run as up to four chunks of series: the upload of chunk i+1
-    // (copy stream) overlaps the evaluation of chunk i (the caller's stream), and
-    // each chunk's results come back while the next one runs.  Chunk sizes double
-    // (1/15, 2/15, 4/15, 8/15 of the points): only the first, small upload waits
-    // with nothing to overlap, and as copies outrun the scan-bound evaluations,
-    // each later upload still ends before the chunk ahead of it.  Pinned host
-    // buffers are needed for the copies to overlap.
+    // Large batches run as up to four chunks of series: every chunk's upload is
+    // queued at once on the copy stream, so the link streams the whole batch
+    // without a pause, and chunk i's evaluation (the caller's stream) starts when
+    // its own upload has landed; each chunk's results come back on a third stream
+    // while the next chunk runs.  Chunk sizes double (1/15, 2/15, 4/15, 8/15 of
+    // the points): only the first, small upload waits with nothing to overlap.
+    // The evaluations' own small transfers (statistics read-back, table uploads)
+    // go through copy_pinned, a kernel, so they never wait behind the bulk
+    // uploads on the copy engines.  Pinned host buffers are needed for the copies
+    // to overlap.
     const int64_t pts = nx + ny;
     const int C = (int)std::min<int64_t>(B, pts * 16 > (int64_t)(256 << 20) ? 4 : 1);
     std::vector<int64_t> cut(C + 1, B);
@@ -1578,16 +1581,19 @@ static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *
     }
     if (!ctx->copy_st && cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking) != cudaSuccess)
         return fail(ctx, NCF_ECUDA, "%s: copy stream creation failed", who);
+    if (!ctx->back_st && cudaStreamCreateWithFlags(&ctx->back_st, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(ctx, NCF_ECUDA, "%s: copy stream creation failed", who);
     while ((int)ctx->copy_ev.size() < 2 * C + 1) {
         cudaEvent_t e;
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
             return fail(ctx, NCF_ECUDA, "%s: event creation failed", who);
         ctx->copy_ev.push_back(e);
     }
-    cudaStream_t cs = ctx->copy_st;
+    cudaStream_t cs = ctx->copy_st, rs = ctx->back_st;
     cudaEvent_t *ev_in = ctx->copy_ev.data(), *ev_out = ev_in + C, ev_start = ev_in[2 * C];
-    // the copy stream starts after the work already queued on the caller's stream
-    bool ok = cudaEventRecord(ev_start, st) == cudaSuccess && cudaStreamWaitEvent(cs, ev_start, 0) == cudaSuccess;
+    // the copy streams start after the work already queued on the caller's stream
+    bool ok = cudaEventRecord(ev_start, st) == cudaSuccess && cudaStreamWaitEvent(cs, ev_start, 0) == cudaSuccess &&
+              cudaStreamWaitEvent(rs, ev_start, 0) == cudaSuccess;
     auto upload = [&](int c) {
         const int64_t b0 = cut[c], b1 = cut[c + 1];
         const int64_t x0 = offs_x[b0], x1 = offs_x[b1];
@@ -1601,7 +1607,7 @@ static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *
         return k && cudaEventRecord(ev_in[c], cs) == cudaSuccess;
     };
     ok = ok && cudaMemcpyAsync(dl, lags, K * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
-    for (int c = 0; c < std::min(C, 2); ++c) ok = ok && upload(c);
+    for (int c = 0; c < C; ++c) ok = ok && upload(c);
     if (!ok) return fail(ctx, NCF_ECUDA, "host-to-device copy failed: %s", cudaGetErrorString(cudaGetLastError()));
     std::vector<int64_t> ox, oy;
     for (int c = 0; c < C; ++c) {
@@ -1629,21 +1635,22 @@ static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *
                                        cc.data(), bb.data(), nn.data(), st);
             if (rc) {
                 cudaStreamSynchronize(cs);
+                cudaStreamSynchronize(rs);
                 return rc;
             }
         }
         ok = cudaEventRecord(ev_out[c], st) == cudaSuccess;
-        if (c + 2 < C) ok = ok && upload(c + 2);
-        ok = ok && cudaStreamWaitEvent(cs, ev_out[c], 0) == cudaSuccess;
+        ok = ok && cudaStreamWaitEvent(rs, ev_out[c], 0) == cudaSuccess;
         auto d2h = [&](void *h, const void *d) {
-            return cudaMemcpyAsync(h, d, nb * K * 8, cudaMemcpyDeviceToHost, cs) == cudaSuccess;
+            return cudaMemcpyAsync(h, d, nb * K * 8, cudaMemcpyDeviceToHost, rs) == cudaSuccess;
         };
         for (int o = 0; o < n_opts && nb > 0; ++o)
             ok = ok && d2h(c_out[o] + b0 * K, dc[o] + b0 * K) && (!bo(o) || d2h(bo(o) + b0 * K, db[o] + b0 * K)) &&
                  (!no(o) || d2h(no(o) + b0 * K, dn[o] + b0 * K));
         if (!ok) break;
     }
-    if (!ok || cudaStreamSynchronize(cs) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+    if (!ok || cudaStreamSynchronize(cs) != cudaSuccess || cudaStreamSynchronize(rs) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
         ctx->err = std::string("copy failed: ") + cudaGetErrorString(cudaGetLastError());
         return NCF_ECUDA;
     }

@@ -160,6 +160,13 @@ void launch_lag0_scale_rect(const unsigned long long *cnt_x, const unsigned long
                             int64_t B, double inv_v2, double *scale, cudaStream_t st);
 void launch_lag0_scale_gauss(const double *num_x, const double *den_x, const double *num_y,
                              const double *den_y, int64_t B, double *scale, cudaStream_t st);
+// Small staging copies between device memory and a context's pinned host
+// buffer (allocated device-mapped), done by a kernel instead of a copy engine:
+// a kernel's loads and stores do not queue behind bulk copies that other
+// streams have put on the copy engines (a concurrent upload of a whole batch
+// would otherwise hold up every statistics read-back and table upload).  dst
+// and src 8-byte aligned; stream-ordered like cudaMemcpyAsync.
+void copy_pinned(void *dst, const void *src, size_t bytes, cudaStream_t st);
 // c = N / max(B, 1e-16) from the scan accumulators; optional lag-0 scaling.
 // status (nullable): a nonzero status word turns every result into NaN
 // (count -1): a device-side check of an executed plan failed.

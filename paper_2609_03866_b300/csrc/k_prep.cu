@@ -17,6 +17,8 @@
 //   X_i = round(x_std,i * 2^p) and P = exclusive prefix sums of X in int64
 //   with wrap-around: a window sum P[hi] - P[lo] is exact whenever its true
 //   value fits in 63 bits, whatever the prefix values themselves do.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace ncf {
@@ -324,7 +326,26 @@ __global__ void keys_guard_kernel(const SeriesStats *__restrict__ sx, const Seri
     if (!(m <= t_abs)) atomicOr(status, STATUS_RANGE);
 }
 
+// dst[0 .. bytes) = src[0 .. bytes) in 8-byte words, then the tail bytes
+__global__ void copy_pinned_kernel(unsigned char *__restrict__ dst, const unsigned char *__restrict__ src,
+                                   size_t bytes) {
+    const size_t nw = bytes / 8;
+    const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = i0; i < nw; i += stride)
+        reinterpret_cast<unsigned long long *>(dst)[i] = reinterpret_cast<const unsigned long long *>(src)[i];
+    for (size_t i = nw * 8 + i0; i < bytes; i += stride) dst[i] = src[i];
+}
+
 }  // namespace
+
+void copy_pinned(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) return;
+    const size_t words = (bytes + 7) / 8;
+    const unsigned blocks = (unsigned)std::min<size_t>((words + 255) / 256, 592);
+    NCF_LAUNCH("copy_pinned_kernel", st,
+               copy_pinned_kernel<<<blocks, 256, 0, st>>>(static_cast<unsigned char *>(dst),
+                                                          static_cast<const unsigned char *>(src), bytes));
+}
 
 void launch_stats_guard(const SeriesStats *sx, const SeriesStats *sy, int64_t B, int *status,
                         cudaStream_t st) {

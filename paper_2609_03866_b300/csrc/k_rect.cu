@@ -985,7 +985,7 @@ ncf_status rect_prepare(const RectArgs &a, char *ws, size_t ws_cap, char *pinned
     auto take = [&](size_t bytes) { char *p = ws + used; used += al(bytes); return p; };
     auto up = [&](void *dst, const void *src, size_t bytes) {
         std::memcpy(pinned + off, src, bytes);
-        cudaMemcpyAsync(dst, pinned + off, bytes, cudaMemcpyHostToDevice, st);
+        copy_pinned(dst, pinned + off, bytes, st);
         off += al(bytes);
     };
     RectPrepared r;

@@ -848,7 +848,7 @@ void prepare_typed(const SpectralPrepared &p, char *ws, const double *h_tc,
     size_t off = 0;
     auto up = [&](void *dst, const void *src, size_t bytes) {
         std::memcpy(pinned + off, src, bytes);
-        cudaMemcpyAsync(dst, pinned + off, bytes, cudaMemcpyHostToDevice, st);
+        copy_pinned(dst, pinned + off, bytes, st);
         off += al(bytes);
     };
     up(bf.d_tc, h_tc, B * 8);
@@ -1226,7 +1226,7 @@ void paper_modes_run(const PaperModes &pm, const SpecSide &x, const SpecSide *y,
     size_t off = 0;
     auto up = [&](void *dst, const void *src, size_t bytes) {
         std::memcpy(pinned + off, src, bytes);
-        cudaMemcpyAsync(dst, pinned + off, bytes, cudaMemcpyHostToDevice, st);
+        copy_pinned(dst, pinned + off, bytes, st);
         off += al(bytes);
     };
     up(bf.d_tc, &pm.tc, 8);
@@ -1560,8 +1560,7 @@ void spectral_prepare(const SpectralPrepared &p, char *ws, char *pinned, cudaStr
         for (const auto &bk : p.buckets) {
             spectral_prepare(bk->p, ws + bk->ws_off, pinned + bk->pin_off, st);
             std::memcpy(pinned + bk->tab_pin_off, bk->tab_img.data(), bk->tab_img.size());
-            cudaMemcpyAsync(ws + bk->tab_off, pinned + bk->tab_pin_off, bk->tab_img.size(), cudaMemcpyHostToDevice,
-                            st);
+            copy_pinned(ws + bk->tab_off, pinned + bk->tab_pin_off, bk->tab_img.size(), st);
         }
         return;
     }
