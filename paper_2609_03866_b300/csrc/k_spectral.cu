@@ -778,11 +778,11 @@ void make_plan(const SpectralArgs &a, double max_span, SpectralPrepared &p) {
     p.Kp = (p.K1 + 3) / 4 * 4;
     p.M2 = a.acf ? p.Mp : 2 * p.Mp;
     p.fp32 = a.fp32;
-    // One FP64 series: the mode sums at the lags directly (exact 64-bit phases, 6
-    // FP64 operations per mode and lag) instead of a [modes x lags] table whose
-    // entries each cost an FP64 sincospi and are read once.  A batch shares the
-    // table across its series and keeps it.
-    p.direct = !a.fp32 && a.B == 1;
+    // One series: the mode sums at the lags directly (runs of modes from exactly
+    // reduced 64-bit phases, stepped by rotations) instead of a [modes x lags]
+    // table whose entries would each be computed, packed and read once.  A batch
+    // shares the table across its series and keeps it.
+    p.direct = a.B == 1;
     p.kernel = a.kernel;
     p.acf = a.acf;
     p.lag0 = a.lag0;
@@ -822,7 +822,7 @@ Bufs<R> carve(const SpectralPrepared &p, char *ws) {
     b.Anum = take<R>(ws, used, B * p.M2);
     b.Aden = take<R>(ws, used, B * p.M2);
     b.E = take<R>(ws, used, p.direct ? 0 : p.M2 * p.Kp);
-    b.Apk = take<double2>(ws, used, p.direct ? 2 * p.Mp : 0);
+    b.Apk = take<double2>(ws, used, (p.direct && !std::is_same<R, float>::value) ? 2 * p.Mp : 0);
     const bool tc = std::is_same<R, float>::value && !p.direct;
     b.At = take<unsigned char>(ws, used, tc ? tc_a_tiles_bytes(B, p.M2) : 0);
     b.Et = take<unsigned char>(ws, used, tc ? tc_e_tiles_bytes(p.M2, p.Kp) : 0);
@@ -871,6 +871,70 @@ void prepare_typed(const SpectralPrepared &p, char *ws, const double *h_tc,
     }
 }
 
+// Direct mode sums of one FP32 series at the lags: for channel z (numerator,
+// denominator) and lag k, acc_z[k] += sum_m (A_z[m] cos(2 pi m tau_k / L) +
+// A_z[Mp + m] sin(2 pi m tau_k / L)) (the sin block for a CCF only).  A warp
+// takes kDirRuns runs of kDirRun modes, one lag per lane (with few lags, S lanes
+// share a lag and take every S-th mode); each run starts from its exactly
+// reduced 64-bit phase m phi[k] (split-phase FP32 sincos, as the lag table)
+// and steps by the rotation S phi[k], so FP32 rounding drifts over at most
+// kDirRun / S steps.  Runs are summed in FP32, the warp's runs and lanes in FP64.
+constexpr int kDirWarps = 8, kDirRun = 32, kDirRuns = 8;
+__global__ void __launch_bounds__(kDirWarps * 32)
+direct_modes_f32_kernel(const float *__restrict__ An, const float *__restrict__ Ad, int64_t Mp, bool ccf,
+                        const unsigned long long *__restrict__ phi, int64_t K, double *__restrict__ acc_n,
+                        double *__restrict__ acc_d) {
+    __shared__ double part_n[kDirWarps][32], part_d[kDirWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int S = (K <= 16) ? (int)(32 / K) : 1;
+    const int64_t k = (int64_t)blockIdx.y * 32 + lane / S;
+    const int sub = lane % S;
+    const int64_t m0 = ((int64_t)blockIdx.x * kDirWarps + warp) * (kDirRun * kDirRuns);
+    double sn = 0.0, sd = 0.0;
+    if (k < K && lane / S < 32 / S) {
+        const unsigned long long ph = phi[k];
+        float rc, rs;
+        lag_sincos<float>((unsigned long long)S * ph, rc, rs);
+        for (int r = 0; r < kDirRuns; ++r) {
+            const int64_t ma = m0 + (int64_t)r * kDirRun, mb = min(ma + kDirRun, Mp);
+            if (ma + sub >= mb) break;
+            float zc, zs;
+            lag_sincos<float>((unsigned long long)(ma + sub) * ph, zc, zs);
+            float fn = 0.0f, fd = 0.0f;
+            for (int64_t m = ma + sub; m < mb; m += S) {
+                if (ccf) {
+                    fn = fmaf(An[m], zc, fmaf(An[Mp + m], zs, fn));
+                    fd = fmaf(Ad[m], zc, fmaf(Ad[Mp + m], zs, fd));
+                } else {
+                    fn = fmaf(An[m], zc, fn);
+                    fd = fmaf(Ad[m], zc, fd);
+                }
+                const float c2 = fmaf(zc, rc, -zs * rs);
+                zs = fmaf(zs, rc, zc * rs);
+                zc = c2;
+            }
+            sn += (double)fn;
+            sd += (double)fd;
+        }
+    }
+    part_n[warp][lane] = sn;
+    part_d[warp][lane] = sd;
+    __syncthreads();
+    if (warp == 0 && lane < 32 / S) {
+        const int64_t kk = (int64_t)blockIdx.y * 32 + lane;
+        if (kk < K) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < kDirWarps; ++w)
+                for (int j = 0; j < S; ++j) {
+                    a += part_n[w][lane * S + j];
+                    b += part_d[w][lane * S + j];
+                }
+            atomicAdd(acc_n + kk, a);
+            atomicAdd(acc_d + kk, b);
+        }
+    }
+}
+
 // The FP64 spectra rows of one series as complex values (cos row, sin row; an
 // ACF's sin row is zero) for the direct mode sums.
 __global__ void pack_rows_kernel(const double *__restrict__ num, const double *__restrict__ den, int64_t Mp,
@@ -889,11 +953,18 @@ ncf_status contract_and_finish(const SpectralArgs &a, const SpectralPrepared &p,
     const bool ccf = !p.acf;
     cudaMemsetAsync(bf.acc_num, 0, B * p.Kp * 8, st);
     cudaMemsetAsync(bf.acc_den, 0, B * p.Kp * 8, st);
-    if (std::is_same<R, float>::value && p.contract_variant == 0) {
+    if (std::is_same<R, float>::value && !p.direct && p.contract_variant == 0) {
         // FP32 form: tensor cores (TF32 split products, FP64 chunk sums)
         launch_tc_pack_a(reinterpret_cast<const float *>(bf.Anum), reinterpret_cast<const float *>(bf.Aden), B,
                          p.M2, bf.At, st);
         launch_contract_tc(bf.At, bf.Et, B, p.M2, p.Kp, a.sm_count, bf.acc_num, bf.acc_den, status, st);
+    } else if (p.direct && std::is_same<R, float>::value) {
+        const int64_t per = (int64_t)kDirWarps * kDirRun * kDirRuns;
+        dim3 grid((unsigned)((p.Mp + per - 1) / per), (unsigned)((p.K1 + 31) / 32));
+        NCF_LAUNCH("direct_modes_f32_kernel", st,
+                   direct_modes_f32_kernel<<<grid, kDirWarps * 32, 0, st>>>(
+                       reinterpret_cast<const float *>(bf.Anum), reinterpret_cast<const float *>(bf.Aden), p.Mp,
+                       ccf, bf.d_phi, p.K1, bf.acc_num, bf.acc_den));
     } else if (p.direct) {
         // N_k = sum_m Re(A_m exp(-2 pi i m tau_k / L)), A_m = (cos row, sin row) of
         // the spectra, at the K + 1 lags (with the appended zero lag)
@@ -911,7 +982,7 @@ ncf_status contract_and_finish(const SpectralArgs &a, const SpectralPrepared &p,
     }
     const int mode = p.lag0 ? (ccf ? 2 : 1) : 0;
     // the tensor-core contraction leaves out the m = 0 term, which the finish adds in FP64
-    const bool m0_apart = std::is_same<R, float>::value && p.contract_variant == 0;
+    const bool m0_apart = std::is_same<R, float>::value && !p.direct && p.contract_variant == 0;
     NCF_LAUNCH("finish_spectral_kernel", st,
                finish_spectral_kernel<<<(unsigned)((B * p.K + 255) / 256), 256, 0, st>>>(
                    bf.acc_num, bf.acc_den, B, p.K, p.Kp, mode, bf.lag0, status,
