@@ -1559,18 +1559,19 @@ static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *
     }
     auto bo = [&](int o) { return b_out ? b_out[o] : nullptr; };
     auto no = [&](int o) { return count_out ? count_out[o] : nullptr; };
-    // Large batches run as up to four chunks of series: every chunk's upload is
+    // Large batches run as up to five chunks of series: every chunk's upload is
     // queued at once on the copy stream, so the link streams the whole batch
     // without a pause, and chunk i's evaluation (the caller's stream) starts when
     // its own upload has landed; each chunk's results come back on a third stream
-    // while the next chunk runs.  Chunk sizes double (1/15, 2/15, 4/15, 8/15 of
-    // the points): only the first, small upload waits with nothing to overlap.
-    // The evaluations' own small transfers (statistics read-back, table uploads)
-    // go through copy_pinned, a kernel, so they never wait behind the bulk
-    // uploads on the copy engines.  Pinned host buffers are needed for the copies
-    // to overlap.
+    // while the next chunk runs.  Chunk sizes double (1/31, 2/31, ..., 16/31 of
+    // the points): only the first, small upload waits with nothing to overlap
+    // (four chunks: 0.5 ms more per bench step; six: no better).  The
+    // evaluations' own small transfers (statistics read-back, table uploads) go
+    // through copy_pinned, a kernel, so they never wait behind the bulk uploads
+    // on the copy engines.  Pinned host buffers are needed for the copies to
+    // overlap.
     const int64_t pts = nx + ny;
-    const int C = (int)std::min<int64_t>(B, pts * 16 > (int64_t)(256 << 20) ? 4 : 1);
+    const int C = (int)std::min<int64_t>(B, pts * 16 > (int64_t)(256 << 20) ? 5 : 1);
     std::vector<int64_t> cut(C + 1, B);
     cut[0] = 0;
     for (int c = 1; c < C; ++c) {
