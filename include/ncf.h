@@ -565,8 +565,8 @@ NCF_API void ncf_server_destroy(ncf_server *srv);
  *   NCF_EUNSUPPORTED (use ncf_corr).  Other errors as for ncf_corr
  *   (NCF_EINVAL, NCF_ENOTSORTED, NCF_ENONFINITE, NCF_EDEGENERATE, NCF_ECUDA).
  *   The first call on a device looks up the scratch array's device address
- *   (cudaGetSymbolAddress) with that device current; make it before any
- *   stream capture.  The call synchronises `stream` once (input validation).
+ *   (cudaGetSymbolAddress) with that device current.  The call synchronises
+ *   `stream` once (input validation).
  *   All calls share the one scratch array: calls that may overlap on the GPU
  *   (other streams or host threads) race and must be serialised by the caller.
  */

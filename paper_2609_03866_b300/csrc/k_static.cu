@@ -13,8 +13,7 @@
 // for the device variable: handing it to a kernel would fault, or on systems
 // where the GPU can reach host memory silently use the wrong memory.  Its
 // device address is therefore fetched with cudaGetSymbolAddress, once per
-// device, by the first call made while that device is current (so make that
-// first call before starting any stream capture).  Every call shares the same
+// device, by the first call made while that device is current.  Every call shares the same
 // array and the array keeps the last call's contents: the accumulators are
 // cleared at the start of each call, and calls that overlap on the GPU (two
 // streams, two threads) race on it.
