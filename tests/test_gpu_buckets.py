@@ -142,3 +142,64 @@ def test_split_plan_in_a_cuda_graph_and_within_the_memory_bound(precision):
     bound, _ = api.workspace_bytes(t.size, B, lags.size, span, float(lags.max()), kernel="gaussian", h=0.5,
                                    path="spectral", precision=precision)
     assert plan.device_bytes <= bound
+
+
+def _three_spans(seed=11):
+    """Three series of very different spans (20, 200, 1400 d): one series per grid
+    size, so each bucket holds a single series and sums its modes directly."""
+    rng = np.random.default_rng(seed)
+    ts, xs = [], []
+    for span, n in ((20.0, 3000), (200.0, 5000), (1400.0, 8000)):
+        t = np.sort(rng.uniform(0.0, span, n)) + 100.0
+        ts.append(t)
+        xs.append(np.sin(2 * np.pi * t / 3.7) + rng.normal(size=n))
+    offs = np.concatenate([[0], np.cumsum([t.size for t in ts])]).astype(np.int64)
+    return offs, np.concatenate(ts), np.concatenate(xs)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+@pytest.mark.parametrize("norm", ["none", "lag0"])
+def test_single_series_buckets_and_pearson(precision, tol, norm):
+    offs, t, x = _three_spans()
+    lags = np.linspace(0.0, 8.0, 25)
+    ctx = api.Context()
+    try:
+        split = to_np(api.corr_batch(offs, t, x, lags, kernel="gaussian", h=0.5, path="spectral",
+                                     precision=precision, norm=norm, ctx=ctx))
+        assert ctx.last_plan()["buckets"] == 3
+    finally:
+        ctx.close()
+    one = _one_grid(lambda: to_np(api.corr_batch(offs, t, x, lags, kernel="gaussian", h=0.5, path="spectral",
+                                                 precision="fp64", norm=norm)))
+    assert np.max(np.abs(split["c"] - one["c"])) < tol
+    for b in range(3):
+        tb, xb = t[offs[b]:offs[b + 1]], x[offs[b]:offs[b + 1]]
+        ref = oracle.corr(tb, xb, lags, "gaussian", 0.5, norm=norm, method="windowed", trunc_R=8.0)
+        assert np.max(np.abs(split["c"][b] - ref["c"])) < tol, b
+
+
+def test_ccf_buckets_with_pearson():
+    offs, t, x, _ = _mixed_spans(B=24, seed=12, n_lo=600, n_hi=2000)
+    rng = np.random.default_rng(13)
+    ss, ys = [], []
+    for b in range(24):
+        tb, xb = t[offs[b]:offs[b + 1]], x[offs[b]:offs[b + 1]]
+        sb = np.sort(rng.uniform(tb[0], tb[-1], tb.size))
+        ss.append(sb)
+        ys.append(np.interp(sb - 0.7, tb, xb) + 0.5 * rng.normal(size=sb.size))
+    oy = np.concatenate([[0], np.cumsum([s.size for s in ss])]).astype(np.int64)
+    s, y = np.concatenate(ss), np.concatenate(ys)
+    lags = np.linspace(-6.0, 6.0, 25)
+    kw = dict(kernel="gaussian", h=0.5, offs_y=oy, s=s, y=y, path="spectral", norm="lag0")
+    ctx = api.Context()
+    try:
+        split = to_np(api.corr_batch(offs, t, x, lags, ctx=ctx, **kw))
+        assert ctx.last_plan()["buckets"] > 1
+    finally:
+        ctx.close()
+    one = _one_grid(lambda: to_np(api.corr_batch(offs, t, x, lags, **kw)))
+    assert np.max(np.abs(split["c"] - one["c"])) < 1e-10
+    b = 5
+    ref = oracle.corr(t[offs[b]:offs[b + 1]], x[offs[b]:offs[b + 1]], lags, "gaussian", 0.5,
+                      s=s[oy[b]:oy[b + 1]], y=y[oy[b]:oy[b + 1]], norm="lag0", method="windowed", trunc_R=8.0)
+    assert np.max(np.abs(split["c"][b] - ref["c"])) < 1e-10
