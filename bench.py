@@ -990,7 +990,9 @@ def main():
                              "fft": {0: "shared-memory FFT fused with the spectrum", 1: "global Stockham passes"}
                              .get(tuned["fft_variant"]),
                              "contraction": {0: "tensor cores (tcgen05, split TF32)", 1: "FP32 pipe"}
-                             .get(tuned["contract_variant"])},
+                             .get(tuned["contract_variant"]),
+                             "spreading": {0: "CTAs of 4096 points", 1: "CTAs of 2048 points"}
+                             .get(tuned["spread_variant"])},
                    "l2": f"inputs larger than L2 ({(w.t.nbytes + w.x.nbytes) / 1e9:.2f} GB per step)"},
         "per_estimator": {
             "note": "each estimator alone: its own plan and graph, statistics pass included",

@@ -56,7 +56,7 @@ class ncf_plan_info(ctypes.Structure):
 
 class ncf_tuning(ctypes.Structure):
     _fields_ = [("rect_variant", ctypes.c_int32), ("fft_variant", ctypes.c_int32),
-                ("contract_variant", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("contract_variant", ctypes.c_int32), ("spread_variant", ctypes.c_int32)]
 
 
 class NcfError(RuntimeError):
@@ -209,10 +209,10 @@ class Context:
 
     def last_tuning(self) -> dict:
         """The autotuner's latest choices (ncf_last_tuning): rect_variant,
-        fft_variant, contract_variant; -1 where none was made yet."""
+        fft_variant, contract_variant, spread_variant; -1 where none was made yet."""
         info = ncf_tuning()
         self.check(lib().ncf_last_tuning(self._h, ctypes.byref(info)))
-        return {f: getattr(info, f) for f, _ in ncf_tuning._fields_ if f != "reserved"}
+        return {f: getattr(info, f) for f, _ in ncf_tuning._fields_}
 
     def profile(self, on: bool = True):
         """Bracket every kernel launch of this context with CUDA events."""

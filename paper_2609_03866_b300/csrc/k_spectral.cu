@@ -226,7 +226,8 @@ template <typename V> __device__ __forceinline__ void atomic_add_v(V *p, decltyp
 
 constexpr int kSpreadThreads = 256;
 constexpr int kSpreadTile = 2048;                          // grid cells of the SMEM tile
-constexpr int kStagePad = kPrepChunk + kPrepChunk / 128;   // staged points, one pad per 128
+// staged points of a CTA of kPts points: one pad slot per kPts / 32 (a lane's run)
+template <int kPts> __host__ __device__ constexpr int stage_pad() { return kPts + 32; }
 
 // ceil(g) and ceil(g) - g for 1 <= g < 2^52 from the bit pattern of g: on this
 // GPU FP64 conversion instructions run at about half the FP64 add rate, while
@@ -282,7 +283,7 @@ template <> struct PointPhase<double> {
 //            stores for the interior, atomic adds for the W-cell edges shared
 //            with the neighbouring chunks.
 // A chunk spanning more cells than the tile (a sparse series) adds straight to HBM.
-template <typename R, int W>
+template <typename R, int W, int kPts>
 __global__ void __launch_bounds__(kSpreadThreads)
 spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
               const int64_t *__restrict__ offs, const int64_t *__restrict__ offs_end,
@@ -293,15 +294,21 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
     using V = typename CT<R>::V;
     constexpr int D = PolyDeg<W>::D;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int kSub = kPrepChunk / kPts;         // CTAs per statistics chunk
+    constexpr int kRunLen = kPts / 32;              // a lane's run of points
+    constexpr int kPer = kPts / kSpreadThreads;     // points per thread
+    static_assert(kSub * kPts == kPrepChunk && kPer * kSpreadThreads == kPts, "whole chunks");
+    auto pad = [](int p) { return p + p / kRunLen; };
     V *tile = reinterpret_cast<V *>(smem_raw);
     R *sf = reinterpret_cast<R *>(tile + kSpreadTile);
-    R *sx = sf + kStagePad;
-    int *sl = reinterpret_cast<int *>(sx + kStagePad);
-    const int64_t g = blockIdx.x;
+    R *sx = sf + stage_pad<kPts>();
+    int *sl = reinterpret_cast<int *>(sx + stage_pad<kPts>());
+    const int64_t g = blockIdx.x / kSub;
     const int64_t b = cs[g];
     const int64_t a0 = offs[b], a1 = offs_end[b];
-    const int64_t start = a0 + (g - chunk_base[b]) * (int64_t)kPrepChunk;
-    const int n = (int)(min(start + (int64_t)kPrepChunk, a1) - start);
+    const int64_t start = a0 + (g - chunk_base[b]) * (int64_t)kPrepChunk + (int64_t)(blockIdx.x % kSub) * kPts;
+    const int n = (int)(min(start + (int64_t)kPts, a1) - start);
+    if (n <= 0) return;  // the part of a series' last chunk past its end
     const double c_off = -tc[b] * a_scale - 0.5 * W + nf;
     const double mean = st[b].mean;
     R mhi, mlo;
@@ -318,13 +325,13 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
     V *grid = grids + b * (int64_t)nf;
     const int mask = nf - 1;
 #pragma unroll 4
-    for (int r = 0; r < kPrepChunk / kSpreadThreads; ++r) {
+    for (int r = 0; r < kPer; ++r) {
         const int p = threadIdx.x + r * kSpreadThreads;
         if (p < n) {
             int l0;
             R f0, xs;
             PointPhase<R>::eval(t[start + p], x[start + p], a_scale, c_off, mhi, mlo, inv, l0, f0, xs);
-            const int pi = p + (p >> 7);
+            const int pi = pad(p);
             sl[pi] = l0;
             sf[pi] = f0;
             sx[pi] = xs;
@@ -332,7 +339,7 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
     }
     __syncthreads();
     const int l_first = sl[0];
-    const int l_last = sl[(n - 1) + ((n - 1) >> 7)] + W - 1;
+    const int l_last = sl[pad(n - 1)] + W - 1;
     const int span = l_last - l_first + 1;
     const bool use_tile = span <= kSpreadTile;
     if (use_tile) {
@@ -360,10 +367,10 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
         }
     };
 #pragma unroll 1
-    for (int q = 0; q < kPrepChunk / kSpreadThreads; ++q) {
-        const int p = lane * 128 + warp * 16 + q;
+    for (int q = 0; q < kPer; ++q) {
+        const int p = lane * kRunLen + warp * kPer + q;
         if (p >= n) break;
-        const int pi = p + (p >> 7);
+        const int pi = pad(p);
         const int l0 = sl[pi];
         const R f0 = sf[pi], xs = sx[pi];
         if (!started) {
@@ -433,9 +440,9 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
     }
 }
 
-template <typename R>
+template <typename R, int kPts>
 constexpr size_t spread_smem_bytes() {
-    return kSpreadTile * sizeof(typename CT<R>::V) + (size_t)kStagePad * (2 * sizeof(R) + sizeof(int));
+    return kSpreadTile * sizeof(typename CT<R>::V) + (size_t)stage_pad<kPts>() * (2 * sizeof(R) + sizeof(int));
 }
 
 // ---------------------------------------------------------------------------
@@ -1007,10 +1014,13 @@ ncf_status launch_typed(const SpectralArgs &a, const SpectralPrepared &p, char *
     Bufs<R> bf = carve<R>(p, ws);
     // spreading
     const double a_scale = (double)p.nf / p.L;
-    constexpr size_t smem = spread_smem_bytes<R>();
+    constexpr size_t smem = spread_smem_bytes<R, kPrepChunk>();
+    constexpr size_t smem_half = spread_smem_bytes<R, kPrepChunk / 2>();
     static std::atomic<unsigned long long> attr_done{0};
     once_per_device(attr_done, [&] {
-        return set_smem_limit(spread_kernel<R, 8>, smem) & set_smem_limit(spread_kernel<R, 16>, smem);
+        return set_smem_limit(spread_kernel<R, 8, kPrepChunk>, smem) &
+               set_smem_limit(spread_kernel<R, 8, kPrepChunk / 2>, smem_half) &
+               set_smem_limit(spread_kernel<R, 16, kPrepChunk>, smem);
     });
     EsPoly<R, 8, PolyDeg<8>::D> poly8{};
     EsPoly<R, 16, PolyDeg<16>::D> poly16{};
@@ -1021,14 +1031,20 @@ ncf_status launch_typed(const SpectralArgs &a, const SpectralPrepared &p, char *
     auto spread = [&](const SpecSide &sd, V *grid) {
         cudaMemsetAsync(grid, 0, B * (size_t)p.nf * sizeof(V), st);
         const int64_t *offs_end = sd.d_offs_end ? sd.d_offs_end : sd.d_offs + 1;
-        if (p.W == 8)
+        if (p.W == 8 && p.spread_variant == 1)  // CTAs of half a statistics chunk (the tuner's choice)
             NCF_LAUNCH("spread_kernel", st,
-                       spread_kernel<R, 8><<<(unsigned)sd.n_chunks, kSpreadThreads, smem, st>>>(
+                       spread_kernel<R, 8, kPrepChunk / 2><<<(unsigned)(2 * sd.n_chunks), kSpreadThreads, smem_half,
+                                                             st>>>(sd.t, sd.v, sd.d_offs, offs_end, sd.d_chunk_base,
+                                                                   sd.d_cs, sd.d_stats, bf.d_tc, a_scale, p.nf,
+                                                                   poly8, grid));
+        else if (p.W == 8)
+            NCF_LAUNCH("spread_kernel", st,
+                       spread_kernel<R, 8, kPrepChunk><<<(unsigned)sd.n_chunks, kSpreadThreads, smem, st>>>(
                            sd.t, sd.v, sd.d_offs, offs_end, sd.d_chunk_base, sd.d_cs, sd.d_stats, bf.d_tc, a_scale,
                            p.nf, poly8, grid));
         else
             NCF_LAUNCH("spread_kernel", st,
-                       spread_kernel<R, 16><<<(unsigned)sd.n_chunks, kSpreadThreads, smem, st>>>(
+                       spread_kernel<R, 16, kPrepChunk><<<(unsigned)sd.n_chunks, kSpreadThreads, smem, st>>>(
                            sd.t, sd.v, sd.d_offs, offs_end, sd.d_chunk_base, sd.d_cs, sd.d_stats, bf.d_tc, a_scale,
                            p.nf, poly16, grid));
     };
@@ -1304,16 +1320,16 @@ void paper_modes_run(const PaperModes &pm, const SpecSide &x, const SpecSide *y,
     up(bf.d_gx, pm.gx.data(), pm.nq / 2 * 8);
     up(bf.d_gphi, pm.gphi.data(), pm.nq / 2 * 8);
     up(bf.lagw, paper_lagrange_weights().data(), (size_t)kPhiStep * kPhiTaps * 8);
-    constexpr size_t smem = spread_smem_bytes<double>();
+    constexpr size_t smem = spread_smem_bytes<double, kPrepChunk>();
     static std::atomic<unsigned long long> attr_done{0};
-    once_per_device(attr_done, [&] { return set_smem_limit(spread_kernel<double, 16>, smem); });
+    once_per_device(attr_done, [&] { return set_smem_limit(spread_kernel<double, 16, kPrepChunk>, smem); });
     EsPoly<double, 16, PolyDeg<16>::D> poly{};
     for (size_t i = 0; i < pm.poly.size(); ++i) poly.c[i] = pm.poly[i];
     const double a_scale = (double)pm.nf / pm.L;
     auto spread = [&](const SpecSide &sd, double2 *grid) {
         cudaMemsetAsync(grid, 0, (size_t)pm.nf * sizeof(double2), st);
         NCF_LAUNCH("spread_kernel", st,
-                   spread_kernel<double, 16><<<(unsigned)sd.n_chunks, kSpreadThreads, smem, st>>>(
+                   spread_kernel<double, 16, kPrepChunk><<<(unsigned)sd.n_chunks, kSpreadThreads, smem, st>>>(
                        sd.t, sd.v, sd.d_offs, sd.d_offs + 1, sd.d_chunk_base, sd.d_cs, sd.d_stats, bf.d_tc,
                        a_scale, pm.nf,
                        poly, grid));
@@ -1646,6 +1662,7 @@ ncf_status spectral_launch(const SpectralArgs &a, const SpectralPrepared &p, cha
             const SpectralArgs ab = bucket_args(a, *bk, ws, st);
             bk->p.fft_variant = p.fft_variant;  // the shapes tuned for the evaluation
             bk->p.contract_variant = p.contract_variant;
+            bk->p.spread_variant = p.spread_variant;
             ncf_status rc = bk->p.fp32 ? launch_typed<float>(ab, bk->p, ws + bk->ws_off, status, st, msg)
                                        : launch_typed<double>(ab, bk->p, ws + bk->ws_off, status, st, msg);
             if (rc) return rc;

@@ -54,6 +54,9 @@ struct SpectralPrepared {
     // shared memory fused with its spectrum (0) or as global passes (1); the
     // contraction on tensor cores (0) or on the FP32 pipe (1)
     int fft_variant = 0, contract_variant = 0;
+    // FP32 spreading by CTAs of a whole statistics chunk of points (0) or of half
+    // of one (1, half the shared memory, more CTAs per SM)
+    int spread_variant = 0;
     int kernel = 0;
     std::vector<double> tc, gx, gphi, poly;
     std::vector<unsigned long long> phi;

@@ -1,8 +1,9 @@
-"""The autotuner's FP32 spectral shapes: the FFT of an ACF grid of up to 2^14
-cells in shared memory (fused with its spectrum) or as global passes, and the
-mode-to-lag contraction on tensor cores or on the FP32 pipe.
+"""The autotuner's FP32 spectral shapes: the spreading by CTAs of 4096 or 2048
+points, the FFT of an ACF grid of up to 2^14 cells in shared memory (fused with
+its spectrum) or as global passes, and the mode-to-lag contraction on tensor
+cores or on the FP32 pipe.
 
-Each of the four shapes, pinned with NCF_SPEC_VARIANT, and the shape the tuner
+Each of the eight shapes, pinned with NCF_SPEC_VARIANT, and the shape the tuner
 picks by itself must match the FP64 spectral path (within 1e-10 of the oracle)
 at the FP32 form's 1e-5 on every series and lag, for a light-curve batch and a
 batch of cross-correlations (where only the contraction varies).
@@ -34,7 +35,7 @@ def _pinned(v, fn):
             os.environ["NCF_SPEC_VARIANT"] = old
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, None])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, None])
 def test_acf_batch_every_shape_matches_fp64(variant):
     w = synth.light_curves(B=160, n_lo=200, n_hi=40_000, K=130, seed=77)
     ref = to_np(api.corr_batch(w.offs, w.t, w.x, w.lags, kernel="gaussian", h=0.5, path="spectral",
@@ -70,11 +71,12 @@ def test_last_tuning_reports_the_shapes_used():
     w = synth.light_curves(B=40, n_lo=500, n_hi=5000, K=20, seed=78)
     ctx = api.Context()
     try:
-        for v in range(4):
+        for v in range(8):
             _pinned(v, lambda: api.corr_batch(w.offs, w.t, w.x, w.lags, kernel="gaussian", h=0.5,
                                               path="spectral", precision="fp32", ctx=ctx))
             tu = ctx.last_tuning()
-            assert tu["fft_variant"] == (v & 1) and tu["contract_variant"] == (v >> 1), (v, tu)
+            assert tu["fft_variant"] == (v & 1) and tu["contract_variant"] == ((v >> 1) & 1), (v, tu)
+            assert tu["spread_variant"] == (v >> 2), (v, tu)
         _pinned(1, lambda: api.corr_batch(w.offs, w.t, w.x, w.lags, kernel="rectangle", h=0.5, ctx=ctx))
         assert ctx.last_tuning()["rect_variant"] in (0, 1, 2, 3)
     finally:
