@@ -373,9 +373,19 @@ __device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
     asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
     return v;
 }
-// shared address of the rank-table entry of query v
-__device__ __forceinline__ uint32_t pt_bin_addr(uint32_t aT, int32_t v, int bsh) {
-    return aT + ((uint32_t)(v >> bsh) << 1);
+// Bin of a value v in [0, R] of a sub-group's query range: floor(v mult / 2^32),
+// with mult chosen so that the kPtBins bins span [0, R] exactly (a power-of-two
+// shift would leave up to half of them unused).  Monotone in v, so every key in
+// a lower bin than a query's is below the query.
+__device__ __forceinline__ uint32_t pt_bin(int32_t v, uint32_t mult) {
+    return __umulhi((uint32_t)max(v, 0), mult);
+}
+__host__ __device__ __forceinline__ uint32_t pt_bin_mult(int32_t R) {
+    return R + 1 <= kPtBins ? 0xffffffffu : (uint32_t)(((uint64_t)kPtBins << 32) / (uint64_t)(R + 1));
+}
+// shared address of the rank-table entry of query v (v >= 0)
+__device__ __forceinline__ uint32_t pt_bin_addr(uint32_t aT, int32_t v, uint32_t mult) {
+    return aT + (__umulhi((uint32_t)v, mult) << 1);
 }
 
 // Bounds of lower_bound(Tx, ia, ib, v) from the planning samples samp[m] =
@@ -493,7 +503,8 @@ struct PtLagArgs {
     const double *tx, *sy, *slags;
     int64_t j0, k, ia_s, lim, eta;
     double h;
-    int eps, bsh, pa, pb;
+    int eps, pa, pb;
+    uint32_t mult;
 };
 
 // One lag over this lane's outer points of the segment [pa, pb) (the whole
@@ -528,8 +539,8 @@ __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (
         int4 el[kPtBatch], eh[kPtBatch];
 #pragma unroll
         for (int i = 0; i < kPtBatch; ++i) {
-            ol[i] = lds_u16(pt_bin_addr(aT, s[i] + L.x, g.bsh));
-            oh[i] = lds_u16(pt_bin_addr(aT, s[i] + L.z, g.bsh));
+            ol[i] = lds_u16(pt_bin_addr(aT, s[i] + L.x, g.mult));
+            oh[i] = lds_u16(pt_bin_addr(aT, s[i] + L.z, g.mult));
         }
 #pragma unroll
         for (int i = 0; i < kPtBatch; ++i) {
@@ -776,8 +787,7 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                 // are stored relative to vmin, the bins cover [0, vmax - vmin]
                 const int32_t vmin = sca + (int32_t)((S0 + sb.dmin - eta - base) >> sh);
                 const int32_t vmax = scb + (int32_t)((S0 + sb.dmax + eta - base) >> sh) + 2;
-                const int vbits = 32 - __clz(max(vmax - vmin, 1));
-                const int bsh = max(0, vbits - kPtBinsLog);
+                const uint32_t mult = pt_bin_mult(max(vmax - vmin, 1));
                 // entries 0 .. nK: keys (nK: the sentinel) and the limbs of P[ia + i].
                 // Tx and P of entry i are copied asynchronously into its own 16-byte
                 // slot (all copies in flight at once), then each thread rewrites its
@@ -815,9 +825,9 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                                                    (int32_t)((S0 + du + eta - base) >> sh) + 2 - vmin);
                 }
                 __syncthreads();
-                // rank table: sT[b] = the first index with key >= b << bsh, as a
-                // merge of the bins (values b << bsh) with the keys, bin b before key
-                // e iff key_e >= b << bsh.  Each thread takes an equal share of the
+                // rank table: sT[b] = the first index whose key's bin is >= b, as a
+                // merge of the bins b with the keys, bin b before key e iff
+                // bin(key_e) >= b.  Each thread takes an equal share of the
                 // merged sequence (merge path), so a dense stretch of keys and a
                 // long gap cost the same; entry nK is the sentinel, after every bin.
                 {
@@ -829,12 +839,12 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                     int lo = max(0, d0 - nE), hi = min(d0, kPtBins);  // bins among the first d0
                     while (lo < hi) {
                         const int mid = (lo + hi) >> 1;
-                        if (sm.sE[d0 - 1 - mid].x >= (mid << bsh)) lo = mid + 1; else hi = mid;
+                        if (pt_bin(sm.sE[d0 - 1 - mid].x, mult) >= (uint32_t)mid) lo = mid + 1; else hi = mid;
                     }
                     int a = lo, e = d0 - lo;
                     int32_t ke = sm.sE[min(e, nE - 1)].x;
                     for (int d = d0; d < d1 && a < kPtBins; ++d) {
-                        if (ke >= (a << bsh)) {
+                        if (pt_bin(ke, mult) >= (uint32_t)a) {
                             sm.sT[a] = (uint16_t)e;
                             ++a;
                         } else {
@@ -844,7 +854,7 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                     }
                 }
                 __syncthreads();
-                PtLagArgs ga{Tx, Sy, dls, dus, tx, sy, slags, tile.j0, 0, sb.ia, lim, eta, h, eps, bsh, pa, pb};
+                PtLagArgs ga{Tx, Sy, dls, dus, tx, sy, slags, tile.j0, 0, sb.ia, lim, eta, h, eps, pa, pb, mult};
                 for (int kl = sb.ka; kl < sb.kb; ++kl) {
                     const int4 L = sm.lc[kl];
                     ga.k = k0 + kl;
