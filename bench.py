@@ -991,7 +991,10 @@ def main():
                              .get(tuned["fft_variant"]),
                              "contraction": {0: "tensor cores (tcgen05, split TF32)", 1: "FP32 pipe"}
                              .get(tuned["contract_variant"]),
-                             "spreading": {0: "CTAs of 4096 points", 1: "CTAs of 2048 points"}
+                             "spreading": {0: "CTAs of 4096 points, FP32 tile sums",
+                                           1: "CTAs of 2048 points, FP32 tile sums",
+                                           2: "CTAs of 4096 points, fixed-point tile sums",
+                                           3: "CTAs of 2048 points, fixed-point tile sums"}
                              .get(tuned["spread_variant"])},
                    "l2": f"inputs larger than L2 ({(w.t.nbytes + w.x.nbytes) / 1e9:.2f} GB per step)"},
         "per_estimator": {

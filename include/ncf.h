@@ -156,12 +156,13 @@ NCF_API ncf_status ncf_last_plan(const ncf_ctx *ctx, ncf_plan_info *out);
  * of 2^7..2^14 cells in shared memory, fused with its spectrum, 1 = global
  * Stockham passes (the only choice for larger grids and for CCFs);
  * contract_variant 0 = mode-to-lag contraction on tensor cores, 1 = on the FP32
- * pipe; spread_variant 0 = spreading by CTAs of 4096 points, 1 = of 2048 points
- * (half the shared memory, more CTAs per SM).  Each choice is the fastest of its
- * candidates when first timed for a problem bucket (device, sizes in powers of
- * two, ACF/CCF), and is kept for the process; NCF_RECT_VARIANT and
- * NCF_SPEC_VARIANT (bit 0 fft, bit 1 contraction, bit 2 spreading) in the
- * environment pin them.  The estimators' results agree between variants:
+ * pipe; spread_variant bit 0 = spreading by CTAs of 2048 points instead of 4096
+ * (half the shared memory, more CTAs per SM), bit 1 = the CTA's tile summed in
+ * fixed point by integer atomics instead of in FP32 by compare-and-swap.  Each
+ * choice is the fastest of its candidates when first timed for a problem bucket
+ * (device, sizes in powers of two, ACF/CCF), and is kept for the process;
+ * NCF_RECT_VARIANT and NCF_SPEC_VARIANT (fft + 2 contraction + 4 spreading,
+ * 0..15) in the environment pin them.  The estimators' results agree between variants:
  * bit for bit on the rectangle scan, within the FP32 form's error otherwise.
  * No counterpart in the paper (an implementation choice).
  */

@@ -809,15 +809,19 @@ ncf_status tune_rect(ncf_ctx *ctx, Eval &ev, cudaStream_t st) {
 }
 
 
-// Autotuned FP32 spectral shapes per (device, problem bucket): the spreading's
-// CTA size (a statistics chunk of points or half of one), the FFT of an ACF
+// Autotuned FP32 spectral shapes per (device, problem bucket): the spreading
+// (CTAs of a statistics chunk of points or of half of one; tile sums in FP32 by
+// compare-and-swap or in fixed point by integer atomics), the FFT of an ACF
 // grid that fits shared memory (there, fused with its spectrum, or as global
 // passes) and the mode-to-lag contraction (tensor cores or the FP32 pipe).  The
 // candidates agree within the FP32 form's error, not bit for bit; the one kept
 // is the fastest on the first batch of its bucket, and the caller's evaluation
 // then runs with it.
 std::map<std::pair<int, uint64_t>, int> g_tune_spec;
-constexpr int kSpecVariants = 8;  // bit 0: global-pass FFT; bit 1: FP32-pipe contraction; bit 2: half-chunk spreading CTAs
+// v = fft + 2 contraction + 4 spreading: fft 1 = global passes, contraction 1 = the
+// FP32 pipe, spreading bit 0 = CTAs of half a statistics chunk, bit 1 = fixed-point
+// tile sums
+constexpr int kSpecVariants = 16;
 
 uint64_t spec_tune_key(const Eval &ev) {
     auto lg = [](double v) { return (uint64_t)std::max(0.0, std::floor(std::log2(std::max(v, 1.0)))); };
@@ -828,7 +832,7 @@ uint64_t spec_tune_key(const Eval &ev) {
 void set_spec_variant(ncf_ctx *ctx, Eval &ev, int v) {
     ev.sp.fft_variant = v & 1;
     ev.sp.contract_variant = (v >> 1) & 1;
-    ev.sp.spread_variant = (v >> 2) & 1;
+    ev.sp.spread_variant = v >> 2;
     // the shared-memory FFT applies to ACF grids of 2^7..2^14 cells only
     const bool fft_choice = ev.acf && ev.sp.lg >= 7 && ev.sp.lg <= 14;
     ctx->tuning.fft_variant = fft_choice ? ev.sp.fft_variant : 1;
@@ -838,7 +842,7 @@ void set_spec_variant(ncf_ctx *ctx, Eval &ev, int v) {
 
 ncf_status tune_spectral(ncf_ctx *ctx, Eval &ev, cudaStream_t st) {
     if (rect_scan(ev) || ev.path == NCF_PATH_WINDOWED || !ev.sp.fp32 || ev.sp.direct) return NCF_OK;
-    // NCF_SPEC_VARIANT=0..7 pins the shapes (tests, measurements) and skips the timing
+    // NCF_SPEC_VARIANT=0..15 pins the shapes (tests, measurements) and skips the timing
     if (const char *pin = std::getenv("NCF_SPEC_VARIANT")) {
         const int v = std::atoi(pin);
         if (v >= 0 && v < kSpecVariants) {

@@ -116,6 +116,24 @@ std::vector<double> es_poly(int W, double beta, int D) {
     return out;
 }
 
+// Largest sum over the W taps of one point, max over u in [0, 1] of
+// sum_k P_k(2u - 1) (sampled finely, with a margin far above the sampling's
+// error for these smooth, bounded interpolants): a bound for fixed-point sums.
+double es_tap_sum(const std::vector<double> &poly, int W, int D) {
+    double best = 0.0;
+    for (int i = 0; i <= 4096; ++i) {
+        const double u = 2.0 * i / 4096.0 - 1.0;
+        double s = 0.0;
+        for (int k = 0; k < W; ++k) {
+            double v = 0.0;
+            for (int d = D; d >= 0; --d) v = v * u + poly[(size_t)k * (D + 1) + d];
+            s += std::fabs(v);
+        }
+        best = std::max(best, s);
+    }
+    return best * 1.01 + 1e-3;
+}
+
 template <typename R, int W, int D> struct EsPoly { R c[W * (D + 1)]; };
 template <int W> struct PolyDeg;
 template <> struct PolyDeg<8> { static constexpr int D = 8; };
@@ -283,14 +301,26 @@ template <> struct PointPhase<double> {
 //            stores for the interior, atomic adds for the W-cell edges shared
 //            with the neighbouring chunks.
 // A chunk spanning more cells than the tile (a sparse series) adds straight to HBM.
-template <typename R, int W, int kPts>
+//
+// kFix (FP32): the tile holds fixed-point integers and a departing window cell
+// is added with native 32-bit integer shared-memory atomics, instead of the
+// compare-and-swap loop an FP32 add to shared memory takes.  A cell value v
+// becomes round(v q); q is set per CTA so that no cell's sum can reach 2^31 (a
+// cell sums at most the chunk's |x_std| for the values and its points' tap sums
+// for the unit weights; each rounding adds at most 1/2), so the integer sums are
+// exact and each flush is off by at most 1/(2q): about 8e-7 for the values and
+// 3e-6 for the weights of a dense 4096-point chunk, the size of the FP32
+// rounding of the same tile sums.
+template <typename R, int W, int kPts, bool kFix = false>
 __global__ void __launch_bounds__(kSpreadThreads)
 spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
               const int64_t *__restrict__ offs, const int64_t *__restrict__ offs_end,
               const int64_t *__restrict__ chunk_base,
               const int32_t *__restrict__ cs,
               const SeriesStats *__restrict__ st, const double *__restrict__ tc, double a_scale,
-              int nf, const EsPoly<R, W, PolyDeg<W>::D> poly, typename CT<R>::V *__restrict__ grids) {
+              int nf, const EsPoly<R, W, PolyDeg<W>::D> poly, float tap_sum,
+              typename CT<R>::V *__restrict__ grids) {
+    static_assert(!kFix || sizeof(R) == 4, "fixed-point tiles for the FP32 form");
     using V = typename CT<R>::V;
     constexpr int D = PolyDeg<W>::D;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -324,6 +354,7 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
     const R inv = (R)st[b].inv_std;
     V *grid = grids + b * (int64_t)nf;
     const int mask = nf - 1;
+    float asum = 0.0f;
 #pragma unroll 4
     for (int r = 0; r < kPer; ++r) {
         const int p = threadIdx.x + r * kSpreadThreads;
@@ -335,9 +366,25 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
             sl[pi] = l0;
             sf[pi] = f0;
             sx[pi] = xs;
+            if constexpr (kFix) asum += fabsf(xs);
         }
     }
+    __shared__ float fix_q[2 + kSpreadThreads / 32];
+    if constexpr (kFix) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) asum += __shfl_xor_sync(0xffffffffu, asum, o);
+        if ((threadIdx.x & 31) == 0) fix_q[2 + (threadIdx.x >> 5)] = asum;
+    }
     __syncthreads();
+    if constexpr (kFix) {
+        if (threadIdx.x == 0) {
+            float s = 0.0f;
+            for (int w = 0; w < kSpreadThreads / 32; ++w) s += fix_q[2 + w];
+            const float room = 2147483648.0f - 8.0f * (float)n;  // below 2^31 after the roundings
+            fix_q[0] = room / fmaxf(1.01f * s, 1e-20f);
+            fix_q[1] = room / (1.01f * tap_sum * (float)n);
+        }
+    }
     const int l_first = sl[0];
     const int l_last = sl[pad(n - 1)] + W - 1;
     const int span = l_last - l_first + 1;
@@ -356,12 +403,23 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
     for (int k = 0; k < W; ++k) { wre[k] = 0; wim[k] = 0; }
     int wbase = 0;
     bool started = false;
+    float qr = 0.0f, qi = 0.0f;
+    if constexpr (kFix) {
+        qr = fix_q[0];
+        qi = fix_q[1];
+    }
     auto flush_cell = [&](int cell, R re, R im) {
         if (re == (R)0 && im == (R)0) return;
         // inside the tile for sorted, in-domain points; anything else goes to the grid
         if (use_tile && (unsigned)(cell - l_first) < (unsigned)span) {
-            atomicAdd(&tile[cell - l_first].x, re);
-            atomicAdd(&tile[cell - l_first].y, im);
+            if constexpr (kFix) {
+                int2 *ic = reinterpret_cast<int2 *>(tile) + (cell - l_first);
+                atomicAdd(&ic->x, __float2int_rn(re * qr));
+                atomicAdd(&ic->y, __float2int_rn(im * qi));
+            } else {
+                atomicAdd(&tile[cell - l_first].x, re);
+                atomicAdd(&tile[cell - l_first].y, im);
+            }
         } else {
             atomic_add_v(&grid[cell & mask], re, im);
         }
@@ -426,7 +484,12 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
         // first and last W cells, so the interior is this chunk's alone and goes to
         // the (zeroed) grid with plain stores; the edges are added atomically.
         for (int i = threadIdx.x; i < span; i += blockDim.x) {
-            const V v = tile[i];
+            V v = tile[i];
+            if constexpr (kFix) {
+                const int2 c = reinterpret_cast<const int2 *>(tile)[i];
+                v.x = (float)c.x / qr;
+                v.y = (float)c.y / qi;
+            }
             if (v.x == 0 && v.y == 0) continue;
             V *dst = &grid[(l_first + i) & mask];
             if (i >= W && i < span - W) {
@@ -1020,7 +1083,9 @@ ncf_status launch_typed(const SpectralArgs &a, const SpectralPrepared &p, char *
     once_per_device(attr_done, [&] {
         return set_smem_limit(spread_kernel<R, 8, kPrepChunk>, smem) &
                set_smem_limit(spread_kernel<R, 8, kPrepChunk / 2>, smem_half) &
-               set_smem_limit(spread_kernel<R, 16, kPrepChunk>, smem);
+               set_smem_limit(spread_kernel<R, 16, kPrepChunk>, smem) &
+               (sizeof(R) != 4 || (set_smem_limit(spread_kernel<float, 8, kPrepChunk, true>, smem) &
+                                   set_smem_limit(spread_kernel<float, 8, kPrepChunk / 2, true>, smem_half)));
     });
     EsPoly<R, 8, PolyDeg<8>::D> poly8{};
     EsPoly<R, 16, PolyDeg<16>::D> poly16{};
@@ -1028,25 +1093,27 @@ ncf_status launch_typed(const SpectralArgs &a, const SpectralPrepared &p, char *
         if (p.W == 8) poly8.c[i] = (R)p.poly[i];
         else poly16.c[i] = (R)p.poly[i];
     }
+    const float tap_sum = (float)p.tap_sum;
+    // FP32 spreading shapes (the tuner's choice): bit 0 = CTAs of half a statistics
+    // chunk, bit 1 = fixed-point tile sums
     auto spread = [&](const SpecSide &sd, V *grid) {
         cudaMemsetAsync(grid, 0, B * (size_t)p.nf * sizeof(V), st);
         const int64_t *offs_end = sd.d_offs_end ? sd.d_offs_end : sd.d_offs + 1;
-        if (p.W == 8 && p.spread_variant == 1)  // CTAs of half a statistics chunk (the tuner's choice)
+        auto go = [&](auto kern, unsigned grid_dim, size_t sm, const auto &poly) {
             NCF_LAUNCH("spread_kernel", st,
-                       spread_kernel<R, 8, kPrepChunk / 2><<<(unsigned)(2 * sd.n_chunks), kSpreadThreads, smem_half,
-                                                             st>>>(sd.t, sd.v, sd.d_offs, offs_end, sd.d_chunk_base,
-                                                                   sd.d_cs, sd.d_stats, bf.d_tc, a_scale, p.nf,
-                                                                   poly8, grid));
-        else if (p.W == 8)
-            NCF_LAUNCH("spread_kernel", st,
-                       spread_kernel<R, 8, kPrepChunk><<<(unsigned)sd.n_chunks, kSpreadThreads, smem, st>>>(
-                           sd.t, sd.v, sd.d_offs, offs_end, sd.d_chunk_base, sd.d_cs, sd.d_stats, bf.d_tc, a_scale,
-                           p.nf, poly8, grid));
-        else
-            NCF_LAUNCH("spread_kernel", st,
-                       spread_kernel<R, 16, kPrepChunk><<<(unsigned)sd.n_chunks, kSpreadThreads, smem, st>>>(
-                           sd.t, sd.v, sd.d_offs, offs_end, sd.d_chunk_base, sd.d_cs, sd.d_stats, bf.d_tc, a_scale,
-                           p.nf, poly16, grid));
+                       kern<<<grid_dim, kSpreadThreads, sm, st>>>(sd.t, sd.v, sd.d_offs, offs_end, sd.d_chunk_base,
+                                                                   sd.d_cs, sd.d_stats, bf.d_tc, a_scale, p.nf, poly,
+                                                                   tap_sum, grid));
+            return NCF_OK;
+        };
+        const unsigned full = (unsigned)sd.n_chunks, half = (unsigned)(2 * sd.n_chunks);
+        if (p.W != 8) return go(spread_kernel<R, 16, kPrepChunk>, full, smem, poly16);
+        if constexpr (sizeof(R) == 4) {
+            if (p.spread_variant == 2) return go(spread_kernel<float, 8, kPrepChunk, true>, full, smem, poly8);
+            if (p.spread_variant == 3) return go(spread_kernel<float, 8, kPrepChunk / 2, true>, half, smem_half, poly8);
+        }
+        if (p.spread_variant & 1) return go(spread_kernel<R, 8, kPrepChunk / 2>, half, smem_half, poly8);
+        return go(spread_kernel<R, 8, kPrepChunk>, full, smem, poly8);
     };
     spread(a.x, bf.grid_x);
     if (ccf) spread(a.y, bf.grid_y);
@@ -1332,7 +1399,7 @@ void paper_modes_run(const PaperModes &pm, const SpecSide &x, const SpecSide *y,
                    spread_kernel<double, 16, kPrepChunk><<<(unsigned)sd.n_chunks, kSpreadThreads, smem, st>>>(
                        sd.t, sd.v, sd.d_offs, sd.d_offs + 1, sd.d_chunk_base, sd.d_cs, sd.d_stats, bf.d_tc,
                        a_scale, pm.nf,
-                       poly, grid));
+                       poly, 0.0f, grid));
     };
     spread(x, bf.grid_x);
     if (ccf) {
@@ -1623,6 +1690,7 @@ ncf_status spectral_plan(const SpectralArgs &a, SpectralPrepared *sp, size_t *ws
     for (int q = 0; q < p.nq; ++q)
         p.gphi[q] = gw[q] * std::exp(p.beta * (std::sqrt(std::max(0.0, 1.0 - p.gx[q] * p.gx[q])) - 1.0));
     p.poly = es_poly(p.W, p.beta, p.W == 8 ? PolyDeg<8>::D : PolyDeg<16>::D);
+    p.tap_sum = es_tap_sum(p.poly, p.W, p.W == 8 ? PolyDeg<8>::D : PolyDeg<16>::D);
     *ws_bytes = p.fp32 ? carve<float>(p, nullptr).used : carve<double>(p, nullptr).used;
     *pinned_bytes = al(B * 8) + al(p.Kp * 8) + 2 * al(p.nq * 8);
     *sp = std::move(p);

@@ -54,9 +54,12 @@ struct SpectralPrepared {
     // shared memory fused with its spectrum (0) or as global passes (1); the
     // contraction on tensor cores (0) or on the FP32 pipe (1)
     int fft_variant = 0, contract_variant = 0;
-    // FP32 spreading by CTAs of a whole statistics chunk of points (0) or of half
-    // of one (1, half the shared memory, more CTAs per SM)
+    // FP32 spreading: bit 0, CTAs of half a statistics chunk of points (half the
+    // shared memory, more CTAs per SM); bit 1, the CTA's tile of cells summed in
+    // fixed point by native integer shared-memory atomics instead of in FP32 by
+    // compare-and-swap loops
     int spread_variant = 0;
+    double tap_sum = 0;  // an upper bound of sum_k phi_k(u) over the W taps of one point
     int kernel = 0;
     std::vector<double> tc, gx, gphi, poly;
     std::vector<unsigned long long> phi;

@@ -1,12 +1,12 @@
-"""The autotuner's FP32 spectral shapes: the spreading by CTAs of 4096 or 2048
-points, the FFT of an ACF grid of up to 2^14 cells in shared memory (fused with
-its spectrum) or as global passes, and the mode-to-lag contraction on tensor
-cores or on the FP32 pipe.
+"""The autotuner's FP32 spectral shapes: the spreading (CTAs of 4096 or 2048
+points; tile sums in FP32 or in fixed point), the FFT of an ACF grid of up to
+2^14 cells in shared memory (fused with its spectrum) or as global passes, and
+the mode-to-lag contraction on tensor cores or on the FP32 pipe.
 
-Each of the eight shapes, pinned with NCF_SPEC_VARIANT, and the shape the tuner
+Each of the sixteen shapes, pinned with NCF_SPEC_VARIANT, and the shape the tuner
 picks by itself must match the FP64 spectral path (within 1e-10 of the oracle)
 at the FP32 form's 1e-5 on every series and lag, for a light-curve batch and a
-batch of cross-correlations (where only the contraction varies).
+batch of cross-correlations (where the contraction and the spreading vary).
 """
 import os
 
@@ -35,7 +35,7 @@ def _pinned(v, fn):
             os.environ["NCF_SPEC_VARIANT"] = old
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, None])
+@pytest.mark.parametrize("variant", list(range(16)) + [None])
 def test_acf_batch_every_shape_matches_fp64(variant):
     w = synth.light_curves(B=160, n_lo=200, n_hi=40_000, K=130, seed=77)
     ref = to_np(api.corr_batch(w.offs, w.t, w.x, w.lags, kernel="gaussian", h=0.5, path="spectral",
@@ -47,8 +47,8 @@ def test_acf_batch_every_shape_matches_fp64(variant):
     assert np.max(np.abs(got["b"] / ref["b"] - 1.0)) < 1e-4
 
 
-@pytest.mark.parametrize("variant", [0, 2])
-def test_ccf_batch_both_contractions_match_fp64(variant):
+@pytest.mark.parametrize("variant", [0, 2, 8, 14])
+def test_ccf_batch_contractions_and_spreadings_match_fp64(variant):
     rng = np.random.default_rng(5)
     B = 24
     xs, ys = [], []
@@ -71,7 +71,7 @@ def test_last_tuning_reports_the_shapes_used():
     w = synth.light_curves(B=40, n_lo=500, n_hi=5000, K=20, seed=78)
     ctx = api.Context()
     try:
-        for v in range(8):
+        for v in range(16):
             _pinned(v, lambda: api.corr_batch(w.offs, w.t, w.x, w.lags, kernel="gaussian", h=0.5,
                                               path="spectral", precision="fp32", ctx=ctx))
             tu = ctx.last_tuning()
