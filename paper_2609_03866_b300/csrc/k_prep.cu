@@ -101,6 +101,11 @@ stats_chunks_kernel(const double *__restrict__ t, const double *__restrict__ x,
     const double xref = x[a0];
     DF f1{0.0f, 0.0f}, f2{0.0f, 0.0f};  // this thread's sums of d and d^2
     int flags = 0;
+    // largest exponent field of the thread's values (bits 20..30 of the high
+    // words), tested for 0x7FF once at the end: written as a per-value test of
+    // the exponent, the compiler turned it into two FP64 compares per point, on
+    // this GPU's slow FP64 pipe
+    unsigned emax = 0u;
     constexpr int kPer = kPrepChunk / kThreads;
     const int lane = threadIdx.x & 31;
     // order-preserving integer image of a time
@@ -116,9 +121,8 @@ stats_chunks_kernel(const double *__restrict__ t, const double *__restrict__ x,
         // the point before i is lane - 1's point of the same round (lane 0: a load)
         const double tprev_l = __shfl_up_sync(0xffffffffu, ti, 1);
         if (in) {
-            const unsigned long long ux = (unsigned long long)__double_as_longlong(xi);
-            const unsigned long long ut = (unsigned long long)__double_as_longlong(ti);
-            if (((ux >> 52) & 0x7FF) == 0x7FF || ((ut >> 52) & 0x7FF) == 0x7FF) flags |= STAT_NONFINITE;
+            emax = max(emax, max((unsigned)__double2hiint(xi) & 0x7FF00000u,
+                                 (unsigned)__double2hiint(ti) & 0x7FF00000u));
             if (i > a0) {
                 const double tprev = lane ? tprev_l : t[i - 1];
                 if (okey(tprev) > okey(ti)) flags |= STAT_UNSORTED;
@@ -131,6 +135,7 @@ stats_chunks_kernel(const double *__restrict__ t, const double *__restrict__ x,
             f2 = df_add(f2, df_sqr(d));
         }
     }
+    if (emax == 0x7FF00000u) flags |= STAT_NONFINITE;
     double s1 = (double)f1.h + (double)f1.l, s2 = (double)f2.h + (double)f2.l;
     __shared__ double sh1[kThreads / 32], sh2[kThreads / 32];
     __shared__ int shf[kThreads / 32];
@@ -276,7 +281,8 @@ prefix_apply_kernel(const int64_t *__restrict__ offs, const int64_t *__restrict_
     __shared__ unsigned long long sx[kPrepChunk + kPrepChunk / kItems];
     auto pad = [](int i) { return i + i / kItems; };
     const int n = (int)(end - start);
-    for (int i = threadIdx.x; i < kPrepChunk; i += kThreads)
+#pragma unroll
+    for (int i = threadIdx.x; i < kPrepChunk; i += kThreads)  // all 16 loads in flight
         sx[pad(i)] = i < n ? (unsigned long long)Xq[start + i] : 0ull;
     __syncthreads();
     const int my0 = threadIdx.x * kItems;
@@ -306,6 +312,7 @@ prefix_apply_kernel(const int64_t *__restrict__ offs, const int64_t *__restrict_
         run += loc[q];
     }
     __syncthreads();
+#pragma unroll 4
     for (int i = threadIdx.x; i < n; i += kThreads) P[start + i] = (int64_t)sx[pad(i)];
     if (g == (int64_t)gridDim.x - 1 && threadIdx.x == 0) P[n_total] = (int64_t)*total;
 }

@@ -148,6 +148,26 @@ def test_full_size_ccf_rectangle_counts_exact():
     assert abs(w.lags[int(np.argmax(got["c"]))] - 15.0) < 1.1
 
 
+@pytest.mark.parametrize("where", ["x_nan", "x_inf", "t_inf"])
+def test_non_finite_values_inside_a_batch_are_rejected(where):
+    """A NaN or an infinity anywhere in a batch (here in the middle of the second
+    series' third statistics chunk) is found by the statistics pass and reported,
+    for the batched FP32 form and for the exact rectangle scan."""
+    w = synth.light_curves(B=3, n_lo=12000, n_hi=14000, K=5, seed=9)
+    t, x = w.t.copy(), w.x.copy()
+    i = int(w.offs[1]) + 2 * 4096 + 77
+    if where == "x_nan":
+        x[i] = np.nan
+    elif where == "x_inf":
+        x[i] = -np.inf
+    else:
+        t[-1] = np.inf  # still sorted
+    for kw in (dict(kernel="gaussian", h=0.5, path="spectral", precision="fp32"), dict(kernel="rectangle", h=0.5)):
+        with pytest.raises(api.NcfError) as e:
+            api.corr_batch(w.offs, t, x, w.lags, **kw)
+        assert e.value.name == "NCF_ENONFINITE", e.value.name
+
+
 def test_invalid_inputs_are_rejected_before_any_launch():
     t = np.arange(10.0)
     x = np.arange(10.0) ** 2
