@@ -685,6 +685,7 @@ fft_spectrum_smem_kernel(const float2 *__restrict__ grids, int lg, int64_t M, in
     float2 *T1 = g + sfft_pad(nf), *T2 = T1 + kSmemFftTw;
     const int64_t b = blockIdx.x;
     const float4 *src = reinterpret_cast<const float4 *>(grids + b * (int64_t)nf);  // two cells per load
+#pragma unroll 8
     for (int i = threadIdx.x; i < nf / 2; i += kSmemFftThreads) {
         const float4 v = src[i];
         g[sfft_pad(2 * i)] = make_float2(v.x, v.y);
