@@ -495,8 +495,11 @@ NCF_API size_t ncf_plan_device_bytes(const ncf_plan *plan);
  * Gaussian, whose path is chosen from the data, it covers both paths.  The
  * request server admits requests against its budget with this bound.  *pinned_bytes (may be NULL)
  * receives the context's pinned host staging.  Not included: the caller's own
- * inputs and outputs, and the uploaded copies of the host-buffer calls (16 bytes
- * per point plus 8 per lag).  Returns NCF_EINVAL or NCF_EUNSUPPORTED for options
+ * inputs and outputs, and what the host-buffer calls add: the uploaded copies
+ * (16 bytes per point plus 8 per lag), and a second pre-statistics workspace and
+ * pinned staging for the next chunk's statistics stage, which runs beside the
+ * current chunk's evaluation (about 64 bytes per series plus 28 per 4096
+ * points).  Returns NCF_EINVAL or NCF_EUNSUPPORTED for options
  * or sizes that the calls would refuse (a spectral grid beyond 2^28 cells).
  */
 NCF_API ncf_status ncf_workspace_bytes(ncf_ctx *ctx, int64_t n_x, int64_t n_y, int64_t B, int64_t K,

@@ -47,6 +47,14 @@ struct ncf_ctx {
     size_t ws2_cap = 0;
     char *pinned = nullptr;      // host staging for uploads and read-backs
     size_t pinned_cap = 0;
+    // host-buffer calls: the next chunk's statistics stage runs on a stream of its
+    // own beside the current chunk's evaluation, with a second pre-statistics
+    // workspace (chunks alternate between ws and ws_alt) and its own staging
+    char *ws_alt = nullptr;
+    size_t ws_alt_cap = 0;
+    char *pinned_pre = nullptr;
+    size_t pinned_pre_cap = 0;
+    cudaStream_t prep_st = nullptr;
     char *hbuf = nullptr;        // device copies of host inputs (ncf_corr_batch_host)
     size_t hbuf_cap = 0;
     char *boot = nullptr;        // bootstrap replicates and their multiplicities
@@ -61,7 +69,7 @@ struct ncf_ctx {
     std::vector<cudaEvent_t> copy_ev;
     NcfProfiler prof;
     ncf_plan_info plan{0.0, 0, 0, 0, 0, 0, 0};
-    ncf_tuning tuning{-1, -1, -1, 0};
+    ncf_tuning tuning{-1, -1, -1, -1};
     std::string err;
 };
 
@@ -121,7 +129,7 @@ ncf_status fail(ncf_ctx *ctx, ncf_status s, const char *fmt, ...) {
 
 // device bytes the context holds now (its workspaces only grow)
 size_t ctx_device_bytes(const ncf_ctx *ctx) {
-    return ctx->ws_cap + ctx->ws2_cap + ctx->hbuf_cap + ctx->boot_cap + ctx->paper_cap;
+    return ctx->ws_cap + ctx->ws_alt_cap + ctx->ws2_cap + ctx->hbuf_cap + ctx->boot_cap + ctx->paper_cap;
 }
 
 ncf_status grow(ncf_ctx *ctx, char **buf, size_t *cap, size_t need, cudaStream_t st) {
@@ -143,23 +151,26 @@ ncf_status grow(ncf_ctx *ctx, char **buf, size_t *cap, size_t need, cudaStream_t
     return NCF_OK;
 }
 
-ncf_status grow_pinned(ncf_ctx *ctx, size_t need, cudaStream_t st) {
-    if (need <= ctx->pinned_cap) return NCF_OK;
-    size_t ncap = std::max(need, ctx->pinned_cap * 2);
-    if (ctx->pinned) {
+ncf_status grow_pinned_buf(ncf_ctx *ctx, char **buf, size_t *cap, size_t need, cudaStream_t st) {
+    if (need <= *cap) return NCF_OK;
+    size_t ncap = std::max(need, *cap * 2);
+    if (*buf) {
         NCF_CUDA(cudaStreamSynchronize(st));
-        NCF_CUDA(cudaFreeHost(ctx->pinned));
-        ctx->pinned = nullptr;
-        ctx->pinned_cap = 0;
+        NCF_CUDA(cudaFreeHost(*buf));
+        *buf = nullptr;
+        *cap = 0;
     }
     // device-mapped: small staging copies are done by a kernel (copy_pinned)
-    if (cudaHostAlloc(&ctx->pinned, ncap, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+    if (cudaHostAlloc(buf, ncap, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
         cudaGetLastError();
-        ctx->pinned = nullptr;
+        *buf = nullptr;
         return fail(ctx, NCF_ENOMEM, "cudaHostAlloc of %zu bytes failed", ncap);
     }
-    ctx->pinned_cap = ncap;
+    *cap = ncap;
     return NCF_OK;
+}
+ncf_status grow_pinned(ncf_ctx *ctx, size_t need, cudaStream_t st) {
+    return grow_pinned_buf(ctx, &ctx->pinned, &ctx->pinned_cap, need, st);
 }
 
 size_t al(size_t b) { return (b + 255) & ~size_t(255); }
@@ -387,13 +398,18 @@ void run_stats(Eval &ev, cudaStream_t st) {
 
 // Uploads the CSR tables, runs the statistics pass and reads back the
 // per-series statistics and the lags (the one host synchronisation).
-ncf_status analyze(ncf_ctx *ctx, Eval &ev, const double *lags, cudaStream_t st) {
+// `pre_staging`: stage through the context's second pinned buffer, not the one the
+// evaluations' preparation uses (a statistics stage that runs beside another
+// chunk's evaluation).
+ncf_status analyze(ncf_ctx *ctx, Eval &ev, const double *lags, cudaStream_t st, bool pre_staging = false) {
     const int64_t B = ev.B, K = ev.K;
     ncf_status rc;
     const size_t up_bytes = al((B + 1) * 8) * 4;
     const size_t down_bytes = al(B * sizeof(SeriesStats)) * 2 + al(K * 8);
-    if ((rc = grow_pinned(ctx, up_bytes + down_bytes, st))) return rc;
-    char *hp = ctx->pinned;
+    char **pin = pre_staging ? &ctx->pinned_pre : &ctx->pinned;
+    size_t *pin_cap = pre_staging ? &ctx->pinned_pre_cap : &ctx->pinned_cap;
+    if ((rc = grow_pinned_buf(ctx, pin, pin_cap, up_bytes + down_bytes, st))) return rc;
+    char *hp = *pin;
     auto upload = [&](void *dst, const void *src, size_t bytes) -> ncf_status {
         std::memcpy(hp, src, bytes);
         copy_pinned(dst, hp, bytes, st);
@@ -409,7 +425,7 @@ ncf_status analyze(ncf_ctx *ctx, Eval &ev, const double *lags, cudaStream_t st) 
     launch_chunk_series(ev.X.d_chunk_base, B, ev.X.d_cs, st);
     if (!ev.acf) launch_chunk_series(ev.Y.d_chunk_base, B, ev.Y.d_cs, st);
     run_stats(ev, st);
-    char *down = ctx->pinned + up_bytes;
+    char *down = *pin + up_bytes;
     copy_pinned(down, ev.X.d_stats, B * sizeof(SeriesStats), st);
     if (!ev.acf) copy_pinned(down + al(B * sizeof(SeriesStats)), ev.Y.d_stats, B * sizeof(SeriesStats), st);
     double *h_lags = reinterpret_cast<double *>(down + 2 * al(B * sizeof(SeriesStats)));
@@ -944,28 +960,39 @@ static ncf_status corr_batch_impl(ncf_ctx *ctx, const int64_t *offs_x, const dou
 // Several option sets (estimators) on one batch: the statistics pass and its
 // read-back run once, then each option set prepares and launches its own path
 // on the same statistics.
-static ncf_status corr_batch_multi_impl(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
-                                        const int64_t *offs_y, const double *s, const double *y, int64_t B,
-                                        const double *lags, int64_t K, const ncf_options *opts, int n_opts,
-                                        double *const *c_out, double *const *b_out, int64_t *const *count_out,
-                                        cudaStream_t st) {
-    LaunchScope scope(ctx);
-    ctx->err.clear();
+// The statistics stage of a batched call with several option sets: arguments
+// checked, the pre-statistics workspace carved from *ws, the statistics pass run
+// on `st` and read back (the host waits for `st` here).  `pre_staging`: the
+// stage runs beside another chunk's evaluation and stages through the second
+// pinned buffer.
+static ncf_status batch_pre(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                            const int64_t *offs_y, const double *s, const double *y, int64_t B, const double *lags,
+                            int64_t K, const ncf_options *opts, int n_opts, double *const *c_out, Eval &ev,
+                            std::vector<int> &paths, char **ws, size_t *ws_cap, bool pre_staging, cudaStream_t st) {
     if (!opts || n_opts < 1 || !c_out) return fail(ctx, NCF_EINVAL, "no option set or c_out is NULL");
-    if (ctx->staged) NCF_CUDA(cudaEventSynchronize(ctx->staged));
-    Eval ev;
+    if (!pre_staging && ctx->staged) NCF_CUDA(cudaEventSynchronize(ctx->staged));
     ncf_status rc = check_args(ctx, offs_x, t, x, offs_y, s, y, B, lags, K, &opts[0], ev);
     if (rc) return rc;
-    std::vector<int> paths(n_opts);
+    paths.assign(n_opts, 0);
     for (int o = 0; o < n_opts; ++o) {
         if (!c_out[o]) return fail(ctx, NCF_EINVAL, "c_out of option set %d is NULL", o);
         if ((rc = check_options(ctx, &opts[o], B, K, &paths[o]))) return rc;
     }
     ev.X.t = t; ev.X.v = x;
     if (!ev.acf) { ev.Y.t = s; ev.Y.v = y; }
-    if ((rc = grow(ctx, &ctx->ws, &ctx->ws_cap, pre_bytes(ev), st))) return rc;
-    carve_pre(ev, ctx->ws);
-    if ((rc = analyze(ctx, ev, lags, st))) return rc;
+    if ((rc = grow(ctx, ws, ws_cap, pre_bytes(ev), st))) return rc;
+    carve_pre(ev, *ws);
+    return analyze(ctx, ev, lags, st, pre_staging);
+}
+
+// The rest of a batched call, on `st` after its statistics stage: each option
+// set prepared and launched.
+static ncf_status batch_main(ncf_ctx *ctx, const Eval &ev, const std::vector<int> &paths, const double *lags,
+                             const ncf_options *opts, int n_opts, double *const *c_out, double *const *b_out,
+                             int64_t *const *count_out, cudaStream_t st) {
+    ncf_status rc;
+    // the pinned staging may still feed the previous evaluation's uploads
+    if (ctx->staged) NCF_CUDA(cudaEventSynchronize(ctx->staged));
     // The host prepares each option set after the statistics read-back while the
     // GPU runs what is already queued: the long real-space scans go first, so the
     // spectral sets' host preparation hides behind them.
@@ -999,6 +1026,21 @@ static ncf_status corr_batch_multi_impl(ncf_ctx *ctx, const int64_t *offs_x, con
             return rc;
     }
     return NCF_OK;
+}
+
+static ncf_status corr_batch_multi_impl(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
+                                        const int64_t *offs_y, const double *s, const double *y, int64_t B,
+                                        const double *lags, int64_t K, const ncf_options *opts, int n_opts,
+                                        double *const *c_out, double *const *b_out, int64_t *const *count_out,
+                                        cudaStream_t st) {
+    LaunchScope scope(ctx);
+    ctx->err.clear();
+    Eval ev;
+    std::vector<int> paths;
+    ncf_status rc = batch_pre(ctx, offs_x, t, x, offs_y, s, y, B, lags, K, opts, n_opts, c_out, ev, paths, &ctx->ws,
+                              &ctx->ws_cap, false, st);
+    if (rc) return rc;
+    return batch_main(ctx, ev, paths, lags, opts, n_opts, c_out, b_out, count_out, st);
 }
 
 // frac(tau / L) 2^64 to about one unit: q = fl(tau / L), the exact remainder
@@ -1264,6 +1306,9 @@ void ncf_destroy(ncf_ctx *ctx) {
     if (ctx->ws2) cudaFree(ctx->ws2);
     if (ctx->hbuf) cudaFree(ctx->hbuf);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    if (ctx->ws_alt) cudaFree(ctx->ws_alt);
+    if (ctx->pinned_pre) cudaFreeHost(ctx->pinned_pre);
+    if (ctx->prep_st) cudaStreamDestroy(ctx->prep_st);
     if (ctx->staged) cudaEventDestroy(ctx->staged);
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
     if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
@@ -1535,6 +1580,7 @@ static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *
                              const double *lags, int64_t K, const ncf_options *opts, int n_opts,
                              double *const *c_out, double *const *b_out, int64_t *const *count_out,
                              cudaStream_t st, const char *who) {
+    ctx->err.clear();
     if (!offs_x || B < 1 || K < 1 || !t || !x || !lags || !opts || n_opts < 1 || !c_out) {
         ctx->err = std::string(who) + ": NULL pointer, empty batch or no option set";
         return NCF_EINVAL;
@@ -1575,8 +1621,11 @@ static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *
     // (four chunks: 0.5 ms more per bench step; six: no better).  The
     // evaluations' own small transfers (statistics read-back, table uploads) go
     // through copy_pinned, a kernel, so they never wait behind the bulk uploads
-    // on the copy engines.  Pinned host buffers are needed for the copies to
-    // overlap.
+    // on the copy engines.  Chunk i + 1's statistics stage (pass, read-back and
+    // the host's wait for it) runs on a fourth stream while chunk i's evaluation
+    // is on the GPU, so the host prepares chunk i + 1 with no gap on the device;
+    // consecutive chunks take turns with two pre-statistics workspaces.  Pinned
+    // host buffers are needed for the copies to overlap.
     const int64_t pts = nx + ny;
     const int C = (int)std::min<int64_t>(B, pts * 16 > (int64_t)(256 << 20) ? 5 : 1);
     std::vector<int64_t> cut(C + 1, B);
@@ -1591,17 +1640,20 @@ static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *
         return fail(ctx, NCF_ECUDA, "%s: copy stream creation failed", who);
     if (!ctx->back_st && cudaStreamCreateWithFlags(&ctx->back_st, cudaStreamNonBlocking) != cudaSuccess)
         return fail(ctx, NCF_ECUDA, "%s: copy stream creation failed", who);
-    while ((int)ctx->copy_ev.size() < 2 * C + 1) {
+    if (!ctx->prep_st && cudaStreamCreateWithFlags(&ctx->prep_st, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(ctx, NCF_ECUDA, "%s: stream creation failed", who);
+    while ((int)ctx->copy_ev.size() < 2 * C + 2) {
         cudaEvent_t e;
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
             return fail(ctx, NCF_ECUDA, "%s: event creation failed", who);
         ctx->copy_ev.push_back(e);
     }
-    cudaStream_t cs = ctx->copy_st, rs = ctx->back_st;
-    cudaEvent_t *ev_in = ctx->copy_ev.data(), *ev_out = ev_in + C, ev_start = ev_in[2 * C];
-    // the copy streams start after the work already queued on the caller's stream
+    cudaStream_t cs = ctx->copy_st, rs = ctx->back_st, ps = ctx->prep_st;
+    cudaEvent_t *ev_in = ctx->copy_ev.data(), *ev_out = ev_in + C, ev_start = ev_in[2 * C], ev_pre = ev_in[2 * C + 1];
+    // the copy and statistics streams start after the work already queued on the caller's stream
     bool ok = cudaEventRecord(ev_start, st) == cudaSuccess && cudaStreamWaitEvent(cs, ev_start, 0) == cudaSuccess &&
-              cudaStreamWaitEvent(rs, ev_start, 0) == cudaSuccess;
+              cudaStreamWaitEvent(rs, ev_start, 0) == cudaSuccess &&
+              cudaStreamWaitEvent(ps, ev_start, 0) == cudaSuccess;
     auto upload = [&](int c) {
         const int64_t b0 = cut[c], b1 = cut[c + 1];
         const int64_t x0 = offs_x[b0], x1 = offs_x[b1];
@@ -1617,19 +1669,56 @@ static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *
     ok = ok && cudaMemcpyAsync(dl, lags, K * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
     for (int c = 0; c < C; ++c) ok = ok && upload(c);
     if (!ok) return fail(ctx, NCF_ECUDA, "host-to-device copy failed: %s", cudaGetErrorString(cudaGetLastError()));
-    std::vector<int64_t> ox, oy;
+    // chunk c's statistics stage, on the statistics stream once its upload has
+    // landed and (c >= 2) chunk c - 2's evaluation, the last user of its
+    // workspace, has finished
+    struct Pre {
+        Eval ev;
+        std::vector<int> paths;
+        std::vector<int64_t> ox, oy;
+    };
+    Pre pre[2];
+    auto run_pre = [&](int c) -> ncf_status {
+        const int64_t b0 = cut[c], b1 = cut[c + 1], nb = b1 - b0;
+        if (nb <= 0) return NCF_OK;
+        Pre &P = pre[c & 1];
+        P = Pre{};
+        const int64_t x0 = offs_x[b0], y0 = acf ? 0 : offs_y[b0];
+        P.ox.assign(offs_x + b0, offs_x + b1 + 1);
+        for (auto &v : P.ox) v -= x0;
+        if (!acf) {
+            P.oy.assign(offs_y + b0, offs_y + b1 + 1);
+            for (auto &v : P.oy) v -= y0;
+        }
+        if (cudaStreamWaitEvent(ps, ev_in[c], 0) != cudaSuccess ||
+            (c >= 2 && cudaStreamWaitEvent(ps, ev_out[c - 2], 0) != cudaSuccess))
+            return fail(ctx, NCF_ECUDA, "%s: stream wait failed", who);
+        std::vector<double *> cc(n_opts);
+        for (int o = 0; o < n_opts; ++o) cc[o] = dc[o] + b0 * K;
+        return batch_pre(ctx, P.ox.data(), dt + x0, dx + x0, acf ? nullptr : P.oy.data(), acf ? nullptr : ds + y0,
+                         acf ? nullptr : dy + y0, nb, dl, K, opts, n_opts, cc.data(), P.ev, P.paths,
+                         (c & 1) ? &ctx->ws_alt : &ctx->ws, (c & 1) ? &ctx->ws_alt_cap : &ctx->ws_cap, true, ps);
+    };
+    auto bail = [&](ncf_status r) {
+        cudaStreamSynchronize(cs);
+        cudaStreamSynchronize(rs);
+        cudaStreamSynchronize(ps);
+        return r;
+    };
+    // the lags go up on the caller's stream; the statistics stages read them too
+    if (!ok || cudaEventRecord(ev_pre, st) != cudaSuccess || cudaStreamWaitEvent(ps, ev_pre, 0) != cudaSuccess)
+        return bail(fail(ctx, NCF_ECUDA, "%s: stream wait failed", who));
+    {
+        LaunchScope scope(ctx);
+        if ((rc = run_pre(0))) return bail(rc);
+    }
     for (int c = 0; c < C; ++c) {
         const int64_t b0 = cut[c], b1 = cut[c + 1], nb = b1 - b0;
         if (nb > 0) {
-            const int64_t x0 = offs_x[b0], y0 = acf ? 0 : offs_y[b0];
-            ox.assign(offs_x + b0, offs_x + b1 + 1);
-            for (auto &v : ox) v -= x0;
-            if (!acf) {
-                oy.assign(offs_y + b0, offs_y + b1 + 1);
-                for (auto &v : oy) v -= y0;
-            }
-            if (cudaStreamWaitEvent(st, ev_in[c], 0) != cudaSuccess)
-                return fail(ctx, NCF_ECUDA, "%s: stream wait failed", who);
+            LaunchScope scope(ctx);
+            // the evaluation waits for its statistics stage
+            if (cudaEventRecord(ev_pre, ps) != cudaSuccess || cudaStreamWaitEvent(st, ev_pre, 0) != cudaSuccess)
+                return bail(fail(ctx, NCF_ECUDA, "%s: stream wait failed", who));
             std::vector<double *> cc(n_opts), bb(n_opts);
             std::vector<int64_t *> nn(n_opts);
             for (int o = 0; o < n_opts; ++o) {
@@ -1638,14 +1727,9 @@ static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *
                 nn[o] = no(o) ? dn[o] + b0 * K : nullptr;
             }
             // one statistics pass for every option set of the chunk
-            rc = corr_batch_multi_impl(ctx, ox.data(), dt + x0, dx + x0, acf ? nullptr : oy.data(),
-                                       acf ? nullptr : ds + y0, acf ? nullptr : dy + y0, nb, dl, K, opts, n_opts,
-                                       cc.data(), bb.data(), nn.data(), st);
-            if (rc) {
-                cudaStreamSynchronize(cs);
-                cudaStreamSynchronize(rs);
-                return rc;
-            }
+            rc = batch_main(ctx, pre[c & 1].ev, pre[c & 1].paths, dl, opts, n_opts, cc.data(), bb.data(), nn.data(),
+                            st);
+            if (rc) return bail(rc);
         }
         ok = cudaEventRecord(ev_out[c], st) == cudaSuccess;
         ok = ok && cudaStreamWaitEvent(rs, ev_out[c], 0) == cudaSuccess;
@@ -1656,9 +1740,13 @@ static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *
             ok = ok && d2h(c_out[o] + b0 * K, dc[o] + b0 * K) && (!bo(o) || d2h(bo(o) + b0 * K, db[o] + b0 * K)) &&
                  (!no(o) || d2h(no(o) + b0 * K, dn[o] + b0 * K));
         if (!ok) break;
+        if (c + 1 < C) {  // the next chunk's statistics, beside this chunk's evaluation
+            LaunchScope scope(ctx);
+            if ((rc = run_pre(c + 1))) return bail(rc);
+        }
     }
     if (!ok || cudaStreamSynchronize(cs) != cudaSuccess || cudaStreamSynchronize(rs) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaStreamSynchronize(ps) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
         ctx->err = std::string("copy failed: ") + cudaGetErrorString(cudaGetLastError());
         return NCF_ECUDA;
     }

@@ -85,3 +85,39 @@ def test_several_estimators_ccf_with_optional_outputs_left_out():
         assert max_abs(got["c"].numpy()[0], ref["c"]) < 1e-10
         if "count" in got:
             assert np.array_equal(got["count"].numpy()[0], ref["count"])
+
+
+def test_chunked_host_batch_ccf_and_repeated_calls():
+    """A chunked batch of cross-correlations (both sides uploaded per chunk, each
+    chunk's statistics stage beside the previous chunk's evaluation), called
+    twice on one context with a device-buffer call in between: every call equals
+    the device-buffer call (the rectangle exactly)."""
+    rng = np.random.default_rng(31)
+    xs, ys = [], []
+    for b in range(24):
+        c = synth.ou_ccf(nA=int(rng.integers(350_000, 450_000)), nB=int(rng.integers(350_000, 450_000)), K=33,
+                         seed=500 + b)
+        xs.append((c.t, c.x))
+        ys.append((c.s, c.y))
+        lags = c.lags
+    ox = np.concatenate([[0], np.cumsum([t.size for t, _ in xs])]).astype(np.int64)
+    oy = np.concatenate([[0], np.cumsum([s.size for s, _ in ys])]).astype(np.int64)
+    t = np.concatenate([a for a, _ in xs]); x = np.concatenate([b for _, b in xs])
+    s = np.concatenate([a for a, _ in ys]); y = np.concatenate([b for _, b in ys])
+    assert (t.size + s.size) * 16 > (256 << 20)  # the chunked path
+    kw = dict(kernel="rectangle", h=0.5, offs_y=oy)
+    ctx = api.Context()
+    try:
+        ref = to_np(api.corr_batch(ox, t, x, lags, s=s, y=y, ctx=ctx, **kw))
+        for _ in range(2):
+            B, K = ox.size - 1, lags.size
+            out = {"c": torch.empty(B, K, dtype=torch.float64).pin_memory(),
+                   "count": torch.empty(B, K, dtype=torch.int64).pin_memory()}
+            api.corr_batch_host(ox, pinned(t), pinned(x), pinned(lags), s=pinned(s), y=pinned(y), out=out, ctx=ctx,
+                                **kw)
+            assert np.array_equal(out["count"].numpy(), ref["count"])
+            assert np.array_equal(out["c"].numpy(), ref["c"])
+            dev = to_np(api.corr_batch(ox, t, x, lags, s=s, y=y, ctx=ctx, **kw))
+            assert np.array_equal(dev["c"], ref["c"])
+    finally:
+        ctx.close()
