@@ -668,8 +668,25 @@ __device__ __forceinline__ void sfft_pass(float2 *g, int lg, int Llg, const floa
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = g[sfft_pad(base + (r << slg))];
         dft<R>(v);
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], sfft_tw(T1, T2, (j * r) << blg));
+        // twiddles w^(q r), q = j 2^blg: w^q, w^2q and w^4q from the tables, the
+        // others as their products (about 3 ulp), so that a butterfly reads 3
+        // table pairs instead of R - 1
+        const int q = j << blg;
+        const float2 w1 = sfft_tw(T1, T2, q);
+        v[1] = cmul(v[1], w1);
+        if constexpr (R >= 4) {
+            const float2 w2 = sfft_tw(T1, T2, 2 * q);
+            v[2] = cmul(v[2], w2);
+            const float2 w3 = cmul(w2, w1);
+            v[3] = cmul(v[3], w3);
+            if constexpr (R == 8) {
+                const float2 w4 = sfft_tw(T1, T2, 4 * q);
+                v[4] = cmul(v[4], w4);
+                v[5] = cmul(v[5], cmul(w4, w1));
+                v[6] = cmul(v[6], cmul(w4, w2));
+                v[7] = cmul(v[7], cmul(w4, w3));
+            }
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) g[sfft_pad(base + (r << slg))] = v[r];
     }
