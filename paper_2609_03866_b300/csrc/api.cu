@@ -256,17 +256,16 @@ ncf_status check_stats(ncf_ctx *ctx, const Side &sd, int64_t B, const char *name
     return NCF_OK;
 }
 
-FixedScales choose_scales(double m_abs, int64_t n_max) {
-    FixedScales fs;
+// Time-key scale of a rectangle scan from the largest |time| it compares (the
+// value bits are per series side: value_bits in common.cuh).
+FixedScales choose_scales(double m_abs) {
+    FixedScales fs{};
     int e = 0;
     std::frexp(std::max(m_abs, 1e-300), &e);  // m_abs < 2^e
     fs.q = std::max(-1000, std::min(1000, 60 - e));
     fs.tscale = std::ldexp(1.0, fs.q);
     // two FP64 roundings of magnitude <= m_abs, plus three floor() truncations
     fs.eta = 4 + (int64_t)std::ldexp(1.0, e - 52 + fs.q);
-    const double lg = 1.5 * std::log2((double)std::max<int64_t>(n_max, 2));
-    fs.p = std::max(8, std::min(40, (int)std::floor(61.0 - lg)));
-    fs.vscale = std::ldexp(1.0, fs.p);
     return fs;
 }
 
@@ -469,6 +468,20 @@ ncf_status analyze(ncf_ctx *ctx, Eval &ev, const double *lags, cudaStream_t st, 
     return NCF_OK;
 }
 
+// Value bits of a rectangle evaluation's sides: each series side by its own
+// size; a shard standardised with pooled statistics by the whole series' size,
+// so that shards of one series quantise alike.
+ValueBits value_bits_of(const Eval &ev) {
+    ValueBits vb;
+    vb.offs_x = ev.X.d_offs;
+    vb.offs_y = ev.acf ? nullptr : ev.Y.d_offs;
+    if (ev.pooled) {
+        vb.nfx = ev.pooled->n_x;
+        vb.nfy = ev.acf ? 0 : ev.pooled->n_y;
+    }
+    return vb;
+}
+
 SpectralArgs spectral_args(const Eval &ev, double *c_out, double *b_out, int64_t *count_out) {
     SpectralArgs sa;
     sa.acf = ev.acf;
@@ -545,11 +558,7 @@ ncf_status prepare(ncf_ctx *ctx, Eval &ev, char *mem, size_t cap, char *pinned, 
     ev.d_lags = d_lags;
     if (rect_scan(ev)) {
         Side &X = ev.X, &O = ev.outer();
-        // |x_std| <= sqrt(n) bounds the quantised values; pooled statistics come from
-        // the whole series, so its size bounds them
-        int64_t n_bound = std::max(X.n_max, O.n_max);
-        if (ev.pooled) n_bound = std::max({n_bound, ev.pooled->n_x, ev.pooled->n_y});
-        ev.fs = choose_scales(ev.t_abs + ev.max_tau + ev.opt.h + 1.0, n_bound);
+        ev.fs = choose_scales(ev.t_abs + ev.max_tau + ev.opt.h + 1.0);
         auto keys = [&](const Side &sd, int64_t *&T, int64_t *&Xq, int64_t *&P, int64_t *&C) {
             T = a2.take<int64_t>(sd.n_total);
             Xq = a2.take<int64_t>(sd.n_total);
@@ -653,11 +662,12 @@ ncf_status launch(ncf_ctx *ctx, Eval &ev, bool stats_fresh, bool guard, double *
     if (guard && first) launch_stats_guard(ev.X.d_stats, ev.acf ? nullptr : ev.Y.d_stats, B, ev.status, st);
     Side &X = ev.X, &O = ev.outer();
     if (rect_scan(ev)) {
+        const ValueBits vb = value_bits_of(ev);
         launch_keys_prefix(X.t, X.v, X.d_offs, X.d_chunk_base, X.d_cs, X.n_chunks, kPrepChunk, X.d_stats, ev.fs,
-                           ev.kxT, ev.kxX, ev.kxP, ev.kxC, X.n_total, st);
+                           vb.nfx, ev.kxT, ev.kxX, ev.kxP, ev.kxC, X.n_total, st);
         if (!ev.acf)
             launch_keys_prefix(ev.Y.t, ev.Y.v, ev.Y.d_offs, ev.Y.d_chunk_base, ev.Y.d_cs, ev.Y.n_chunks, kPrepChunk,
-                               ev.Y.d_stats, ev.fs, ev.kyT, ev.kyX, ev.kyP, ev.kyC, ev.Y.n_total, st);
+                               ev.Y.d_stats, ev.fs, vb.nfy, ev.kyT, ev.kyX, ev.kyP, ev.kyC, ev.Y.n_total, st);
         if (guard) launch_keys_guard(ev.X.d_stats, ev.acf ? nullptr : ev.Y.d_stats, B, ev.t_abs, ev.status, st);
         NCF_CUDA(cudaMemsetAsync(ev.cnt, 0, B * K * 8, st));
         NCF_CUDA(cudaMemsetAsync(ev.num, 0, 2 * B * K * 8, st));
@@ -665,7 +675,6 @@ ncf_status launch(ncf_ctx *ctx, Eval &ev, bool stats_fresh, bool guard, double *
         RectArgs ra{ev.kxT, ev.kxP, X.t, X.d_offs, ev.kyT, ev.kyX, O.t, &O.offs, B, K, ev.lagv.data(), eps,
                     ev.opt.h, ev.fs, ev.cnt, ev.num};
         if ((rc = rect_launch(ra, ev.r_main, st, &msg))) return fail(ctx, rc, "%s", msg.c_str());
-        const double inv_v2 = std::ldexp(1.0, -2 * ev.fs.p);
         if (ev.lag0) {
             NCF_CUDA(cudaMemsetAsync(ev.cnt0, 0, 2 * B * 8, st));
             NCF_CUDA(cudaMemsetAsync(ev.num0, 0, 4 * B * 8, st));
@@ -680,9 +689,9 @@ ncf_status launch(ncf_ctx *ctx, Eval &ev, bool stats_fresh, bool guard, double *
                 if ((rc = rect_launch(ay, ev.r_y, st, &msg))) return fail(ctx, rc, "%s", msg.c_str());
             }
             launch_lag0_scale_rect(ev.cnt0, ev.num0, ev.acf ? nullptr : ev.cnt0 + B,
-                                   ev.acf ? nullptr : ev.num0 + 2 * B, B, inv_v2, ev.scale, st);
+                                   ev.acf ? nullptr : ev.num0 + 2 * B, B, vb, ev.scale, st);
         }
-        launch_finish_rect(ev.cnt, ev.num, B, K, inv_v2, ev.lag0 ? ev.scale : nullptr, ev.status, c_out, b_out,
+        launch_finish_rect(ev.cnt, ev.num, B, K, vb, ev.lag0 ? ev.scale : nullptr, ev.status, c_out, b_out,
                            count_out, st);
     } else if (ev.path == NCF_PATH_WINDOWED) {
         const int hann = ev.opt.kernel == NCF_HANNING;
@@ -788,11 +797,12 @@ ncf_status tune_rect(ncf_ctx *ctx, Eval &ev, cudaStream_t st) {
     }
     const int64_t B = ev.B, K = ev.K;
     Side &X = ev.X, &O = ev.outer();
+    const ValueBits vb = value_bits_of(ev);
     launch_keys_prefix(X.t, X.v, X.d_offs, X.d_chunk_base, X.d_cs, X.n_chunks, kPrepChunk, X.d_stats, ev.fs,
-                       ev.kxT, ev.kxX, ev.kxP, ev.kxC, X.n_total, st);
+                       vb.nfx, ev.kxT, ev.kxX, ev.kxP, ev.kxC, X.n_total, st);
     if (!ev.acf)
         launch_keys_prefix(ev.Y.t, ev.Y.v, ev.Y.d_offs, ev.Y.d_chunk_base, ev.Y.d_cs, ev.Y.n_chunks, kPrepChunk,
-                           ev.Y.d_stats, ev.fs, ev.kyT, ev.kyX, ev.kyP, ev.kyC, ev.Y.n_total, st);
+                           ev.Y.d_stats, ev.fs, vb.nfy, ev.kyT, ev.kyX, ev.kyP, ev.kyC, ev.Y.n_total, st);
     cudaEvent_t e[kRectVariants + 1];
     for (auto &x : e) NCF_CUDA(cudaEventCreate(&x));
     std::string msg;
@@ -1575,6 +1585,16 @@ namespace ncf {
 
 // The host-buffer calls: one upload of the batch, then n_opts evaluations of it
 // (each option set its own result buffers), chunk by chunk.
+// growth factor of the host-buffer calls' chunk sizes; the copies (about 55 GB/s)
+// stay ahead of the evaluation as long as it is below the ratio of the
+// evaluation's time to the upload's (3.2 on the light-curve batch)
+constexpr int64_t kChunkGrowth = 3;
+static int64_t ipow(int64_t b, int e) {
+    int64_t r = 1;
+    while (e-- > 0) r *= b;
+    return r;
+}
+
 static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *t, const double *x,
                              const int64_t *offs_y, const double *s, const double *y, int64_t B,
                              const double *lags, int64_t K, const ncf_options *opts, int n_opts,
@@ -1616,9 +1636,9 @@ static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *
     // queued at once on the copy stream, so the link streams the whole batch
     // without a pause, and chunk i's evaluation (the caller's stream) starts when
     // its own upload has landed; each chunk's results come back on a third stream
-    // while the next chunk runs.  Chunk sizes double (1/31, 2/31, ..., 16/31 of
-    // the points): only the first, small upload waits with nothing to overlap
-    // (four chunks: 0.5 ms more per bench step; six: no better).  The
+    // while the next chunk runs.  Chunk sizes triple (1/121, 3/121, ..., 81/121 of
+    // the points; kChunkGrowth): only the first, small upload waits with nothing
+    // to overlap.  The
     // evaluations' own small transfers (statistics read-back, table uploads) go
     // through copy_pinned, a kernel, so they never wait behind the bulk uploads
     // on the copy engines.  Chunk i + 1's statistics stage (pass, read-back and
@@ -1631,7 +1651,7 @@ static ncf_status host_batch(ncf_ctx *ctx, const int64_t *offs_x, const double *
     std::vector<int64_t> cut(C + 1, B);
     cut[0] = 0;
     for (int c = 1; c < C; ++c) {
-        const int64_t target = pts * ((int64_t(1) << c) - 1) / ((int64_t(1) << C) - 1);
+        const int64_t target = pts * (ipow(kChunkGrowth, c) - 1) / (ipow(kChunkGrowth, C) - 1);
         int64_t b = cut[c - 1];
         while (b < B && offs_x[b] + (acf ? 0 : offs_y[b]) < target) ++b;
         cut[c] = std::max(b, cut[c - 1]);

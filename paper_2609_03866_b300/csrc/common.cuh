@@ -43,13 +43,41 @@ struct ChunkPartial {
 };
 
 // Fixed-point scales of the exact rectangle scan.
-//   time keys:  T = floor(t * 2^q)               (monotone in t)
-//   values:     X = round(x_std * 2^p)           (exact integer prefix sums)
+//   time keys:  T = floor(t * 2^q)               (monotone in t; one q per call)
+//   values:     X = round(x_std * 2^p)           (exact integer prefix sums; p per
+//                                                  series side, value_bits below)
 struct FixedScales {
     double tscale;    // 2^q
-    double vscale;    // 2^p
     int64_t eta;      // half-width of the ambiguity band of a window bound, key units
-    int32_t q, p;
+    int32_t q, pad;
+};
+
+// Value bits p of a series side of n points: p = 61 - ceil(1.5 ceil(log2 n)),
+// clamped to [8, 40], so that p <= 61 - 1.5 log2 n bounds the quantised values
+// (|x_std| <= sqrt(n)) and their window sums as the scan's 128-bit sums assume.
+// Integer arithmetic only: host and device agree, and a series' quantisation
+// depends on its own length alone, not on the other series of its batch.
+__host__ __device__ inline int value_bits(int64_t n) {
+    const unsigned long long m = (unsigned long long)(n > 2 ? n - 1 : 1);
+#ifdef __CUDA_ARCH__
+    const int L = 64 - __clzll((long long)m);
+#else
+    const int L = 64 - __builtin_clzll(m);
+#endif
+    const int p = 61 - (3 * L + 1) / 2;
+    return p < 8 ? 8 : (p > 40 ? 40 : p);
+}
+// The value bits of side x (and y) of series b: its own point count, or n_force
+// (> 0) for a shard standardised with a whole series' pooled statistics.
+struct ValueBits {
+    const int64_t *offs_x = nullptr, *offs_y = nullptr;  // offs_y NULL: an ACF (y = x)
+    int64_t nfx = 0, nfy = 0;
+#ifdef __CUDACC__
+    __device__ int px(int64_t b) const { return value_bits(nfx > 0 ? nfx : offs_x[b + 1] - offs_x[b]); }
+    __device__ int py(int64_t b) const {
+        return offs_y ? value_bits(nfy > 0 ? nfy : offs_y[b + 1] - offs_y[b]) : px(b);
+    }
+#endif
 };
 
 // Stream-ordered bump allocator over the context workspace.
@@ -84,9 +112,10 @@ void launch_keys_guard(const SeriesStats *sx, const SeriesStats *sy, int64_t B, 
                        cudaStream_t st);
 // Fixed-point keys and the exclusive prefix sum of the quantised standardised values.
 // Writes Tk[total], Xq[total] and P[total + 1].
+// Side values quantised with value_bits of their series (n_force > 0: of n_force points).
 void launch_keys_prefix(const double *t, const double *x, const int64_t *offs,
                         const int64_t *chunk_base, const int32_t *cs, int64_t n_chunks, int chunk,
-                        const SeriesStats *stats, FixedScales fs, int64_t *Tk, int64_t *Xq,
+                        const SeriesStats *stats, FixedScales fs, int64_t n_force, int64_t *Tk, int64_t *Xq,
                         int64_t *P, int64_t *chunk_sums, int64_t n_total, cudaStream_t st);
 
 // ---- real-space scans (k_scan.cu) ----
@@ -157,7 +186,7 @@ int scan_tile_points();
 // scale = c_xx(0) or sqrt(c_xx(0) * c_yy(0)) (Algorithms 4 and 10).
 void launch_lag0_scale_rect(const unsigned long long *cnt_x, const unsigned long long *num_x,
                             const unsigned long long *cnt_y, const unsigned long long *num_y,
-                            int64_t B, double inv_v2, double *scale, cudaStream_t st);
+                            int64_t B, ValueBits vb, double *scale, cudaStream_t st);
 void launch_lag0_scale_gauss(const double *num_x, const double *den_x, const double *num_y,
                              const double *den_y, int64_t B, double *scale, cudaStream_t st);
 // Small staging copies between device memory and a context's pinned host
@@ -170,8 +199,9 @@ void copy_pinned(void *dst, const void *src, size_t bytes, cudaStream_t st);
 // c = N / max(B, 1e-16) from the scan accumulators; optional lag-0 scaling.
 // status (nullable): a nonzero status word turns every result into NaN
 // (count -1): a device-side check of an executed plan failed.
+// N in units of 2^(px + py) of series b (ValueBits).
 void launch_finish_rect(const unsigned long long *cnt, const unsigned long long *num128,
-                        int64_t B, int64_t K, double inv_v2, const double *scale, const int *status,
+                        int64_t B, int64_t K, ValueBits vb, const double *scale, const int *status,
                         double *c, double *b, int64_t *count, cudaStream_t st);
 void launch_finish_gauss(const double *num, const double *den, const unsigned long long *cnt,
                          int64_t B, int64_t K, const double *scale, const int *status, double *c,

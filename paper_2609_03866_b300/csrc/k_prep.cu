@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kThreads)
 keys_chunks_kernel(const double *__restrict__ t, const double *__restrict__ x,
                    const int64_t *__restrict__ offs, const int64_t *__restrict__ chunk_base,
                    const int32_t *__restrict__ cs, int chunk, const SeriesStats *__restrict__ stats,
-                   FixedScales fs, int64_t *__restrict__ Tk, int64_t *__restrict__ Xq,
+                   FixedScales fs, int64_t n_force, int64_t *__restrict__ Tk, int64_t *__restrict__ Xq,
                    unsigned long long *__restrict__ chunk_sums) {
     const int64_t g = blockIdx.x;
     const int64_t b = cs[g];
@@ -212,6 +212,7 @@ keys_chunks_kernel(const double *__restrict__ t, const double *__restrict__ x,
     const int64_t start = a0 + (g - chunk_base[b]) * (int64_t)chunk;
     const int64_t end = min(start + (int64_t)chunk, a1);
     const double mean = stats[b].mean, inv = stats[b].inv_std;
+    const int p = value_bits(n_force > 0 ? n_force : a1 - a0);
     unsigned long long acc = 0;
 #pragma unroll 4
     for (int r = 0; r < kPrepChunk / kThreads; ++r) {
@@ -219,7 +220,7 @@ keys_chunks_kernel(const double *__restrict__ t, const double *__restrict__ x,
         if (i < end) {
             Tk[i] = fixed_floor(t[i], fs.q);
             // round(x_std 2^p) = floor(x_std 2^(p+1) + 1) >> 1, half up
-            const long long q2 = fixed_floor((x[i] - mean) * inv, fs.p + 1);
+            const long long q2 = fixed_floor((x[i] - mean) * inv, p + 1);
             const long long q = (q2 + 1) >> 1;
             Xq[i] = q;
             acc += (unsigned long long)q;
@@ -387,13 +388,13 @@ void launch_stats_finish(const double *t, const double *x, const int64_t *offs,
 
 void launch_keys_prefix(const double *t, const double *x, const int64_t *offs,
                         const int64_t *chunk_base, const int32_t *cs, int64_t n_chunks, int chunk,
-                        const SeriesStats *stats, FixedScales fs, int64_t *Tk, int64_t *Xq,
+                        const SeriesStats *stats, FixedScales fs, int64_t n_force, int64_t *Tk, int64_t *Xq,
                         int64_t *P, int64_t *chunk_sums, int64_t n_total, cudaStream_t st) {
     // chunk must equal kThreads * kItems (= kPrepChunk) for prefix_apply_kernel
     auto *csum = reinterpret_cast<unsigned long long *>(chunk_sums);
     NCF_LAUNCH("keys_chunks_kernel", st,
                keys_chunks_kernel<<<(unsigned)n_chunks, kThreads, 0, st>>>(t, x, offs, chunk_base, cs, chunk,
-                                                                            stats, fs, Tk, Xq, csum));
+                                                                            stats, fs, n_force, Tk, Xq, csum));
     NCF_LAUNCH("scan_chunk_sums_kernel", st,
                scan_chunk_sums_kernel<<<1, 1024, 0, st>>>(csum, n_chunks, csum + n_chunks));
     NCF_LAUNCH("prefix_apply_kernel", st,

@@ -9,7 +9,8 @@
 //    S_j + e Tau_k - H differs from the scaled FP64 bound by less than eta
 //    units, so a key more than eta below / at least eta above decides the
 //    comparison; a key inside the band is decided by the FP64 predicate itself.
-//  * numerators.  X = round(x_std 2^p), P = int64 prefix sums (wrap-around; a
+//  * numerators.  X = round(x_std 2^p) with p the value bits of the series side
+//    (value_bits of its length), P = int64 prefix sums (wrap-around; a
 //    window sum is exact whenever its value fits in 63 bits), N accumulated in
 //    128-bit integers: order-independent and identical on every run.
 //
@@ -309,7 +310,7 @@ rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
 // signed), so one 16-byte load at a window edge yields both the key the edge
 // search compares and the prefix sum the numerator needs.
 //
-// Numerators.  With p <= 61 - 1.5 log2(n_max) and |x_std| <= sqrt(n) the
+// Numerators.  With p <= 61 - 1.5 log2(n) for each series side and |x_std| <= sqrt(n) the
 // quantised values satisfy |Y| < 2^61 and every window sum |w| < 2^62.  The
 // limb differences of w = P[hi] - P[lo] are d0, d1 in (-2^21, 2^21) and d2 (the
 // top-limb difference taken modulo 2^22, exact because |w| < 2^62), and

@@ -180,12 +180,14 @@ __device__ __forceinline__ bool failed_write(const int *status, int64_t i, doubl
 
 __global__ void finish_rect_kernel(const unsigned long long *__restrict__ cnt,
                                    const unsigned long long *__restrict__ num128, int64_t B,
-                                   int64_t K, double inv_v2, const double *__restrict__ scale,
+                                   int64_t K, ValueBits vb, const double *__restrict__ scale,
                                    const int *__restrict__ status, double *__restrict__ c,
                                    double *__restrict__ b, int64_t *__restrict__ count) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * K) return;
     if (failed_write(status, i, c, b, count)) return;
+    const int64_t sb = i / K;
+    const double inv_v2 = ldexp(1.0, -(vb.px(sb) + vb.py(sb)));
     const unsigned long long n = cnt[i];
     const double N = ((double)(long long)num128[2 * i + 1] * 18446744073709551616.0 +
                       (double)num128[2 * i]) * inv_v2;
@@ -216,15 +218,17 @@ __global__ void lag0_scale_rect_kernel(const unsigned long long *__restrict__ cx
                                        const unsigned long long *__restrict__ nx,
                                        const unsigned long long *__restrict__ cy,
                                        const unsigned long long *__restrict__ ny, int64_t B,
-                                       double inv_v2, double *__restrict__ scale) {
+                                       ValueBits vb, double *__restrict__ scale) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    auto val = [&](const unsigned long long *c, const unsigned long long *n) {
-        const double N = ((double)(long long)n[2 * b + 1] * 18446744073709551616.0 + (double)n[2 * b]) * inv_v2;
+    // the lag-0 ACF of side x is in units of 2^(2 px), of side y in 2^(2 py)
+    auto val = [&](const unsigned long long *c, const unsigned long long *n, int p) {
+        const double N = ((double)(long long)n[2 * b + 1] * 18446744073709551616.0 + (double)n[2 * b]) *
+                         ldexp(1.0, -2 * p);
         return N / fmax((double)c[b], 1e-16);
     };
-    const double sx = val(cx, nx);
-    scale[b] = cy ? sqrt(sx * val(cy, ny)) : sx;
+    const double sx = val(cx, nx, vb.px(b));
+    scale[b] = cy ? sqrt(sx * val(cy, ny, vb.py(b))) : sx;
 }
 
 __global__ void lag0_scale_gauss_kernel(const double *__restrict__ nx, const double *__restrict__ dx,
@@ -242,10 +246,10 @@ int scan_tile_points() { return kTileJ; }
 
 void launch_lag0_scale_rect(const unsigned long long *cnt_x, const unsigned long long *num_x,
                             const unsigned long long *cnt_y, const unsigned long long *num_y,
-                            int64_t B, double inv_v2, double *scale, cudaStream_t st) {
+                            int64_t B, ValueBits vb, double *scale, cudaStream_t st) {
     NCF_LAUNCH("lag0_scale_rect_kernel", st,
     lag0_scale_rect_kernel<<<(unsigned)((B + 127) / 128), 128, 0, st>>>(cnt_x, num_x, cnt_y, num_y, B,
-                                                                         inv_v2, scale));
+                                                                         vb, scale));
 }
 
 void launch_lag0_scale_gauss(const double *num_x, const double *den_x, const double *num_y,
@@ -272,11 +276,11 @@ void launch_gauss_window(const double *tx, const double *x, const int64_t *offs_
 }
 
 void launch_finish_rect(const unsigned long long *cnt, const unsigned long long *num128,
-                        int64_t B, int64_t K, double inv_v2, const double *scale, const int *status,
+                        int64_t B, int64_t K, ValueBits vb, const double *scale, const int *status,
                         double *c, double *b, int64_t *count, cudaStream_t st) {
     const int64_t n = B * K;
     NCF_LAUNCH("finish_rect_kernel", st,
-    finish_rect_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cnt, num128, B, K, inv_v2, scale, status,
+    finish_rect_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cnt, num128, B, K, vb, scale, status,
                                                                      c, b, count));
 }
 

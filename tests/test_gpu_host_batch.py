@@ -121,3 +121,18 @@ def test_chunked_host_batch_ccf_and_repeated_calls():
             assert np.array_equal(dev["c"], ref["c"])
     finally:
         ctx.close()
+
+
+def test_rectangle_result_of_a_series_does_not_depend_on_its_batch():
+    """The rectangle's fixed-point values are scaled by each series' own length
+    (value_bits), so a series gives the same bits alone and in a batch beside a
+    series 30 times longer (whose length alone sets a coarser scale)."""
+    small = synth.light_curves(B=1, K=40, sizes=[3000], seed=synth.BASE_SEED + 301)
+    big = synth.light_curves(B=1, K=40, sizes=[90_000], seed=synth.BASE_SEED + 302)
+    lags = small.lags
+    alone = to_np(api.corr_batch(small.offs, small.t, small.x, lags, kernel="rectangle", h=0.5))
+    offs = np.array([0, small.t.size, small.t.size + big.t.size], dtype=np.int64)
+    t = np.concatenate([small.t, big.t]); x = np.concatenate([small.x, big.x])
+    both = to_np(api.corr_batch(offs, t, x, lags, kernel="rectangle", h=0.5))
+    assert np.array_equal(both["count"][0], alone["count"][0])
+    assert np.array_equal(both["c"][0], alone["c"][0])
