@@ -91,7 +91,8 @@ def test_chunked_host_batch_ccf_and_repeated_calls():
     """A chunked batch of cross-correlations (both sides uploaded per chunk, each
     chunk's statistics stage beside the previous chunk's evaluation), called
     twice on one context with a device-buffer call in between: every call equals
-    the device-buffer call (the rectangle exactly)."""
+    the device-buffer call (the rectangle exactly; the Gaussian through the FP64
+    and FP32 spectral forms within their tolerances)."""
     rng = np.random.default_rng(31)
     xs, ys = [], []
     for b in range(24):
@@ -119,6 +120,15 @@ def test_chunked_host_batch_ccf_and_repeated_calls():
             assert np.array_equal(out["c"].numpy(), ref["c"])
             dev = to_np(api.corr_batch(ox, t, x, lags, s=s, y=y, ctx=ctx, **kw))
             assert np.array_equal(dev["c"], ref["c"])
+        # the Gaussian through both spectral forms (each chunk on its own period)
+        for gk, tol in [(dict(path="spectral", precision="fp64"), 1e-10),
+                        (dict(path="spectral", precision="fp32"), 1e-5)]:
+            g = dict(kernel="gaussian", h=0.5, offs_y=oy, **gk)
+            gref = to_np(api.corr_batch(ox, t, x, lags, s=s, y=y, ctx=ctx, **g))
+            out = {"c": torch.empty(ox.size - 1, lags.size, dtype=torch.float64).pin_memory()}
+            api.corr_batch_host(ox, pinned(t), pinned(x), pinned(lags), s=pinned(s), y=pinned(y), out=out, ctx=ctx,
+                                **g)
+            assert max_abs(out["c"].numpy(), gref["c"]) <= tol
     finally:
         ctx.close()
 

@@ -81,3 +81,24 @@ def test_last_tuning_reports_the_shapes_used():
         assert ctx.last_tuning()["rect_variant"] in (0, 1, 2, 3)
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("variant", [4, 12])
+def test_fixed_point_tiles_with_outliers(variant):
+    """Fixed-point tile sums take their scale from the chunk's sum of |x_std|, so a
+    few extreme values coarsen it for every other point of the chunk: light curves
+    with five points per series raised 1000-fold (a 1000-sigma outlier next to
+    ordinary values), FP32 sums (variant 4) and fixed-point sums (12), both
+    against the FP64 spectral path at the FP32 form's 1e-5."""
+    w = synth.light_curves(B=48, n_lo=2000, n_hi=60_000, K=90, seed=91)
+    x = w.x.copy()
+    rng = np.random.default_rng(92)
+    for b in range(w.B):
+        a, e = int(w.offs[b]), int(w.offs[b + 1])
+        x[rng.choice(np.arange(a, e), 5, replace=False)] *= 1000.0
+    ref = to_np(api.corr_batch(w.offs, w.t, x, w.lags, kernel="gaussian", h=0.5, path="spectral",
+                               precision="fp64"))
+    got = _pinned(variant, lambda: to_np(api.corr_batch(w.offs, w.t, x, w.lags, kernel="gaussian", h=0.5,
+                                                        path="spectral", precision="fp32")))
+    assert np.all(np.isfinite(got["c"]))
+    assert np.max(np.abs(got["c"] - ref["c"])) < TOL
