@@ -334,7 +334,7 @@ constexpr int kPtBinsLog = 13;
 constexpr int kPtBins = 1 << kPtBinsLog;            // rank-table bins
 static_assert(kPtBins % (kPtWarps * 32) == 0, "bins split evenly over the threads");
 static_assert(kPtCap + 1 <= 65535, "rank-table entries are 16-bit entry indices");
-static_assert(kPtM % kPtBatch == 0, "whole batches");
+static_assert(kPtM % kPtBatch == 0 && kPtBatch % 2 == 0, "whole batches of slot pairs");
 static_assert(8 * kPtSamples <= 16 * (kPtCap + 1), "planning samples fit the staging area");
 
 struct PtSub {
@@ -550,23 +550,29 @@ __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (
             el[i] = lds_v4(ol[i]);
             eh[i] = lds_v4(oh[i]);
         }
-        // one warp-uniform walk per batch slot rather than one over the whole
-        // batch: a slot's 32 points are consecutive, so their edges lie in one
-        // short stretch of time, and a slot whose stretch falls between clusters
-        // of keys skips the walk however long its neighbours' walks are
+        // one warp-uniform walk per pair of batch slots rather than one over the
+        // whole batch: a slot's 32 points are consecutive, so their edges lie in
+        // one short stretch of time, and a pair whose stretches fall between
+        // clusters of keys skips the walk however long its neighbours' walks are;
+        // pairing halves the loop control and keeps two slots' loads in flight
 #pragma unroll
-        for (int i = 0; i < kPtBatch; ++i) {
-            bool step = (el[i].x < s[i] + L.x) | (eh[i].x < s[i] + L.z);
+        for (int i = 0; i < kPtBatch; i += 2) {
+            bool step = (el[i].x < s[i] + L.x) | (eh[i].x < s[i] + L.z) | (el[i + 1].x < s[i + 1] + L.x) |
+                        (eh[i + 1].x < s[i + 1] + L.z);
             while (__any_sync(0xffffffffu, step)) {
-                if (el[i].x < s[i] + L.x) {
-                    ol[i] += 16u;
-                    el[i] = lds_v4(ol[i]);
+#pragma unroll
+                for (int u = i; u < i + 2; ++u) {
+                    if (el[u].x < s[u] + L.x) {
+                        ol[u] += 16u;
+                        el[u] = lds_v4(ol[u]);
+                    }
+                    if (eh[u].x < s[u] + L.z) {
+                        oh[u] += 16u;
+                        eh[u] = lds_v4(oh[u]);
+                    }
                 }
-                if (eh[i].x < s[i] + L.z) {
-                    oh[i] += 16u;
-                    eh[i] = lds_v4(oh[i]);
-                }
-                step = (el[i].x < s[i] + L.x) | (eh[i].x < s[i] + L.z);
+                step = (el[i].x < s[i] + L.x) | (eh[i].x < s[i] + L.z) | (el[i + 1].x < s[i + 1] + L.x) |
+                       (eh[i + 1].x < s[i + 1] + L.z);
             }
         }
         bool band = false;
