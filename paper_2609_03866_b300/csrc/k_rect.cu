@@ -334,7 +334,7 @@ constexpr int kPtBinsLog = 13;
 constexpr int kPtBins = 1 << kPtBinsLog;            // rank-table bins
 static_assert(kPtBins % (kPtWarps * 32) == 0, "bins split evenly over the threads");
 static_assert(kPtCap + 1 <= 65535, "rank-table entries are 16-bit entry indices");
-static_assert(kPtM % kPtBatch == 0 && kPtBatch % 2 == 0, "whole batches of slot pairs");
+static_assert(kPtM % kPtBatch == 0, "whole batches");
 static_assert(8 * kPtSamples <= 16 * (kPtCap + 1), "planning samples fit the staging area");
 
 struct PtSub {
@@ -511,7 +511,7 @@ struct PtLagArgs {
 // One lag over this lane's outer points of the segment [pa, pb) (the whole
 // full tile when kFull).  Points are handled kPtBatch at a time: the rank-table
 // and entry loads of a batch are issued together; an edge whose bin holds keys
-// below its query steps forward in a warp-uniform loop per batch slot (about
+// below its query steps forward in one warp-uniform loop over the batch (about
 // 0.25 keys per query on the light-curve batch, but over a warp's 32 lanes the
 // loop runs to the largest count), then the rarely entered band test's FP64
 // fix-up, then the counts and the numerators.  Edge positions are
@@ -550,18 +550,21 @@ __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (
             el[i] = lds_v4(ol[i]);
             eh[i] = lds_v4(oh[i]);
         }
-        // one warp-uniform walk per pair of batch slots rather than one over the
-        // whole batch: a slot's 32 points are consecutive, so their edges lie in
-        // one short stretch of time, and a pair whose stretches fall between
-        // clusters of keys skips the walk however long its neighbours' walks are;
-        // pairing halves the loop control and keeps two slots' loads in flight
+        // one warp-uniform walk loop over the batch's four slots: the slots' loads
+        // are in flight together and the loop control is shared.  On the bench
+        // batch's rectangle call: 103.9 ms, against 104.8 ms for a loop per pair
+        // of slots, 105.7 ms for a loop per slot, and 108.6 ms for the same loop
+        // with its pending flag built up slot by slot (the compiler's code for
+        // that form is slower)
+        static_assert(kPtBatch == 4, "the walk below spells out four slots");
 #pragma unroll
-        for (int i = 0; i < kPtBatch; i += 2) {
+        for (int i = 0; i < kPtBatch; i += 4) {
             bool step = (el[i].x < s[i] + L.x) | (eh[i].x < s[i] + L.z) | (el[i + 1].x < s[i + 1] + L.x) |
-                        (eh[i + 1].x < s[i + 1] + L.z);
+                        (eh[i + 1].x < s[i + 1] + L.z) | (el[i + 2].x < s[i + 2] + L.x) | (eh[i + 2].x < s[i + 2] + L.z) |
+                        (el[i + 3].x < s[i + 3] + L.x) | (eh[i + 3].x < s[i + 3] + L.z);
             while (__any_sync(0xffffffffu, step)) {
 #pragma unroll
-                for (int u = i; u < i + 2; ++u) {
+                for (int u = i; u < i + 4; ++u) {
                     if (el[u].x < s[u] + L.x) {
                         ol[u] += 16u;
                         el[u] = lds_v4(ol[u]);
@@ -572,7 +575,8 @@ __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (
                     }
                 }
                 step = (el[i].x < s[i] + L.x) | (eh[i].x < s[i] + L.z) | (el[i + 1].x < s[i + 1] + L.x) |
-                       (eh[i + 1].x < s[i + 1] + L.z);
+                       (eh[i + 1].x < s[i + 1] + L.z) | (el[i + 2].x < s[i + 2] + L.x) | (eh[i + 2].x < s[i + 2] + L.z) |
+                       (el[i + 3].x < s[i + 3] + L.x) | (eh[i + 3].x < s[i + 3] + L.z);
             }
         }
         bool band = false;
