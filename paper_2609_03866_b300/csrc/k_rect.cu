@@ -550,12 +550,14 @@ __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (
             el[i] = lds_v4(ol[i]);
             eh[i] = lds_v4(oh[i]);
         }
-        // one warp-uniform walk loop over the batch's four slots: the slots' loads
-        // are in flight together and the loop control is shared.  On the bench
-        // batch's rectangle call: 103.9 ms, against 104.8 ms for a loop per pair
-        // of slots, 105.7 ms for a loop per slot, and 108.6 ms for the same loop
-        // with its pending flag built up slot by slot (the compiler's code for
-        // that form is slower)
+        // one warp-uniform walk loop over the batch's four slots, two predicated
+        // steps per iteration: the slots' loads are in flight together and the
+        // loop control (a vote) is shared by eight edges and two steps.  On the
+        // bench batch's rectangle call: 102.7 ms, against 103.9 ms with one step
+        // and 103.7 ms with three per iteration, 104.8 ms for a loop per pair of
+        // slots, 105.7 ms for a loop per slot, and 108.6 ms for one step per
+        // iteration with the pending flag built up slot by slot (the compiler's
+        // code for that form is slower)
         static_assert(kPtBatch == 4, "the walk below spells out four slots");
 #pragma unroll
         for (int i = 0; i < kPtBatch; i += 4) {
@@ -563,6 +565,17 @@ __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (
                         (eh[i + 1].x < s[i + 1] + L.z) | (el[i + 2].x < s[i + 2] + L.x) | (eh[i + 2].x < s[i + 2] + L.z) |
                         (el[i + 3].x < s[i + 3] + L.x) | (eh[i + 3].x < s[i + 3] + L.z);
             while (__any_sync(0xffffffffu, step)) {
+#pragma unroll
+                for (int u = i; u < i + 4; ++u) {
+                    if (el[u].x < s[u] + L.x) {
+                        ol[u] += 16u;
+                        el[u] = lds_v4(ol[u]);
+                    }
+                    if (eh[u].x < s[u] + L.z) {
+                        oh[u] += 16u;
+                        eh[u] = lds_v4(oh[u]);
+                    }
+                }
 #pragma unroll
                 for (int u = i; u < i + 4; ++u) {
                     if (el[u].x < s[u] + L.x) {
