@@ -26,6 +26,7 @@
 // across warps in shared memory and added to the output with integer
 // atomics.  A CTA whose union does not fit runs the same scan on global keys.
 #include <algorithm>
+#include <climits>
 #include <cstddef>
 #include <cmath>
 #include <cstdint>
@@ -369,6 +370,11 @@ __device__ __forceinline__ int4 lds_v4(uint32_t a) {
     asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
     return v;
 }
+__device__ __forceinline__ int32_t lds_s32(uint32_t a) {
+    int32_t v;
+    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
 __device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
     unsigned short v;
     asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
@@ -509,7 +515,9 @@ struct PtLagArgs {
 };
 
 // One lag over this lane's outer points of the segment [pa, pb) (the whole
-// full tile when kFull).  Points are handled kPtBatch at a time: the rank-table
+// full tile when kFull).  Bit q of m (warp-uniform) is clear when no window of
+// slot q's points at this lag can hold a key; a batch whose slots are all clear
+// is skipped.  Points are handled kPtBatch at a time: the rank-table
 // and entry loads of a batch are issued together; an edge whose bin holds keys
 // below its query steps forward in one warp-uniform loop over the batch (about
 // 0.25 keys per query on the light-curve batch, but over a warp's 32 lanes the
@@ -519,9 +527,11 @@ struct PtLagArgs {
 template <bool kFull>
 __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (&sc)[kPtM],
                                        const int32_t (&y0)[kPtM], const int32_t (&y1)[kPtM], int pbase,
-                                       int32_t sca, int4 L, const PtLagArgs &g, unsigned &c, PtAcc &A) {
+                                       int32_t sca, int4 L, uint32_t m, const PtLagArgs &g, unsigned &c,
+                                       PtAcc &A) {
 #pragma unroll
     for (int q0 = 0; q0 < kPtM; q0 += kPtBatch) {
+        if (((m >> q0) & ((1u << kPtBatch) - 1u)) == 0u) continue;
         int32_t s[kPtBatch];
         bool ok[kPtBatch];
 #pragma unroll
@@ -529,12 +539,6 @@ __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (
             const int pt = pbase + pt_off(q0 + i);
             ok[i] = kFull || (pt >= g.pa && pt < g.pb);
             s[i] = ok[i] ? sc[q0 + i] : sca;  // a point outside the segment queries in range, counts nothing
-        }
-        if (!kFull) {  // a warp with no point of the segment in this batch skips it
-            bool any = false;
-#pragma unroll
-            for (int i = 0; i < kPtBatch; ++i) any |= ok[i];
-            if (!__any_sync(0xffffffffu, any)) continue;
         }
         uint32_t ol[kPtBatch], oh[kPtBatch];
         int4 el[kPtBatch], eh[kPtBatch];
@@ -878,16 +882,48 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                     }
                 }
                 __syncthreads();
+                // Slots whose windows are empty at a lag.  Slot q of this warp holds 32
+                // consecutive outer points with query offsets in [lo_q, hi_q] (points
+                // of the segment only).  At lag kl, keys below lo_q + L.x are certainly
+                // below every lower bound of the slot (the walk's test) and keys at or
+                // above hi_q + L.w certainly above every upper bound (the band test's),
+                // so when the first key at or above lo_q + L.x is at or above
+                // hi_q + L.w, every window of the slot is empty: count 0, window sum 0.
+                // Lane kl - ka keeps lag kl's mask of the other slots.  Windows that
+                // fall in a seasonal gap or on nights without data are skipped.
+                uint32_t act = 0;
+                {
+                    const int4 Lm = sm.lc[sb.ka + min(lane, sb.kb - sb.ka - 1)];
+#pragma unroll
+                    for (int q = 0; q < kPtM; ++q) {
+                        const int pt = pbase + pt_off(q);
+                        const bool in = full || (pt >= pa && pt < pb);
+                        const int32_t lo_q = __reduce_min_sync(0xffffffffu, in ? sc[q] : INT_MAX);
+                        const int32_t hi_q = __reduce_max_sync(0xffffffffu, in ? sc[q] : INT_MIN);
+                        if (lo_q <= hi_q) {
+                            const int32_t v = lo_q + Lm.x;
+                            uint32_t a = aE + (lds_u16(pt_bin_addr(aT, v, mult)) << 4);
+                            int32_t key = lds_s32(a);
+                            while (key < v) {
+                                a += 16u;
+                                key = lds_s32(a);
+                            }
+                            act |= (key < hi_q + Lm.w ? 1u : 0u) << q;
+                        }
+                    }
+                }
                 PtLagArgs ga{Tx, Sy, dls, dus, tx, sy, slags, tile.j0, 0, sb.ia, lim, eta, h, eps, pa, pb, mult};
                 for (int kl = sb.ka; kl < sb.kb; ++kl) {
+                    const uint32_t m = __shfl_sync(0xffffffffu, act, kl - sb.ka);
+                    if (m == 0u) continue;  // every window of the warp's points is empty
                     const int4 L = sm.lc[kl];
                     ga.k = k0 + kl;
                     unsigned int c = 0;
                     PtAcc A{0, 0, 0, 0, 0, 0};
                     if (full)
-                        pt_lag<true>(aE, aT, sc, y0, y1, pbase, sca, L, ga, c, A);
+                        pt_lag<true>(aE, aT, sc, y0, y1, pbase, sca, L, m, ga, c, A);
                     else
-                        pt_lag<false>(aE, aT, sc, y0, y1, pbase, sca, L, ga, c, A);
+                        pt_lag<false>(aE, aT, sc, y0, y1, pbase, sca, L, m, ga, c, A);
                     c = __reduce_add_sync(0xffffffffu, c >> 4);
                     U128 acc = pt_combine(A);
 #pragma unroll
