@@ -293,8 +293,8 @@ rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
 
 // ---------------------------------------------------------------------------
 // Points-on-lanes scan.  Lane l of warp w owns the outer points
-// (q 8 + w) 32 + l (q < 8) of the tile, so at every step the 32 lanes of a warp
-// hold 32 consecutive outer points: their window edges sit at neighbouring
+// ((b 8 + w) 4 + i) 32 + l (b < 2, i < 4) of the tile, so at every step the 32 lanes
+// of a warp hold 32 consecutive outer points: their window edges sit at neighbouring
 // positions of the staged keys (conflict-free shared-memory access) and the
 // loop over the lags of the group is warp-uniform.  A window edge is found in
 // O(1): a rank table over uniform bins of the coarse key range gives the first
@@ -324,10 +324,14 @@ rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
 constexpr int kPtWarps = 8;
 constexpr int kPtM = kRectTile / (kPtWarps * 32);  // outer points per lane
 constexpr int kPtBatch = 4;                         // points of a lane handled together (load ILP)
-// Lane l of warp w owns points (q kPtWarps + w) 32 + l, q < kPtM: each warp's
-// groups of 32 consecutive points are spread over the whole tile, so dense and
-// sparse stretches of a tile fall evenly on the warps.
-__device__ __forceinline__ constexpr int pt_off(int q) { return q * (kPtWarps * 32); }
+// Lane l of warp w owns point ((b kPtWarps + w) kPtBatch + i) 32 + l of the tile for
+// slot q = b kPtBatch + i: the kPtBatch slots of a batch are 32 kPtBatch consecutive
+// points (their windows tend to be empty together, so the batch is skipped whole),
+// and each warp's batches are spread over the tile.
+__device__ __forceinline__ constexpr int pt_off(int q) {
+    return (q / kPtBatch) * (kPtWarps * kPtBatch * 32) + (q % kPtBatch) * 32;
+}
+__device__ __forceinline__ constexpr int pt_base(int warp, int lane) { return warp * kPtBatch * 32 + lane; }
 constexpr int kPtCap = 5300;                        // staged entries per sub-group
 constexpr int kPtSamples = 1024;                    // planning samples of a lag group's key range
 constexpr int kPtExact = 16;                        // sample stride up to which the bounds stay coarse
@@ -667,7 +671,7 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
     }
     // this lane's outer points: coarse offsets and the two limbs of Y
     int32_t sc[kPtM], y0[kPtM], y1[kPtM];
-    const int pbase = warp * 32 + lane;
+    const int pbase = pt_base(warp, lane);
 #pragma unroll
     for (int q = 0; q < kPtM; ++q) {
         const int pt = pbase + pt_off(q);
