@@ -323,7 +323,7 @@ rect_scan_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ P,
 // ---------------------------------------------------------------------------
 constexpr int kPtWarps = 8;
 constexpr int kPtM = kRectTile / (kPtWarps * 32);  // outer points per lane
-constexpr int kPtBatch = 4;                         // points of a lane handled together (load ILP)
+constexpr int kPtBatch = 2;                         // points of a lane handled together (load ILP)
 // Lane l of warp w owns point ((b kPtWarps + w) kPtBatch + i) 32 + l of the tile for
 // slot q = b kPtBatch + i: the kPtBatch slots of a batch are 32 kPtBatch consecutive
 // points (their windows tend to be empty together, so the batch is skipped whole),
@@ -566,15 +566,14 @@ __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (
         // slots, 105.7 ms for a loop per slot, and 108.6 ms for one step per
         // iteration with the pending flag built up slot by slot (the compiler's
         // code for that form is slower)
-        static_assert(kPtBatch == 4, "the walk below spells out four slots");
+        static_assert(kPtBatch == 2 || kPtBatch == 4, "the walk below spells out two or four slots");
+        const auto pend = [&](int u) { return (el[u].x < s[u] + L.x) | (eh[u].x < s[u] + L.z); };
+        bool step = kPtBatch == 4 ? pend(0) | pend(1) | pend(2) | pend(3) : pend(0) | pend(1);
+        while (__any_sync(0xffffffffu, step)) {
 #pragma unroll
-        for (int i = 0; i < kPtBatch; i += 4) {
-            bool step = (el[i].x < s[i] + L.x) | (eh[i].x < s[i] + L.z) | (el[i + 1].x < s[i + 1] + L.x) |
-                        (eh[i + 1].x < s[i + 1] + L.z) | (el[i + 2].x < s[i + 2] + L.x) | (eh[i + 2].x < s[i + 2] + L.z) |
-                        (el[i + 3].x < s[i + 3] + L.x) | (eh[i + 3].x < s[i + 3] + L.z);
-            while (__any_sync(0xffffffffu, step)) {
+            for (int r = 0; r < 2; ++r) {
 #pragma unroll
-                for (int u = i; u < i + 4; ++u) {
+                for (int u = 0; u < kPtBatch; ++u) {
                     if (el[u].x < s[u] + L.x) {
                         ol[u] += 16u;
                         el[u] = lds_v4(ol[u]);
@@ -584,21 +583,8 @@ __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (
                         eh[u] = lds_v4(oh[u]);
                     }
                 }
-#pragma unroll
-                for (int u = i; u < i + 4; ++u) {
-                    if (el[u].x < s[u] + L.x) {
-                        ol[u] += 16u;
-                        el[u] = lds_v4(ol[u]);
-                    }
-                    if (eh[u].x < s[u] + L.z) {
-                        oh[u] += 16u;
-                        eh[u] = lds_v4(oh[u]);
-                    }
-                }
-                step = (el[i].x < s[i] + L.x) | (eh[i].x < s[i] + L.z) | (el[i + 1].x < s[i + 1] + L.x) |
-                       (eh[i + 1].x < s[i + 1] + L.z) | (el[i + 2].x < s[i + 2] + L.x) | (eh[i + 2].x < s[i + 2] + L.z) |
-                       (el[i + 3].x < s[i + 3] + L.x) | (eh[i + 3].x < s[i + 3] + L.z);
             }
+            step = kPtBatch == 4 ? pend(0) | pend(1) | pend(2) | pend(3) : pend(0) | pend(1);
         }
         bool band = false;
 #pragma unroll
