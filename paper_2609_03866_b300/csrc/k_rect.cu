@@ -332,11 +332,15 @@ __device__ __forceinline__ constexpr int pt_off(int q) {
     return (q / kPtBatch) * (kPtWarps * kPtBatch * 32) + (q % kPtBatch) * 32;
 }
 __device__ __forceinline__ constexpr int pt_base(int warp, int lane) { return warp * kPtBatch * 32 + lane; }
-constexpr int kPtCap = 5300;                        // staged entries per sub-group
+constexpr int kPtCap = 5430;                        // staged entries per sub-group
 constexpr int kPtSamples = 1024;                    // planning samples of a lag group's key range
 constexpr int kPtExact = 16;                        // sample stride up to which the bounds stay coarse
-constexpr int kPtBinsLog = 13;
-constexpr int kPtBins = 1 << kPtBinsLog;            // rank-table bins
+// rank-table bins; with the staging area, the shared memory of two CTAs per SM.
+// On the bench batch's rectangle call: 8192 bins and 5680 entries 83.4 ms, 10240
+// and 5430 81.8 ms, 12288 and 5170 81.9 ms, 14336 and 4915 82.2 ms, 16384 and
+// 4650 87.1 ms (finer bins shorten the walks, a smaller staging area means more
+// sub-groups)
+constexpr int kPtBins = 10240;
 static_assert(kPtBins % (kPtWarps * 32) == 0, "bins split evenly over the threads");
 static_assert(kPtCap + 1 <= 65535, "rank-table entries are 16-bit entry indices");
 static_assert(kPtM % kPtBatch == 0, "whole batches");
