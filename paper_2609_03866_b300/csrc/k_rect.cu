@@ -341,6 +341,8 @@ constexpr int kPtExact = 16;                        // sample stride up to which
 // 4650 87.1 ms (finer bins shorten the walks, a smaller staging area means more
 // sub-groups)
 constexpr int kPtBins = 10240;
+constexpr int kPtWords = kPtBins / 2 / (kPtWarps * 32);  // 32-bit words of the rank table per thread
+static_assert(kPtWords * 2 * kPtWarps * 32 == kPtBins && kPtWords % 4 == 0, "whole 16-byte rows per thread");
 static_assert(kPtBins % (kPtWarps * 32) == 0, "bins split evenly over the threads");
 static_assert(kPtCap + 1 <= 65535, "rank-table entries are 16-bit entry indices");
 static_assert(kPtM % kPtBatch == 0, "whole batches");
@@ -822,7 +824,13 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(slot + 8u), "l"(P + sb.ia + i)
                                  : "memory");
                 }
+                // the rank table is built as a histogram of the keys' bins (two 16-bit
+                // counters per word) and then scanned: cleared while the copies fly
+                uint32_t *const T32 = reinterpret_cast<uint32_t *>(sm.sT);
+                for (int i = tid; i < kPtBins / 8; i += blockDim.x)
+                    reinterpret_cast<uint4 *>(T32)[i] = make_uint4(0u, 0u, 0u, 0u);
                 asm volatile("cp.async.wait_all;" ::: "memory");
+                __syncthreads();
                 // prefix sums rebased to the first entry's: |P[ia + i] - P[ia]| is a sum
                 // of |X| within one series, below n 2^p + n/2 < 2^61 (sum |x_std| <= n for
                 // ddof 0 and p <= 61 - 1.5 log2 n), so the three limbs never wrap
@@ -833,6 +841,8 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                     if (i < nK) {
                         const int64_t v = ((raw.x - base) >> sh) - vmin;
                         key = (int32_t)max(min(v, (int64_t)(1 << 30)), (int64_t)-1);
+                        const uint32_t bk = pt_bin(key, mult);
+                        if (bk < (uint32_t)kPtBins) atomicAdd(T32 + (bk >> 1), (bk & 1u) ? 0x10000u : 1u);
                     }
                     const int64_t pv = (int64_t)((unsigned long long)raw.y - (unsigned long long)P0);
                     sm.sE[i] = make_int4(key, (int32_t)(pv & 0x1fffff), (int32_t)((pv >> 21) & 0x1fffff),
@@ -847,33 +857,45 @@ rect_scan_pt_kernel(const int64_t *__restrict__ Tx, const int64_t *__restrict__ 
                                                    (int32_t)((S0 + du + eta - base) >> sh) + 2 - vmin);
                 }
                 __syncthreads();
-                // rank table: sT[b] = the first index whose key's bin is >= b, as a
-                // merge of the bins b with the keys, bin b before key e iff
-                // bin(key_e) >= b.  Each thread takes an equal share of the
-                // merged sequence (merge path), so a dense stretch of keys and a
-                // long gap cost the same; entry nK is the sentinel, after every bin.
+                // rank table: sT[b] = the first index whose key's bin is >= b, which for
+                // sorted keys (bins non-decreasing) is the number of keys in bins below b:
+                // the exclusive prefix sum of the histogram.  Entry nK, the sentinel, is
+                // after every bin.  Each thread scans 2 kPtWords consecutive bins, the
+                // warps' totals are combined through shared memory (the per-warp sums
+                // of the lag loop's results are written only at the end of the CTA).
                 {
-                    constexpr int kThreads = kPtWarps * 32;
-                    const int nE = max(nK, 0) + 1;
-                    const int total = kPtBins + nE;
-                    const int d0 = (int)(((long long)tid * total) / kThreads);
-                    const int d1 = (int)(((long long)(tid + 1) * total) / kThreads);
-                    int lo = max(0, d0 - nE), hi = min(d0, kPtBins);  // bins among the first d0
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (pt_bin(sm.sE[d0 - 1 - mid].x, mult) >= (uint32_t)mid) lo = mid + 1; else hi = mid;
+                    uint32_t w[kPtWords];
+                    const uint4 *src = reinterpret_cast<const uint4 *>(T32 + tid * kPtWords);
+#pragma unroll
+                    for (int q = 0; q < kPtWords / 4; ++q) {
+                        const uint4 u = src[q];
+                        w[4 * q] = u.x;
+                        w[4 * q + 1] = u.y;
+                        w[4 * q + 2] = u.z;
+                        w[4 * q + 3] = u.w;
                     }
-                    int a = lo, e = d0 - lo;
-                    int32_t ke = sm.sE[min(e, nE - 1)].x;
-                    for (int d = d0; d < d1 && a < kPtBins; ++d) {
-                        if (pt_bin(ke, mult) >= (uint32_t)a) {
-                            sm.sT[a] = (uint16_t)e;
-                            ++a;
-                        } else {
-                            ++e;
-                            ke = sm.sE[min(e, nE - 1)].x;
-                        }
+                    uint32_t run = 0;  // below 2^16: at most kPtCap keys
+#pragma unroll
+                    for (int q = 0; q < kPtWords; ++q) {
+                        const uint32_t lo = w[q] & 0xffffu, hi = w[q] >> 16;
+                        w[q] = run | ((run + lo) << 16);
+                        run += lo + hi;
                     }
+                    uint32_t inc = run;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    if (lane == 31) sm.pc[0][warp] = inc;
+                    __syncthreads();
+                    uint32_t off = inc - run;
+                    for (int v = 0; v < warp; ++v) off += sm.pc[0][v];
+                    off *= 0x10001u;
+                    uint4 *dst = reinterpret_cast<uint4 *>(T32 + tid * kPtWords);
+#pragma unroll
+                    for (int q = 0; q < kPtWords / 4; ++q)
+                        dst[q] = make_uint4(w[4 * q] + off, w[4 * q + 1] + off, w[4 * q + 2] + off, w[4 * q + 3] + off);
                 }
                 __syncthreads();
                 // Slots whose windows are empty at a lag.  Slot q of this warp holds 32
