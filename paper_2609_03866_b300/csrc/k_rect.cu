@@ -332,15 +332,15 @@ __device__ __forceinline__ constexpr int pt_off(int q) {
     return (q / kPtBatch) * (kPtWarps * kPtBatch * 32) + (q % kPtBatch) * 32;
 }
 __device__ __forceinline__ constexpr int pt_base(int warp, int lane) { return warp * kPtBatch * 32 + lane; }
-constexpr int kPtCap = 5430;                        // staged entries per sub-group
+constexpr int kPtCap = 4915;                        // staged entries per sub-group
 constexpr int kPtSamples = 1024;                    // planning samples of a lag group's key range
 constexpr int kPtExact = 16;                        // sample stride up to which the bounds stay coarse
 // rank-table bins; with the staging area, the shared memory of two CTAs per SM.
-// On the bench batch's rectangle call: 8192 bins and 5680 entries 83.4 ms, 10240
-// and 5430 81.8 ms, 12288 and 5170 81.9 ms, 14336 and 4915 82.2 ms, 16384 and
-// 4650 87.1 ms (finer bins shorten the walks, a smaller staging area means more
-// sub-groups)
-constexpr int kPtBins = 10240;
+// On the bench batch's rectangle plan (histogram-built table): 10240 bins and
+// 5430 entries 78.5 ms, 12288 and 5170 77.9 ms, 14336 and 4915 77.1 ms, 16384 and
+// 4650 84.1 ms (finer bins shorten the walks; a smaller staging area means more
+// sub-groups, and below about 4900 entries more split segments)
+constexpr int kPtBins = 14336;
 constexpr int kPtWords = kPtBins / 2 / (kPtWarps * 32);  // 32-bit words of the rank table per thread
 static_assert(kPtWords * 2 * kPtWarps * 32 == kPtBins && kPtWords % 4 == 0, "whole 16-byte rows per thread");
 static_assert(kPtBins % (kPtWarps * 32) == 0, "bins split evenly over the threads");
