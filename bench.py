@@ -54,7 +54,7 @@ WORKLOAD = "light_curves: 4096 series, n log-uniform [200, 2e5], 256 lags on [0,
 # lags), dram__bytes_read.sum + dram__bytes_write.sum from one single-pass ncu capture of
 # this command.  Reported as the roofline's traffic only for that workload; update or
 # remove an entry whenever its kernel changes.
-MEASURED_TRAFFIC = {("rect_scan_pt_kernel", 4096): 3.02e9 + 30.70e6}
+MEASURED_TRAFFIC = {("rect_scan_pt_kernel", 4096): 3.0136e9 + 30.24e6}
 
 
 # Integer rates of this GPU measured by a probe of independent instruction chains
