@@ -564,14 +564,13 @@ __device__ __forceinline__ void pt_lag(uint32_t aE, uint32_t aT, const int32_t (
             el[i] = lds_v4(ol[i]);
             eh[i] = lds_v4(oh[i]);
         }
-        // one warp-uniform walk loop over the batch's four slots, two predicated
-        // steps per iteration: the slots' loads are in flight together and the
-        // loop control (a vote) is shared by eight edges and two steps.  On the
-        // bench batch's rectangle call: 102.7 ms, against 103.9 ms with one step
-        // and 103.7 ms with three per iteration, 104.8 ms for a loop per pair of
-        // slots, 105.7 ms for a loop per slot, and 108.6 ms for one step per
-        // iteration with the pending flag built up slot by slot (the compiler's
-        // code for that form is slower)
+        // one warp-uniform walk loop over the batch's slots, two predicated steps
+        // per iteration: the slots' loads are in flight together and the loop
+        // control (a vote) is shared by all the batch's edges and two steps.  With
+        // four-slot batches on the bench batch's rectangle call: 102.7 ms, against
+        // 103.9 ms with one step and 103.7 ms with three per iteration, 104.8 ms for
+        // a loop per pair of slots, 105.7 ms for a loop per slot; with two-slot
+        // batches one step per iteration is 1 % slower than two
         static_assert(kPtBatch == 2 || kPtBatch == 4, "the walk below spells out two or four slots");
         const auto pend = [&](int u) { return (el[u].x < s[u] + L.x) | (eh[u].x < s[u] + L.z); };
         bool step = kPtBatch == 4 ? pend(0) | pend(1) | pend(2) | pend(3) : pend(0) | pend(1);
