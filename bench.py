@@ -975,6 +975,25 @@ def main():
     roof["traffic"] = MEASURED_TRAFFIC.get((name, B))
     roof["share"] = share
 
+    # the memory-side kernels of the FP32 form and the statistics pass against the HBM
+    # roofline: algorithmic bytes per step (spreading: t and x in, one complex FP32 cell
+    # out per grid cell; shared-memory FFT: the grid in, M complex FP32 spectrum values
+    # out per series; global-pass FFT: the grid in and out once per radix-8/4/2 pass;
+    # statistics: t and x in) over the kernel's time per step
+    def hbm_frac(kname, byts):
+        if kname not in prof:
+            return None
+        per_step_s = prof[kname][1] / 1e3 / args.steps
+        gbs = byts / per_step_s / 1e9
+        return {"ms_per_step": per_step_s * 1e3, "bytes_per_step": byts, "achieved": gbs, "unit": "GB/s",
+                "peak": hbm, "frac": gbs / hbm}
+
+    hbm_kernels = {k: v for k, v in (
+        ("spread_kernel", hbm_frac("spread_kernel", 16.0 * n_pts + 8.0 * B * nf)),
+        ("fft_spectrum_smem_kernel", hbm_frac("fft_spectrum_smem_kernel", 8.0 * B * nf + 8.0 * B * M)),
+        ("fft_pass_kernel", hbm_frac("fft_pass_kernel", 16.0 * B * nf * int(np.ceil(np.log2(nf) / 3)))),
+        ("stats_chunks_kernel", hbm_frac("stats_chunks_kernel", 16.0 * n_pts))) if v is not None}
+
     line = {
         "metric": METRIC, "value": value, "unit": "series*lags/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
@@ -1007,6 +1026,7 @@ def main():
         "device_memory": mem,
         "clocks": clk.summary(),
         "roofline": roof,
+        "hbm_kernels": hbm_kernels,
         "e2e": e2e,
         "north_star": fp64,
         "paper_timings": {
