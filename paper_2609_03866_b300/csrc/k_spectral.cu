@@ -424,6 +424,17 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
             atomic_add_v(&grid[cell & mask], re, im);
         }
     };
+    // FP32 taps (W = 8): the 36 polynomial coefficients stay in registers for the
+    // whole point loop instead of being read from the constant bank for every point
+    // (spreading on the bench batch 1.389 -> 1.212 ms at 90 registers, no spills);
+    // the FP64 form's 120 coefficients (W = 16) stay in the constant bank
+    constexpr bool kHoist = sizeof(R) == 4;
+    constexpr int kNc = W / 2 * (D + 1);
+    R cf[kHoist ? kNc : 1];
+    if constexpr (kHoist) {
+#pragma unroll
+        for (int i = 0; i < kNc; ++i) cf[i] = poly.c[i];
+    }
 #pragma unroll 1
     for (int q = 0; q < kPer; ++q) {
         const int p = lane * kRunLen + warp * kPer + q;
@@ -465,7 +476,8 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
         const R v = u * u;
 #pragma unroll
         for (int k = 0; k < W / 2; ++k) {
-            const R *c = poly.c + k * (D + 1);
+            const R *c;
+            if constexpr (kHoist) c = cf + k * (D + 1); else c = poly.c + k * (D + 1);
             constexpr int De = D & ~1, Do = (D - 1) | 1;  // highest even / odd power
             R e = c[De], o = c[Do];
 #pragma unroll
