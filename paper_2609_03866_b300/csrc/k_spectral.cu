@@ -428,8 +428,8 @@ spread_kernel(const double *__restrict__ t, const double *__restrict__ x,
     };
     // FP32 taps (W = 8): the 36 polynomial coefficients are copied into a local
     // array before the point loop.  The compiler still reads them from the
-    // parameter bank where they are used, but the FP32 instances came down from 62
-    // to 39 registers and the spreading on the bench batch from 1.389 to 1.212 ms.
+    // parameter bank where they are used, but the FP32 instances came down from 48-78
+    // to 39-63 registers and the spreading on the bench batch from 1.389 to 1.212 ms.
     // The FP64 form (W = 16, 120 coefficients) reads poly.c directly.
     constexpr bool kHoist = sizeof(R) == 4;
     constexpr int kNc = W / 2 * (D + 1);
